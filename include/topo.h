@@ -1,0 +1,164 @@
+/*
+ * libtopo: C ABI of the GB300 (sm_103a) hot path of the ROM-accelerated minimum-compliance
+ * SIMP method of Yano, Huang and Zahr (arXiv 2004.05756).
+ *
+ * The operator behind every call is the penalised linear-elasticity stiffness
+ *     K(rho) = sum_e E(rho_e) P_e K_e P_e^T,   E(rho) = Emin + rho^p (E0 - Emin)
+ * (Section 2.1, Eq. linelast-res1, with the material law written as Emin/E0; the paper's
+ * alpha(rho) = rho_l + (1 - rho_l) rho^p is Emin = rho_l E0), applied matrix-free on a
+ * structured grid of unit Q4 (2D, plane stress) or H8 (3D) elements.
+ *
+ * Conventions shared by all calls:
+ *   - Node n = i + (nx+1)(j + (ny+1)k), x fastest. DOF = dim*n + c (interleaved).
+ *     Element e = i + nx(j + ny k). N = dim * nodes, N_e = elements.
+ *   - Vector blocks are column-major N x m with leading dimension ld >= N (in elements).
+ *   - Homogeneous Dirichlet DOFs stay in the vectors: their rows and columns of K act as the
+ *     identity and the loads must be zero there. On the free DOFs this is exactly the
+ *     paper's elimination of Dirichlet DOFs (the remark after Eq. linelastU).
+ *   - Every array argument is a DEVICE pointer owned by the caller, 8-byte aligned, unless a
+ *     comment says "host". The context owns only its own scratch.
+ *   - Calls are asynchronous and ordered on the CUDA stream given to topo_create. Scalar
+ *     outputs are device pointers. A call that must return host data (noted below)
+ *     synchronises the stream.
+ *   - Every call returns a topo_status and never aborts or traps. Invalid arguments return
+ *     TOPO_ERR_INVALID before anything is launched; topo_last_error() gives a message.
+ *     Errors found on the device (non-SPD reduced matrix, timeouts in device-side waits,
+ *     breakdown) are recorded in a sticky device status word read by topo_check().
+ *   - A context must not be used from two host threads at once.
+ */
+#ifndef TOPO_H
+#define TOPO_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct topo_ctx topo_ctx;
+
+typedef enum {
+  TOPO_OK = 0,
+  TOPO_ERR_INVALID = 1,       /* bad argument, shape, pointer or problem description */
+  TOPO_ERR_OOM = 2,           /* scratch allocation failed */
+  TOPO_ERR_NOT_CONVERGED = 3, /* PCG reached maxit before rtol */
+  TOPO_ERR_NOT_SPD = 4,       /* non-positive pivot in the k x k Cholesky or p^T K p <= 0 */
+  TOPO_ERR_TIMEOUT = 5,       /* a device-side wait gave up (bounded spin) */
+  TOPO_ERR_CUDA = 6           /* a CUDA runtime call failed */
+} topo_status;
+
+/* Arithmetic of the operator applications inside a call.
+ *   TOPO_FP64               every step in FP64.
+ *   TOPO_FP32_REFINED       K(rho)V with FP32 vectors, FP32 E(rho) and FP32 K_e, wrapped in
+ *                           FP64-residual iterative refinement where the call has a fixed
+ *                           point (topo_solve_hdm, topo_rom_solve).
+ *   TOPO_FP32_BF16KE_REFINED as above but K_e entries rounded to BF16 (scaled per element by
+ *                           E(rho_e), FP32 accumulation). */
+typedef enum { TOPO_FP64 = 0, TOPO_FP32_REFINED = 1, TOPO_FP32_BF16KE_REFINED = 2 } topo_prec;
+
+/* Problem description. dim = 2 (Q4, nz ignored) or 3 (H8). 1 <= nx, ny, nz; N < 2^31.
+ * E0 > Emin >= 0; 0 <= nu < 0.5; penal an integer in [1, 6]; rmin in (0, 6] is the radius
+ * of the linear density filter in element lengths. fixed_dof_mask is a HOST array of N bytes
+ * (non-zero = homogeneous Dirichlet DOF), copied at creation. */
+typedef struct {
+  int dim, nx, ny, nz;
+  double E0, Emin, nu, penal, rmin;
+  const unsigned char* fixed_dof_mask;
+} topo_problem;
+
+/* Host-side report of topo_solve_hdm (max over load cases). */
+typedef struct {
+  int iters;      /* total PCG iterations (inner FP32 iterations for refined forms) */
+  int outer;      /* FP64 refinement steps (0 for TOPO_FP64) */
+  double relres;  /* final ||f - K u||_2 / ||f||_2 over free DOFs, FP64 */
+  int status;     /* topo_status of the solve */
+} topo_solve_info;
+
+/* Tunable parameters (topo_set_param). */
+typedef enum {
+  TOPO_PARAM_INNER_RTOL = 0,   /* relative tolerance of each FP32 inner PCG solve (default 1e-5) */
+  TOPO_PARAM_MAX_OUTER = 1,    /* max FP64 refinement steps (default 30) */
+  TOPO_PARAM_WAIT_CYCLES = 2,  /* spin limit of device-side waits, in SM clock cycles (default 2e9) */
+  TOPO_PARAM_ROM_REFINE = 3,   /* max FP64 refinement steps of the reduced solve (default 8) */
+  TOPO_PARAM_TILE_X = 4,       /* apply tile width in nodes (autotuner hint; 0 = default) */
+  TOPO_PARAM_PCG_BLOCKS_PER_SM = 5 /* CTAs per SM of the persistent PCG (0 = occupancy) */
+} topo_param;
+
+/* Create a context for one problem; computes K_e (2x2(x2) Gauss quadrature), the filter
+ * weights and normalisers, and uploads the Dirichlet mask. cuda_stream is a cudaStream_t
+ * (NULL = legacy default stream) that the context borrows. The current CUDA device at
+ * creation is the context's device. Allocates device scratch. */
+topo_status topo_create(const topo_problem* prob, void* cuda_stream, topo_ctx** out);
+topo_status topo_destroy(topo_ctx* ctx);
+const char* topo_last_error(const topo_ctx* ctx);
+topo_status topo_set_param(topo_ctx* ctx, topo_param which, double value);
+
+/* Synchronise the context's stream and return (and clear) the sticky device status. */
+topo_status topo_check(topo_ctx* ctx);
+
+/* Sizes of the context's problem (host outputs; any may be NULL). */
+topo_status topo_sizes(const topo_ctx* ctx, long long* ndof, long long* nel, long long* nnodes);
+
+/* Linear density filter (the benchmark's replacement of the Helmholtz filter of
+ * Section 2.2, Eq. cdens-star): w_ei = max(0, rmin - |c_e - c_i|), Hs_e = sum_i w_ei.
+ * adjoint == 0: out_e = sum_i w_ei in_i / Hs_e           (rho = filter(psi))
+ * adjoint != 0: out_i = sum_e w_ei in_e / Hs_e           ((d rho/d psi)^T v, used by
+ *                                                          Eq. pap_sensitivity)
+ * in, out: FP64[N_e], must not alias. */
+topo_status topo_filter(topo_ctx* ctx, const double* in, double* out, int adjoint);
+
+/* Y = K(rho) V for m columns (Eq. linelast-res1, matrix-free). rho: FP64[N_e] in [0, 1].
+ * V, Y: N x m with leading dimension ld, FP64 for TOPO_FP64, FP32 otherwise. Dirichlet rows
+ * give Y = V. V and Y must not alias. m = 0 is a no-op. */
+topo_status topo_apply_K(topo_ctx* ctx, const double* rho, const void* V, void* Y, int m, int ld,
+                         topo_prec prec);
+
+/* State solve K(rho) u = f (Eq. linelastsoln) for m load cases by Jacobi-preconditioned CG
+ * in one persistent cooperative launch, to ||f - K u||_2 <= rtol ||f||_2 over free DOFs
+ * (each column separately). F, U: FP64 N x m, ld; U holds the initial guess on entry and
+ * the solution on exit (Dirichlet DOFs set to 0). maxit bounds the (inner) iterations.
+ * info_host (host, may be NULL): if non-NULL the call synchronises and fills it, and
+ * returns TOPO_ERR_NOT_CONVERGED when rtol was not reached. */
+topo_status topo_solve_hdm(topo_ctx* ctx, const double* rho, const double* F, double* U, int m,
+                           int ld, double rtol, int maxit, topo_prec prec,
+                           topo_solve_info* info_host);
+
+/* Reduced basis from snapshots (Eq. rob-optim; for compliance the adjoint snapshots equal
+ * the primal ones): classical Gram-Schmidt applied twice to the columns of Usnap (FP64
+ * N x m, ld) in order, dropping a column whose orthogonalised norm is < 1e-10 times the
+ * largest snapshot norm. Writes the k kept orthonormal columns to Phi (FP64, capacity
+ * N x m, same ld), then H = Phi^T K(rho) Phi (FP64 k x k, row-major, leading dimension k,
+ * capacity m*m) and b = Phi^T f (FP64[k]; f FP64[N]) (Eq. hatkbm). k_out is a HOST int;
+ * the call synchronises to return it. Usnap and Phi may be the same buffer. */
+topo_status topo_rom_build(topo_ctx* ctx, const double* rho, const double* Usnap, int m, int ld,
+                           double* Phi, int* k_out, double* H, double* b, const double* f);
+
+/* Reduced solve at a new density (Section 3.1 and the cost analysis of Section 3.4):
+ * H(rho) = Phi^T K(rho) Phi, Cholesky H = L L^T in FP64, yhat = H^{-1} b, Jk = b^T yhat.
+ * Phi: FP64 N x k, ld; b FP64[k]; H_work FP64 k*k (on exit: L in the lower triangle,
+ * row-major); yhat FP64[k]; Jk device FP64 scalar. 1 <= k <= 128.
+ * prec TOPO_FP64: H with FP64 applies and contraction.
+ * prec FP32 forms: H from FP32 applies and contraction, then yhat is refined with FP64
+ * reduced residuals b - Phi^T K(rho) Phi yhat (at most TOPO_PARAM_ROM_REFINE steps).
+ * A non-positive pivot sets TOPO_ERR_NOT_SPD in the device status and yhat = NaN. */
+topo_status topo_rom_solve(topo_ctx* ctx, const double* rho, const double* Phi, int k, int ld,
+                           const double* b, double* H_work, double* yhat, double* Jk,
+                           topo_prec prec);
+
+/* A posteriori residual (Section 3.3; the trust-region constraint of Eq. trcon-topopt):
+ * u_k = Phi yhat, r = f - K(rho) u_k on the free DOFs, resnorm[0] = ||r||_2,
+ * resnorm[1] = ||r||_2 / ||f||_2 (device FP64[2]). uk_opt (FP64[N], may be NULL) receives
+ * u_k. Always FP64. */
+topo_status topo_rom_error(topo_ctx* ctx, const double* rho, const double* Phi, int k, int ld,
+                           const double* yhat, const double* f, double* resnorm, double* uk_opt);
+
+/* Compliance and its gradient (Section 2.3 and Eq. pap_sensitivity with lambda = u,
+ * Remark topopt_compl): J = sum_c f_c^T u_c (device scalar), ce_e = sum_c u_{c,e}^T K_e
+ * u_{c,e}, dc_rho_e = -p (E0 - Emin) rho_e^(p-1) ce_e (FP64[N_e]), and, if dc_psi is non-NULL,
+ * dc_psi = filter adjoint of dc_rho (FP64[N_e]). U, F: FP64 N x m, ld. Works for HDM states
+ * and ROM reconstructions alike. */
+topo_status topo_compliance_grad(topo_ctx* ctx, const double* rho, const double* U, int m, int ld,
+                                 const double* F, double* J, double* dc_rho, double* dc_psi);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TOPO_H */

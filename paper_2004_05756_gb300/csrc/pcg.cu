@@ -1,0 +1,563 @@
+// State solve K(rho) u = f (Section 2.1, Eq. linelastsoln) by Jacobi-preconditioned CG in
+// ONE persistent cooperative launch.
+//
+// The paper factorises an assembled sparse K with a direct solver (Section 2.5, step 5);
+// here K is never assembled: every CG iteration applies K(rho) matrix-free, and the whole
+// iteration (operator, dot products, vector updates, convergence test) stays on the GPU.
+// CTAs own node tiles; each iteration has two grid-wide barriers, each folding in a
+// fixed-order reduction of the per-CTA partial dot products (deterministic results).
+//
+// Two forms:
+//   TI = double : plain FP64 PCG (x is the caller's U).
+//   TI = float  : FP32 inner PCG on the correction equation K d = r, wrapped in FP64
+//                 iterative refinement u <- u + d with FP64 residuals r = f - K(rho) u
+//                 computed inside the same launch. The fixed point is the FP64 solution.
+#include <algorithm>
+#include <type_traits>
+
+#include "common.cuh"
+
+namespace topo {
+
+constexpr int PCG_MAX_COLS = 32;
+
+template <int DIM, typename TI>
+struct PcgArgs {
+  Grid g;
+  typename KeOf<DIM, TI>::type ke;
+  typename KeOf<DIM, double>::type ke64;  // refinement residual operator (TI = float)
+  const double* rho;
+  const double* F;
+  long long ldF;
+  double* U;
+  long long ldU;
+  int m;
+  long long N;  // scratch leading dimension
+  TI* E;
+  double* E64;
+  TI* dinv;
+  TI* x;
+  TI* r;
+  TI* z;
+  TI* p0;
+  TI* p1;
+  TI* q;
+  double* partial;
+  double* result;
+  GridSync* gs;
+  double rtol, inner_rtol;
+  int maxit, max_outer;
+  long long wait_cycles;
+  int* info;        // [0] iters, [1] outer, [2] status
+  double* info_rr;  // [0] max_c ||r||^2/||f||^2
+};
+
+template <typename T>
+__device__ __forceinline__ T ldcg(const T* p) {
+  return __ldcg(p);
+}
+
+// Jacobi diagonal of the owned node: sum over adjacent elements of E_e K_e[d, d] at the
+// node's local DOF d.
+template <int DIM, typename T>
+__device__ __forceinline__ void node_diag(const TileSmem<DIM, T>& s, int tx, int ty, int tz,
+                                          const typename KeOf<DIM, T>::type& ke, T* dg) {
+  using TS = TileSmem<DIM, T>;
+  constexpr int ND = DIM == 2 ? 8 : 24;
+#pragma unroll
+  for (int c = 0; c < DIM; ++c) dg[c] = (T)0;
+#pragma unroll
+  for (int cz = 0; cz < (DIM == 3 ? 2 : 1); ++cz)
+#pragma unroll
+    for (int b = 0; b < 2; ++b)
+#pragma unroll
+      for (int a = 0; a < 2; ++a) {
+        const int L = DIM == 2 ? lidx2(1 - a, 1 - b) : lidx3(1 - a, 1 - b, 1 - cz);
+        const T e = s.E[((tz + cz) * TS::EY + (ty + b)) * TS::EX + (tx + a)];
+#pragma unroll
+        for (int c = 0; c < DIM; ++c) dg[c] = fma(e, ke.k[(DIM * L + c) * ND + DIM * L + c], dg[c]);
+      }
+}
+
+template <int DIM, typename TI>
+__global__ void __launch_bounds__(TileShape<DIM>::NT) pcg_kernel(const __grid_constant__ PcgArgs<DIM, TI> a) {
+  constexpr bool REFINED = !std::is_same<TI, double>::value;
+  __shared__ TileSmem<DIM, TI> s;
+  // FP64 tile for the refinement residual (refined form only)
+  __shared__ typename std::conditional<REFINED, TileSmem<DIM, double>, char>::type s64_storage;
+  __shared__ double red[32];
+  __shared__ double sh_rz[PCG_MAX_COLS], sh_alpha[PCG_MAX_COLS], sh_beta[PCG_MAX_COLS], sh_tol2[PCG_MAX_COLS],
+      sh_ff[PCG_MAX_COLS], sh_rr[PCG_MAX_COLS];
+  __shared__ int sh_done[PCG_MAX_COLS], sh_odone[PCG_MAX_COLS];
+
+  const Grid& g = a.g;
+  const int m = a.m;
+  const unsigned int G = gridDim.x;
+  const long long ntiles = num_tiles<DIM>(g);
+  const long long N = a.N;
+  GridSync* gs = a.gs;
+  unsigned int my_gen = *(volatile unsigned int*)&gs->gen;
+  double* part = a.partial;
+  auto P = [&](int slot, int c) -> double* { return part + ((size_t)(slot * m + c)) * G + blockIdx.x; };
+  auto R = [&](int slot, int c) -> double { return __ldcg(a.result + slot * m + c); };
+
+  int iters = 0, outer = 0;
+  bool ok = true;
+
+  // --- P0: element moduli ------------------------------------------------------------
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < g.nel; e += (long long)G * blockDim.x) {
+    const double rv = a.rho[e];
+    a.E[e] = young<TI>((TI)rv, (TI)g.E0, (TI)g.Emin, g.ipenal);
+    if constexpr (REFINED) a.E64[e] = young<double>(rv, g.E0, g.Emin, g.ipenal);
+  }
+  ok = grid_sync_reduce(gs, my_gen, part, a.result, 0, a.wait_cycles);
+  if (!ok) return;
+
+  auto stageE = [&](TileCoord tc) { stage_E<DIM, TI>(s, g, tc, [&](long long e) { return ldcg(a.E + e); }); };
+
+  // --- P1: Jacobi diagonal (owned nodes; read back only by the owner thread) -----------
+  for (long long t = blockIdx.x; t < ntiles; t += G) {
+    const TileCoord tc = tile_coord<DIM>(g, t);
+    stageE(tc);
+    __syncthreads();
+    int tx, ty, tz;
+    long long n;
+    if (owned_node<DIM>(g, tc, tx, ty, tz, n)) {
+      TI dg[DIM];
+      node_diag<DIM, TI>(s, tx, ty, tz, a.ke, dg);
+#pragma unroll
+      for (int c = 0; c < DIM; ++c) {
+        const long long dof = DIM * n + c;
+        a.dinv[dof] = is_fixed(g, dof) ? (TI)0 : (TI)1 / dg[c];
+      }
+    }
+    __syncthreads();
+  }
+
+  // --- inner PCG on (x, r, z) starting from the state prepared by the caller phase -------
+  // Expects sh_rz, sh_tol2, sh_done set; returns false on device error.
+  auto inner_pcg = [&](double* xu, long long ldx, int iter_cap) -> bool {
+    int it = 0;
+    while (true) {
+      bool all = true;
+      for (int c = 0; c < m; ++c) all = all && sh_done[c];
+      if (all || it >= iter_cap) break;
+      TI* pold = (it & 1) ? a.p0 : a.p1;
+      TI* pnew = (it & 1) ? a.p1 : a.p0;
+      // Phase A: p = z + beta p_old (staged with halo), q = K p, partial p.q
+      double pq_acc[PCG_MAX_COLS];
+      for (int c = 0; c < m; ++c) pq_acc[c] = 0.0;
+      for (long long t = blockIdx.x; t < ntiles; t += G) {
+        const TileCoord tc = tile_coord<DIM>(g, t);
+        stageE(tc);
+        int tx, ty, tz;
+        long long n = 0;
+        const bool own = owned_node<DIM>(g, tc, tx, ty, tz, n);
+        for (int c = 0; c < m; ++c) {
+          if (sh_done[c]) continue;
+          const TI* zc = a.z + c * N;
+          const TI* pc = pold + c * N;
+          const TI beta = (TI)sh_beta[c];
+          if (it == 0)
+            stage_V<DIM, TI>(s, g, tc, [&](long long dof) { return ldcg(zc + dof); });
+          else
+            stage_V<DIM, TI>(s, g, tc, [&](long long dof) { return fma(beta, ldcg(pc + dof), ldcg(zc + dof)); });
+          __syncthreads();
+          if (own) {
+            TI out[DIM];
+            node_apply<DIM, TI>(s, tx, ty, tz, a.ke, out);
+            using TS = TileSmem<DIM, TI>;
+            const int h = ((tz + 1) * TS::HY + (ty + 1)) * TS::HX + (tx + 1);
+#pragma unroll
+            for (int cc = 0; cc < DIM; ++cc) {
+              const long long dof = DIM * n + cc;
+              const TI pv = s.v[DIM * h + cc];  // 0 on Dirichlet DOFs
+              const TI qv = is_fixed(g, dof) ? (TI)0 : out[cc];
+              pnew[c * N + dof] = pv;
+              a.q[c * N + dof] = qv;
+              pq_acc[c] = fma((double)pv, (double)qv, pq_acc[c]);
+            }
+          }
+          __syncthreads();
+        }
+      }
+      for (int c = 0; c < m; ++c) {
+        double t = block_sum(pq_acc[c], red);
+        if (threadIdx.x == 0) *P(0, c) = t;
+      }
+      if (!grid_sync_reduce(gs, my_gen, part, a.result, m, a.wait_cycles)) return false;
+      if (threadIdx.x == 0) {
+        for (int c = 0; c < m; ++c) {
+          if (sh_done[c]) continue;
+          const double pq = R(0, c);
+          if (!(pq > 0.0)) {
+            // breakdown: K not SPD on this column (or a NaN)
+            set_status(&gs->status, TOPO_ERR_NOT_SPD);
+            sh_alpha[c] = 0.0;
+            sh_done[c] = 1;
+          } else {
+            sh_alpha[c] = sh_rz[c] / pq;
+          }
+        }
+      }
+      __syncthreads();
+      // Phase B: x += alpha p, r -= alpha q, z = D^-1 r, partial r.z and r.r
+      double rz_acc[PCG_MAX_COLS], rr_acc[PCG_MAX_COLS];
+      for (int c = 0; c < m; ++c) rz_acc[c] = rr_acc[c] = 0.0;
+      for (long long t = blockIdx.x; t < ntiles; t += G) {
+        const TileCoord tc = tile_coord<DIM>(g, t);
+        int tx, ty, tz;
+        long long n = 0;
+        if (!owned_node<DIM>(g, tc, tx, ty, tz, n)) continue;
+        for (int c = 0; c < m; ++c) {
+          if (sh_done[c]) continue;
+          const TI al = (TI)sh_alpha[c];
+#pragma unroll
+          for (int cc = 0; cc < DIM; ++cc) {
+            const long long dof = DIM * n + cc;
+            const long long o = c * N + dof;
+            const TI pv = pnew[o];
+            const TI rv = a.r[o] - al * a.q[o];
+            const TI zv = a.dinv[dof] * rv;
+            if constexpr (REFINED)
+              a.x[o] = a.x[o] + al * pv;
+            else
+              xu[c * ldx + dof] = xu[c * ldx + dof] + (double)al * (double)pv;
+            a.r[o] = rv;
+            a.z[o] = zv;
+            rz_acc[c] = fma((double)rv, (double)zv, rz_acc[c]);
+            rr_acc[c] = fma((double)rv, (double)rv, rr_acc[c]);
+          }
+        }
+      }
+      for (int c = 0; c < m; ++c) {
+        double t1 = block_sum(rz_acc[c], red);
+        double t2 = block_sum(rr_acc[c], red);
+        if (threadIdx.x == 0) {
+          *P(0, c) = t1;
+          *P(1, c) = t2;
+        }
+      }
+      if (!grid_sync_reduce(gs, my_gen, part, a.result, 2 * m, a.wait_cycles)) return false;
+      if (threadIdx.x == 0) {
+        for (int c = 0; c < m; ++c) {
+          if (sh_done[c]) continue;
+          const double rzn = R(0, c), rr = R(1, c);
+          sh_beta[c] = rzn / sh_rz[c];
+          sh_rz[c] = rzn;
+          sh_rr[c] = rr;
+          if (rr <= sh_tol2[c]) sh_done[c] = 1;
+        }
+      }
+      __syncthreads();
+      ++it;
+    }
+    iters += it;
+    return true;
+  };
+
+  if constexpr (!REFINED) {
+    // --- P2: r = f - K x0, z = D^-1 r (x0 = caller's U, Dirichlet entries zeroed) ---------
+    double acc[3][PCG_MAX_COLS];
+    for (int c = 0; c < m; ++c) acc[0][c] = acc[1][c] = acc[2][c] = 0.0;
+    for (long long t = blockIdx.x; t < ntiles; t += G) {
+      const TileCoord tc = tile_coord<DIM>(g, t);
+      stageE(tc);
+      int tx, ty, tz;
+      long long n = 0;
+      const bool own = owned_node<DIM>(g, tc, tx, ty, tz, n);
+      for (int c = 0; c < m; ++c) {
+        double* uc = a.U + c * a.ldU;
+        const double* fc = a.F + c * a.ldF;
+        stage_V<DIM, TI>(s, g, tc, [&](long long dof) { return (TI)ldcg(uc + dof); });
+        __syncthreads();
+        if (own) {
+          TI out[DIM];
+          node_apply<DIM, TI>(s, tx, ty, tz, a.ke, out);
+#pragma unroll
+          for (int cc = 0; cc < DIM; ++cc) {
+            const long long dof = DIM * n + cc;
+            const long long o = c * N + dof;
+            if (is_fixed(g, dof)) {
+              uc[dof] = 0.0;
+              a.r[o] = (TI)0;
+              a.z[o] = (TI)0;
+            } else {
+              const double fv = fc[dof];
+              const TI rv = (TI)fv - out[cc];
+              const TI zv = a.dinv[dof] * rv;
+              a.r[o] = rv;
+              a.z[o] = zv;
+              acc[0][c] = fma((double)rv, (double)zv, acc[0][c]);
+              acc[1][c] = fma((double)rv, (double)rv, acc[1][c]);
+              acc[2][c] = fma(fv, fv, acc[2][c]);
+            }
+          }
+        }
+        __syncthreads();
+      }
+    }
+    for (int c = 0; c < m; ++c)
+      for (int k = 0; k < 3; ++k) {
+        double t = block_sum(acc[k][c], red);
+        if (threadIdx.x == 0) *P(k, c) = t;
+      }
+    if (!grid_sync_reduce(gs, my_gen, part, a.result, 3 * m, a.wait_cycles)) return;
+    if (threadIdx.x == 0) {
+      for (int c = 0; c < m; ++c) {
+        sh_rz[c] = R(0, c);
+        sh_rr[c] = R(1, c);
+        sh_ff[c] = R(2, c);
+        sh_tol2[c] = a.rtol * a.rtol * sh_ff[c];
+        sh_beta[c] = 0.0;
+        sh_done[c] = sh_rr[c] <= sh_tol2[c];
+      }
+    }
+    __syncthreads();
+    ok = inner_pcg(a.U, a.ldU, a.maxit);
+    if (!ok) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      double worst = 0.0;
+      bool conv = true;
+      for (int c = 0; c < m; ++c) {
+        const double q = sh_ff[c] > 0 ? sh_rr[c] / sh_ff[c] : 0.0;
+        worst = fmax(worst, q);
+        conv = conv && (sh_rr[c] <= sh_tol2[c]);
+      }
+      a.info[0] = iters;
+      a.info[1] = 0;
+      a.info[2] = conv ? 0 : TOPO_ERR_NOT_CONVERGED;
+      a.info_rr[0] = worst;
+    }
+    return;
+  } else {
+  // ======================= refined form (TI = float) ==================================
+  TileSmem<DIM, double>& s64 = s64_storage;
+  double worst = 0.0;
+  bool conv = false;
+  for (outer = 0;; ++outer) {
+    // Phase R: r64 = f - K64 u (FP64), r = (float) r64, x = 0, z = D^-1 r
+    double acc[3][PCG_MAX_COLS];
+    for (int c = 0; c < m; ++c) acc[0][c] = acc[1][c] = acc[2][c] = 0.0;
+    for (long long t = blockIdx.x; t < ntiles; t += G) {
+      const TileCoord tc = tile_coord<DIM>(g, t);
+      stage_E<DIM, double>(s64, g, tc, [&](long long e) { return ldcg(a.E64 + e); });
+      int tx, ty, tz;
+      long long n = 0;
+      const bool own = owned_node<DIM>(g, tc, tx, ty, tz, n);
+      for (int c = 0; c < m; ++c) {
+        if (outer > 0 && sh_odone[c]) continue;
+        double* uc = a.U + c * a.ldU;
+        const double* fc = a.F + c * a.ldF;
+        stage_V<DIM, double>(s64, g, tc, [&](long long dof) { return ldcg(uc + dof); });
+        __syncthreads();
+        if (own) {
+          double out[DIM];
+          node_apply<DIM, double>(s64, tx, ty, tz, a.ke64, out);
+#pragma unroll
+          for (int cc = 0; cc < DIM; ++cc) {
+            const long long dof = DIM * n + cc;
+            const long long o = c * N + dof;
+            a.x[o] = (TI)0;
+            if (is_fixed(g, dof)) {
+              if (outer == 0) uc[dof] = 0.0;
+              a.r[o] = (TI)0;
+              a.z[o] = (TI)0;
+            } else {
+              const double fv = fc[dof];
+              const double r64 = fv - out[cc];
+              const TI rv = (TI)r64;
+              const TI zv = a.dinv[dof] * rv;
+              a.r[o] = rv;
+              a.z[o] = zv;
+              acc[0][c] = fma((double)rv, (double)zv, acc[0][c]);
+              acc[1][c] = fma(r64, r64, acc[1][c]);
+              acc[2][c] = fma(fv, fv, acc[2][c]);
+            }
+          }
+        }
+        __syncthreads();
+      }
+    }
+    for (int c = 0; c < m; ++c)
+      for (int k = 0; k < 3; ++k) {
+        double t = block_sum(acc[k][c], red);
+        if (threadIdx.x == 0) *P(k, c) = t;
+      }
+    if (!grid_sync_reduce(gs, my_gen, part, a.result, 3 * m, a.wait_cycles)) return;
+    if (threadIdx.x == 0) {
+      for (int c = 0; c < m; ++c) {
+        if (outer > 0 && sh_odone[c]) continue;
+        const double rz = R(0, c), rr = R(1, c), ff = R(2, c);
+        if (outer == 0) sh_ff[c] = ff;
+        sh_rr[c] = rr;
+        sh_odone[c] = rr <= a.rtol * a.rtol * sh_ff[c];
+        sh_rz[c] = rz;
+        sh_tol2[c] = a.inner_rtol * a.inner_rtol * rr;
+        sh_beta[c] = 0.0;
+        sh_done[c] = sh_odone[c];
+      }
+    }
+    __syncthreads();
+    worst = 0.0;
+    conv = true;
+    for (int c = 0; c < m; ++c) {
+      worst = fmax(worst, sh_ff[c] > 0 ? sh_rr[c] / sh_ff[c] : 0.0);
+      conv = conv && sh_odone[c];
+    }
+    if (conv || outer >= a.max_outer || iters >= a.maxit) break;
+    // inner FP32 PCG on K d = r
+    if (!inner_pcg(nullptr, 0, a.maxit - iters)) return;
+    // Phase U: u += d on free DOFs
+    for (long long t = blockIdx.x; t < ntiles; t += G) {
+      const TileCoord tc = tile_coord<DIM>(g, t);
+      int tx, ty, tz;
+      long long n = 0;
+      if (!owned_node<DIM>(g, tc, tx, ty, tz, n)) continue;
+      for (int c = 0; c < m; ++c) {
+        if (sh_odone[c]) continue;
+#pragma unroll
+        for (int cc = 0; cc < DIM; ++cc) {
+          const long long dof = DIM * n + cc;
+          if (!is_fixed(g, dof)) a.U[c * a.ldU + dof] += (double)a.x[c * N + dof];
+        }
+      }
+    }
+    if (!grid_sync_reduce(gs, my_gen, part, a.result, 0, a.wait_cycles)) return;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    a.info[0] = iters;
+    a.info[1] = outer;
+    a.info[2] = conv ? 0 : TOPO_ERR_NOT_CONVERGED;
+    a.info_rr[0] = worst;
+  }
+  }
+}
+
+template <int DIM, typename TI>
+static topo_status solve_impl(topo_ctx* c, const double* rho, const double* F, double* U, int m, int ld,
+                              double rtol, int maxit, const typename KeOf<DIM, TI>::type& ke,
+                              topo_solve_info* info_host) {
+  constexpr bool REFINED = !std::is_same<TI, double>::value;
+  const Grid& g = c->g;
+  const long long N = g.ndof;
+  const long long ntiles = num_tiles<DIM>(g);
+  // grid: all CTAs co-resident (cooperative launch)
+  int occ = 0;
+  TOPO_CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pcg_kernel<DIM, TI>, TileShape<DIM>::NT, 0));
+  if (occ < 1) return fail(c, TOPO_ERR_CUDA, "pcg kernel cannot be resident");
+  int per_sm = c->pcg_blocks_per_sm > 0 ? std::min(c->pcg_blocks_per_sm, occ) : occ;
+  long long G = (long long)per_sm * c->num_sms;
+  if (G > ntiles) G = ntiles;
+  // scratch layout
+  size_t szT = sizeof(TI);
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off += (bytes + 255) & ~(size_t)255;
+    return o;
+  };
+  size_t oE = take(g.nel * szT), oE64 = take(REFINED ? g.nel * 8 : 0), oD = take(N * szT);
+  size_t ox = take(REFINED ? N * m * szT : 0), orr = take(N * m * szT), oz = take(N * m * szT),
+         op0 = take(N * m * szT), op1 = take(N * m * szT), oq = take(N * m * szT);
+  size_t opart = take(sizeof(double) * 3 * m * G), ores = take(sizeof(double) * 3 * m),
+         oinfo = take(sizeof(int) * 4 + sizeof(double) * 2);
+  topo_status st = ensure_scratch(c, off);
+  if (st) return st;
+  char* base = (char*)c->d_scratch;
+  PcgArgs<DIM, TI> a;
+  a.g = g;
+  a.ke = ke;
+  if (DIM == 2)
+    memcpy(&a.ke64, &c->q4_64, sizeof(a.ke64));
+  else
+    memcpy(&a.ke64, &c->h8_64, sizeof(a.ke64));
+  a.rho = rho;
+  a.F = F;
+  a.ldF = ld;
+  a.U = U;
+  a.ldU = ld;
+  a.m = m;
+  a.N = N;
+  a.E = (TI*)(base + oE);
+  a.E64 = (double*)(base + oE64);
+  a.dinv = (TI*)(base + oD);
+  a.x = (TI*)(base + ox);
+  a.r = (TI*)(base + orr);
+  a.z = (TI*)(base + oz);
+  a.p0 = (TI*)(base + op0);
+  a.p1 = (TI*)(base + op1);
+  a.q = (TI*)(base + oq);
+  a.partial = (double*)(base + opart);
+  a.result = (double*)(base + ores);
+  a.info = (int*)(base + oinfo);
+  a.info_rr = (double*)(base + oinfo + 16);
+  a.gs = c->d_sync;
+  a.rtol = rtol;
+  a.inner_rtol = c->inner_rtol;
+  a.maxit = maxit;
+  a.max_outer = c->max_outer;
+  a.wait_cycles = c->wait_cycles;
+  // barrier arrival counter must start at zero (a previous aborted launch may have left it)
+  TOPO_CUDA_TRY(c, cudaMemsetAsync(c->d_sync, 0, 2 * sizeof(unsigned int), c->stream));  // count, abort
+  TOPO_CUDA_TRY(c, cudaMemsetAsync(a.info, 0, 16, c->stream));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)G);
+  cfg.blockDim = dim3(TileShape<DIM>::NT);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = c->stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  TOPO_CUDA_TRY(c, cudaLaunchKernelEx(&cfg, pcg_kernel<DIM, TI>, a));
+  if (info_host) {
+    int hinfo[4];
+    double hrr[2];
+    TOPO_CUDA_TRY(c, cudaMemcpyAsync(hinfo, a.info, 16, cudaMemcpyDeviceToHost, c->stream));
+    TOPO_CUDA_TRY(c, cudaMemcpyAsync(hrr, a.info_rr, 16, cudaMemcpyDeviceToHost, c->stream));
+    TOPO_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    int dev_status = 0;
+    TOPO_CUDA_TRY(c, cudaMemcpy(&dev_status, &c->d_sync->status, sizeof(int), cudaMemcpyDeviceToHost));
+    info_host->iters = hinfo[0];
+    info_host->outer = hinfo[1];
+    info_host->relres = sqrt(hrr[0]);
+    info_host->status = dev_status ? dev_status : hinfo[2];
+    if (dev_status) {
+      int zero = 0;
+      cudaMemcpy(&c->d_sync->status, &zero, sizeof(int), cudaMemcpyHostToDevice);
+      return fail(c, (topo_status)dev_status, "topo_solve_hdm: device status %d", dev_status);
+    }
+    if (hinfo[2]) return fail(c, TOPO_ERR_NOT_CONVERGED, "topo_solve_hdm: relres %.3e after %d iterations",
+                              info_host->relres, hinfo[0]);
+  }
+  return TOPO_OK;
+}
+
+}  // namespace topo
+
+using namespace topo;
+
+extern "C" topo_status topo_solve_hdm(topo_ctx* c, const double* rho, const double* F, double* U, int m, int ld,
+                                      double rtol, int maxit, topo_prec prec, topo_solve_info* info_host) {
+  if (!c) return TOPO_ERR_INVALID;
+  if (m < 1 || m > PCG_MAX_COLS) return fail(c, TOPO_ERR_INVALID, "topo_solve_hdm: 1 <= m <= %d", PCG_MAX_COLS);
+  if ((long long)ld < c->g.ndof) return fail(c, TOPO_ERR_INVALID, "topo_solve_hdm: ld < N");
+  if (!(rtol > 0.0) || maxit < 0) return fail(c, TOPO_ERR_INVALID, "topo_solve_hdm: rtol > 0, maxit >= 0");
+  if (!dev_ptr_ok(rho) || !dev_ptr_ok(F) || !dev_ptr_ok(U) || F == U)
+    return fail(c, TOPO_ERR_INVALID, "topo_solve_hdm: null, misaligned or aliased pointer");
+  if (info_host) memset(info_host, 0, sizeof(*info_host));
+  if (c->g.dim == 2) {
+    if (prec == TOPO_FP64) return solve_impl<2, double>(c, rho, F, U, m, ld, rtol, maxit, c->q4_64, info_host);
+    if (prec == TOPO_FP32_REFINED) return solve_impl<2, float>(c, rho, F, U, m, ld, rtol, maxit, c->q4_32, info_host);
+    if (prec == TOPO_FP32_BF16KE_REFINED)
+      return solve_impl<2, float>(c, rho, F, U, m, ld, rtol, maxit, c->q4_bf, info_host);
+  } else {
+    if (prec == TOPO_FP64) return solve_impl<3, double>(c, rho, F, U, m, ld, rtol, maxit, c->h8_64, info_host);
+    if (prec == TOPO_FP32_REFINED) return solve_impl<3, float>(c, rho, F, U, m, ld, rtol, maxit, c->h8_32, info_host);
+    if (prec == TOPO_FP32_BF16KE_REFINED)
+      return solve_impl<3, float>(c, rho, F, U, m, ld, rtol, maxit, c->h8_bf, info_host);
+  }
+  return fail(c, TOPO_ERR_INVALID, "topo_solve_hdm: unknown precision");
+}

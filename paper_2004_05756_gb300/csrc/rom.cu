@@ -1,0 +1,488 @@
+// Galerkin reduced-order model on the GPU (Section 3.1, Eq. rom_soln and hatkbm; Section 3.3;
+// the basis of Eq. rob-optim).
+//
+//   basis       classical Gram-Schmidt applied twice per snapshot (FP64), rank rule on the
+//               orthogonalised norm;
+//   projection  H = Phi^T (K(rho) Phi), b = Phi^T f: matrix-free applies of K to the k basis
+//               columns, then a tall-skinny contraction over the N rows with fixed-order
+//               partial sums (deterministic); FP64, or FP32 applies/contraction for the
+//               refined precision forms;
+//   reduced     one-CTA FP64 Cholesky of the k x k matrix and triangular solves; the FP32
+//               forms refine yhat with FP64 reduced residuals b - Phi^T K(rho) Phi yhat;
+//   residual    u_k = Phi yhat, r = f - K(rho) u_k, ||r||_2 and ||r||_2 / ||f||_2 in FP64.
+#include <math.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+
+namespace topo {
+
+// ---------------------------------------------------------------------------------------
+// C = A^T B over N rows (A: N x k1, B: N x k2, column-major, leading dims lda, ldb), written as
+// per-CTA partial sums partial[blockIdx.x][i * k2 + j] (FP64). A CTA owns a contiguous row
+// range and one 64 x 64 output tile (blockIdx.y); each thread accumulates a 4 x 4 block.
+// ---------------------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(256) atb_partial_kernel(const T* __restrict__ A, long long lda, int k1,
+                                                          const T* __restrict__ B, long long ldb, int k2,
+                                                          long long N, long long rows_per_cta, double* partial) {
+  __shared__ T As[32][64 + 1];
+  __shared__ T Bs[32][64 + 1];
+  const int tiles_j = (k2 + 63) / 64;
+  const int ti = blockIdx.y / tiles_j, tj = blockIdx.y % tiles_j;
+  const int i0 = ti * 64, j0 = tj * 64;
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  T acc[4][4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) acc[u][v] = (T)0;
+  const long long r_begin = blockIdx.x * rows_per_cta;
+  const long long r_end = min(N, r_begin + rows_per_cta);
+  for (long long r0 = r_begin; r0 < r_end; r0 += 32) {
+    for (int idx = threadIdx.x; idx < 32 * 64; idx += 256) {
+      const int col = idx / 32, row = idx % 32;
+      const long long r = r0 + row;
+      const bool rin = r < r_end;
+      As[row][col] = (rin && i0 + col < k1) ? A[(long long)(i0 + col) * lda + r] : (T)0;
+      Bs[row][col] = (rin && j0 + col < k2) ? B[(long long)(j0 + col) * ldb + r] : (T)0;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int row = 0; row < 32; ++row) {
+      T av[4], bv[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) av[u] = As[row][ty * 4 + u];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) bv[v] = Bs[row][tx * 4 + v];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = fma(av[u], bv[v], acc[u][v]);
+    }
+    __syncthreads();
+  }
+  double* out = partial + (size_t)blockIdx.x * k1 * k2;
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      const int i = i0 + ty * 4 + u, j = j0 + tx * 4 + v;
+      if (i < k1 && j < k2) out[i * k2 + j] = (double)acc[u][v];
+    }
+}
+
+// Sum the G partial k1 x k2 matrices in CTA order. sym: C = (C + C^T)/2 (k1 == k2).
+__global__ void atb_final_kernel(const double* partial, int G, int k1, int k2, double* C, int sym) {
+  const int KK = k1 * k2;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < KK; e += gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int g = 0; g < G; ++g) s += partial[(size_t)g * KK + e];
+    if (sym) {
+      const int i = e / k2, j = e % k2;
+      double t = 0.0;
+      const int et = j * k2 + i;
+      for (int g = 0; g < G; ++g) t += partial[(size_t)g * KK + et];
+      s = 0.5 * (s + t);
+    }
+    C[e] = s;
+  }
+}
+
+// c = A^T v (A: N x k, v: N), per-CTA partials partial[blockIdx.x * k + j]; warp w handles
+// columns w, w+8, ...; lanes stride the CTA's row range.
+__global__ void atv_partial_kernel(const double* __restrict__ A, long long lda, int k, const double* __restrict__ v,
+                                   long long N, long long rows_per_cta, double* partial) {
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const long long r_begin = blockIdx.x * rows_per_cta;
+  const long long r_end = min(N, r_begin + rows_per_cta);
+  for (int j = w; j < k; j += nw) {
+    const double* a = A + (long long)j * lda;
+    double acc = 0.0;
+    for (long long r = r_begin + l; r < r_end; r += 32) acc = fma(a[r], v[r], acc);
+    acc = warp_sum(acc);
+    if (l == 0) partial[(size_t)blockIdx.x * k + j] = acc;
+  }
+}
+
+// out[j] = (subtract ? base[j] - s : s), s = sum_g partial[g * k + j] (fixed order).
+__global__ void atv_final_kernel(const double* partial, int G, int k, double* out, const double* base) {
+  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < k; j += gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int g = 0; g < G; ++g) s += partial[(size_t)g * k + j];
+    out[j] = base ? base[j] - s : s;
+  }
+}
+
+// y = A c (mode 0), or y -= A c (mode 1); A: N x k, c FP64[k] (device).
+__global__ void gemv_kernel(const double* __restrict__ A, long long lda, int k, const double* __restrict__ cvec,
+                            double* y, long long N, int mode) {
+  extern __shared__ double sc[];
+  for (int j = threadIdx.x; j < k; j += blockDim.x) sc[j] = cvec[j];
+  __syncthreads();
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < N; r += (long long)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int j = 0; j < k; ++j) acc = fma(A[(long long)j * lda + r], sc[j], acc);
+    y[r] = mode ? y[r] - acc : acc;
+  }
+}
+
+// ||x||^2 partials (per CTA) and the final sqrt into *out.
+__global__ void nrm2_partial_kernel(const double* x, long long N, double* partial) {
+  __shared__ double red[32];
+  double acc = 0.0;
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < N; r += (long long)gridDim.x * blockDim.x)
+    acc = fma(x[r], x[r], acc);
+  const double t = block_sum(acc, red);
+  if (threadIdx.x == 0) partial[blockIdx.x] = t;
+}
+__global__ void nrm2_final_kernel(const double* partial, int G, double* out) {
+  __shared__ double red[32];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < G; i += blockDim.x) acc += partial[i];
+  const double t = block_sum(acc, red);
+  if (threadIdx.x == 0) *out = sqrt(t);
+}
+
+__global__ void scale_kernel(double* x, long long N, const double* nrm) {
+  const double s = 1.0 / *nrm;
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < N; r += (long long)gridDim.x * blockDim.x)
+    x[r] *= s;
+}
+
+__global__ void to_float_kernel(const double* __restrict__ A, long long lda, int k, float* B, long long N) {
+  const long long total = N * k;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
+    const long long j = t / N, r = t % N;
+    B[j * N + r] = (float)A[j * lda + r];
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// One-CTA FP64 Cholesky H = L L^T (row-major k x k in global memory, overwritten with L in
+// the lower triangle), then y = H^{-1} b and J = b^T y. A pivot <= 0 (or NaN) sets
+// TOPO_ERR_NOT_SPD and writes NaN to y and J.
+// ---------------------------------------------------------------------------------------
+__global__ void cholesky_kernel(double* H, int k, int* status, int* ok_flag) {
+  extern __shared__ double A[];  // k * k
+  __shared__ int bad;
+  for (int e = threadIdx.x; e < k * k; e += blockDim.x) A[e] = H[e];
+  if (threadIdx.x == 0) bad = 0;
+  __syncthreads();
+  for (int j = 0; j < k; ++j) {
+    if (threadIdx.x == 0) {
+      const double d = A[j * k + j];
+      if (!(d > 0.0)) {
+        bad = 1;
+      } else {
+        A[j * k + j] = sqrt(d);
+      }
+    }
+    __syncthreads();
+    if (bad) break;
+    const double ljj = A[j * k + j];
+    for (int i = j + 1 + threadIdx.x; i < k; i += blockDim.x) A[i * k + j] /= ljj;
+    __syncthreads();
+    const int n = k - j - 1;
+    for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+      const int i = j + 1 + t / n, l = j + 1 + t % n;
+      if (l <= i) A[i * k + l] -= A[i * k + j] * A[l * k + j];
+    }
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < k * k; e += blockDim.x) {
+    const int i = e / k, l = e % k;
+    H[e] = (l <= i) ? A[e] : 0.0;
+  }
+  if (threadIdx.x == 0) {
+    *ok_flag = !bad;
+    if (bad) atomicCAS(status, 0, (int)TOPO_ERR_NOT_SPD);
+  }
+}
+
+// Solve L L^T x = rhs (L lower, row-major). mode 0: y = x; mode 1: y += x. Skipped (y left
+// unchanged) when *skip is non-zero; NaN output when the factorisation failed.
+__global__ void chol_solve_kernel(const double* L, int k, const double* rhs, double* y, int mode, const int* ok_flag,
+                                  const int* skip) {
+  extern __shared__ double sm[];
+  double* Ls = sm;          // k*k
+  double* z = sm + k * k;   // k
+  if (skip && *skip) return;
+  if (!*ok_flag) {
+    for (int i = threadIdx.x; i < k; i += blockDim.x) y[i] = nan("");
+    return;
+  }
+  for (int e = threadIdx.x; e < k * k; e += blockDim.x) Ls[e] = L[e];
+  for (int i = threadIdx.x; i < k; i += blockDim.x) z[i] = rhs[i];
+  __syncthreads();
+  // forward: L z = rhs (column sweep)
+  for (int i = 0; i < k; ++i) {
+    if (threadIdx.x == 0) z[i] /= Ls[i * k + i];
+    __syncthreads();
+    const double zi = z[i];
+    for (int t = i + 1 + threadIdx.x; t < k; t += blockDim.x) z[t] -= Ls[t * k + i] * zi;
+    __syncthreads();
+  }
+  // backward: L^T x = z
+  for (int i = k - 1; i >= 0; --i) {
+    if (threadIdx.x == 0) z[i] /= Ls[i * k + i];
+    __syncthreads();
+    const double xi = z[i];
+    for (int t = threadIdx.x; t < i; t += blockDim.x) z[t] -= Ls[i * k + t] * xi;
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i < k; i += blockDim.x) y[i] = mode ? y[i] + z[i] : z[i];
+}
+
+// J = b^T y (fixed order, one CTA).
+__global__ void dot_small_kernel(const double* b, const double* y, int k, double* J) {
+  __shared__ double red[32];
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < k; i += blockDim.x) acc = fma(b[i], y[i], acc);
+  const double t = block_sum(acc, red);
+  if (threadIdx.x == 0) *J = t;
+}
+
+// Convergence flag of the reduced refinement: skip = ||g|| <= tol * ||b||.
+__global__ void refine_flag_kernel(const double* g, const double* b, int k, double tol, int* skip) {
+  __shared__ double red[32];
+  double a = 0.0, c = 0.0;
+  for (int i = threadIdx.x; i < k; i += blockDim.x) {
+    a = fma(g[i], g[i], a);
+    c = fma(b[i], b[i], c);
+  }
+  const double ta = block_sum(a, red);
+  const double tc = block_sum(c, red);
+  if (threadIdx.x == 0) *skip = (sqrt(ta) <= tol * sqrt(tc)) ? 1 : *skip;
+}
+
+// ---------------------------------------------------------------------------------------
+// Host helpers
+// ---------------------------------------------------------------------------------------
+struct RowSplit {
+  int G;
+  long long rows;
+};
+static RowSplit row_split(topo_ctx* c, long long N, int per_sm) {
+  long long G = (long long)per_sm * c->num_sms;
+  long long rows = (N + G - 1) / G;
+  rows = ((rows + 31) / 32) * 32;
+  if (rows < 32) rows = 32;
+  G = (N + rows - 1) / rows;
+  if (G < 1) G = 1;
+  return {(int)G, rows};
+}
+
+template <typename T>
+static topo_status launch_atb(topo_ctx* c, const T* A, long long lda, int k1, const T* B, long long ldb, int k2,
+                              long long N, double* partial_buf, size_t partial_cap, double* C, int sym) {
+  RowSplit rs = row_split(c, N, 2);
+  size_t need = (size_t)rs.G * k1 * k2;
+  if (need > partial_cap) return fail(c, TOPO_ERR_INVALID, "internal: atb partial buffer too small");
+  const int tiles = ((k1 + 63) / 64) * ((k2 + 63) / 64);
+  atb_partial_kernel<T><<<dim3(rs.G, tiles), 256, 0, c->stream>>>(A, lda, k1, B, ldb, k2, N, rs.rows, partial_buf);
+  atb_final_kernel<<<(k1 * k2 + 255) / 256, 256, 0, c->stream>>>(partial_buf, rs.G, k1, k2, C, sym);
+  TOPO_CUDA_TRY(c, cudaGetLastError());
+  return TOPO_OK;
+}
+
+static topo_status launch_atv(topo_ctx* c, const double* A, long long lda, int k, const double* v, long long N,
+                              double* partial_buf, size_t partial_cap, double* out, const double* base) {
+  RowSplit rs = row_split(c, N, 4);
+  if ((size_t)rs.G * k > partial_cap) return fail(c, TOPO_ERR_INVALID, "internal: atv partial buffer too small");
+  atv_partial_kernel<<<rs.G, 256, 0, c->stream>>>(A, lda, k, v, N, rs.rows, partial_buf);
+  atv_final_kernel<<<1, 128, 0, c->stream>>>(partial_buf, rs.G, k, out, base);
+  TOPO_CUDA_TRY(c, cudaGetLastError());
+  return TOPO_OK;
+}
+
+static int stream_blocks(topo_ctx* c, long long N) {
+  long long b = (N + 255) / 256;
+  long long cap = 8LL * c->num_sms;
+  return (int)std::max(1LL, std::min(b, cap));
+}
+
+static size_t partial_capacity(topo_ctx* c, long long N, int k) {
+  RowSplit a = row_split(c, N, 2), b = row_split(c, N, 4);
+  return std::max((size_t)a.G * k * k, (size_t)b.G * k) + 64;
+}
+
+// Projection H = Phi^T K Phi (and optionally b = Phi^T f) into H (k x k, row-major).
+static topo_status project(topo_ctx* c, const double* rho, const double* Phi, int k, long long ld, topo_prec prec,
+                           double* H, double* b, const double* f, char* scratch) {
+  const long long N = c->g.ndof;
+  size_t pcap = partial_capacity(c, N, k);
+  double* partial = (double*)scratch;
+  char* p = scratch + ((pcap * sizeof(double) + 255) & ~(size_t)255);
+  if (prec == TOPO_FP64) {
+    double* W = (double*)p;
+    topo_status s = launch_apply(c, rho, Phi, W, k, (int)ld, TOPO_FP64);
+    if (s) return s;
+    // W has leading dimension ld (same as Phi)
+    s = launch_atb<double>(c, Phi, ld, k, W, ld, k, N, partial, pcap, H, 1);
+    if (s) return s;
+  } else {
+    float* P32 = (float*)p;
+    float* W32 = P32 + (size_t)N * k;
+    to_float_kernel<<<stream_blocks(c, N * k), 256, 0, c->stream>>>(Phi, ld, k, P32, N);
+    topo_status s = launch_apply(c, rho, P32, W32, k, (int)N, prec);
+    if (s) return s;
+    s = launch_atb<float>(c, P32, N, k, W32, N, k, N, partial, pcap, H, 1);
+    if (s) return s;
+  }
+  if (b) return launch_atv(c, Phi, ld, k, f, N, partial, pcap, b, nullptr);
+  return TOPO_OK;
+}
+
+static size_t project_scratch(topo_ctx* c, int k, long long ld, topo_prec prec) {
+  const long long N = c->g.ndof;
+  size_t pcap = partial_capacity(c, N, k);
+  size_t s = ((pcap * sizeof(double) + 255) & ~(size_t)255);
+  if (prec == TOPO_FP64)
+    s += (size_t)ld * k * sizeof(double);
+  else
+    s += 2 * (size_t)N * k * sizeof(float);
+  return s + 256;
+}
+
+}  // namespace topo
+
+using namespace topo;
+
+extern "C" topo_status topo_rom_build(topo_ctx* c, const double* rho, const double* Usnap, int m, int ld, double* Phi,
+                                      int* k_out, double* H, double* b, const double* f) {
+  if (!c) return TOPO_ERR_INVALID;
+  const long long N = c->g.ndof;
+  if (!k_out) return fail(c, TOPO_ERR_INVALID, "topo_rom_build: k_out is NULL");
+  *k_out = 0;
+  if (m < 1 || m > 128) return fail(c, TOPO_ERR_INVALID, "topo_rom_build: 1 <= m <= 128");
+  if ((long long)ld < N) return fail(c, TOPO_ERR_INVALID, "topo_rom_build: ld < N");
+  if (!dev_ptr_ok(rho) || !dev_ptr_ok(Usnap) || !dev_ptr_ok(Phi) || !dev_ptr_ok(H) || !dev_ptr_ok(b) || !dev_ptr_ok(f))
+    return fail(c, TOPO_ERR_INVALID, "topo_rom_build: null or misaligned pointer");
+  size_t pcap = partial_capacity(c, N, m);
+  size_t need = std::max(project_scratch(c, m, ld, TOPO_FP64), (pcap + 2 * 128 + 64) * sizeof(double));
+  topo_status s = ensure_scratch(c, need);
+  if (s) return s;
+  char* scratch = (char*)c->d_scratch;
+  double* partial = (double*)scratch;
+  double* coef = partial + pcap;       // [128]
+  double* nrm = coef + 128;            // [64]
+  RowSplit rs = row_split(c, N, 4);
+  const int nb = stream_blocks(c, N);
+  // largest snapshot norm
+  std::vector<double> norms(m);
+  for (int j = 0; j < m; ++j) {
+    nrm2_partial_kernel<<<rs.G, 256, 0, c->stream>>>(Usnap + (long long)j * ld, N, partial);
+    nrm2_final_kernel<<<1, 256, 0, c->stream>>>(partial, rs.G, nrm + (j % 64));
+    if (j % 64 == 63 || j == m - 1) {
+      int base = (j / 64) * 64, cnt = j - base + 1;
+      TOPO_CUDA_TRY(c, cudaMemcpyAsync(norms.data() + base, nrm, cnt * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+      TOPO_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    }
+  }
+  double scale = 0.0;
+  for (double v : norms) scale = std::max(scale, v);
+  int k = 0;
+  if (scale > 0.0) {
+    for (int j = 0; j < m; ++j) {
+      double* v = Phi + (long long)k * ld;
+      const double* u = Usnap + (long long)j * ld;
+      if (v != u) TOPO_CUDA_TRY(c, cudaMemcpyAsync(v, u, N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+      for (int pass = 0; pass < 2 && k > 0; ++pass) {
+        s = launch_atv(c, Phi, ld, k, v, N, partial, pcap, coef, nullptr);
+        if (s) return s;
+        gemv_kernel<<<nb, 256, k * sizeof(double), c->stream>>>(Phi, ld, k, coef, v, N, 1);
+      }
+      nrm2_partial_kernel<<<rs.G, 256, 0, c->stream>>>(v, N, partial);
+      nrm2_final_kernel<<<1, 256, 0, c->stream>>>(partial, rs.G, nrm);
+      double hn = 0.0;
+      TOPO_CUDA_TRY(c, cudaMemcpyAsync(&hn, nrm, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+      TOPO_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+      if (hn >= 1e-10 * scale) {
+        scale_kernel<<<nb, 256, 0, c->stream>>>(v, N, nrm);
+        ++k;
+      }
+    }
+  }
+  TOPO_CUDA_TRY(c, cudaGetLastError());
+  *k_out = k;
+  if (k == 0) return TOPO_OK;
+  return project(c, rho, Phi, k, ld, TOPO_FP64, H, b, f, scratch);
+}
+
+extern "C" topo_status topo_rom_solve(topo_ctx* c, const double* rho, const double* Phi, int k, int ld,
+                                      const double* b, double* H_work, double* yhat, double* Jk, topo_prec prec) {
+  if (!c) return TOPO_ERR_INVALID;
+  const long long N = c->g.ndof;
+  if (k < 1 || k > 128) return fail(c, TOPO_ERR_INVALID, "topo_rom_solve: 1 <= k <= 128");
+  if ((long long)ld < N) return fail(c, TOPO_ERR_INVALID, "topo_rom_solve: ld < N");
+  if (prec != TOPO_FP64 && prec != TOPO_FP32_REFINED && prec != TOPO_FP32_BF16KE_REFINED)
+    return fail(c, TOPO_ERR_INVALID, "topo_rom_solve: unknown precision");
+  if (!dev_ptr_ok(rho) || !dev_ptr_ok(Phi) || !dev_ptr_ok(b) || !dev_ptr_ok(H_work) || !dev_ptr_ok(yhat) ||
+      !dev_ptr_ok(Jk))
+    return fail(c, TOPO_ERR_INVALID, "topo_rom_solve: null or misaligned pointer");
+  const bool refine = prec != TOPO_FP64 && c->rom_refine > 0;
+  size_t pcap = partial_capacity(c, N, k);
+  size_t extra = refine ? (2 * (size_t)N + 4 * 128 + 64) * sizeof(double) : 256;
+  size_t need = project_scratch(c, k, ld, prec) + extra + 1024;
+  topo_status s = ensure_scratch(c, need);
+  if (s) return s;
+  char* scratch = (char*)c->d_scratch;
+  s = project(c, rho, Phi, k, ld, prec, H_work, nullptr, nullptr, scratch);
+  if (s) return s;
+  // flags live after the projection scratch
+  char* tail = scratch + project_scratch(c, k, ld, prec);
+  int* flags = (int*)tail;  // [0] ok, [1] skip
+  double* tailD = (double*)(tail + 256);
+  TOPO_CUDA_TRY(c, cudaMemsetAsync(flags, 0, 2 * sizeof(int), c->stream));
+  const size_t sm_chol = (size_t)k * k * sizeof(double);
+  const size_t sm_solve = sm_chol + k * sizeof(double);
+  if (sm_solve > 48 * 1024) {
+    TOPO_CUDA_TRY(c, cudaFuncSetAttribute(cholesky_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_solve));
+    TOPO_CUDA_TRY(c, cudaFuncSetAttribute(chol_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_solve));
+  }
+  cholesky_kernel<<<1, 256, sm_chol, c->stream>>>(H_work, k, &c->d_sync->status, flags);
+  chol_solve_kernel<<<1, 128, sm_solve, c->stream>>>(H_work, k, b, yhat, 0, flags, nullptr);
+  if (refine) {
+    double* u = tailD;
+    double* w = u + N;
+    double* g = w + N;  // [k]
+    double* partial = (double*)scratch;  // projection partials are dead now
+    const int nb = stream_blocks(c, N);
+    for (int it = 0; it < c->rom_refine; ++it) {
+      // g = b - Phi^T K (Phi yhat), all FP64
+      gemv_kernel<<<nb, 256, k * sizeof(double), c->stream>>>(Phi, ld, k, yhat, u, N, 0);
+      s = launch_apply(c, rho, u, w, 1, (int)N, TOPO_FP64);
+      if (s) return s;
+      s = launch_atv(c, Phi, ld, k, w, N, partial, pcap, g, b);
+      if (s) return s;
+      refine_flag_kernel<<<1, 128, 0, c->stream>>>(g, b, k, 1e-14, flags + 1);
+      chol_solve_kernel<<<1, 128, sm_solve, c->stream>>>(H_work, k, g, yhat, 1, flags, flags + 1);
+    }
+  }
+  dot_small_kernel<<<1, 128, 0, c->stream>>>(b, yhat, k, Jk);
+  TOPO_CUDA_TRY(c, cudaGetLastError());
+  return TOPO_OK;
+}
+
+extern "C" topo_status topo_rom_error(topo_ctx* c, const double* rho, const double* Phi, int k, int ld,
+                                      const double* yhat, const double* f, double* resnorm, double* uk_opt) {
+  if (!c) return TOPO_ERR_INVALID;
+  const long long N = c->g.ndof;
+  if (k < 1 || k > 128) return fail(c, TOPO_ERR_INVALID, "topo_rom_error: 1 <= k <= 128");
+  if ((long long)ld < N) return fail(c, TOPO_ERR_INVALID, "topo_rom_error: ld < N");
+  if (!dev_ptr_ok(rho) || !dev_ptr_ok(Phi) || !dev_ptr_ok(yhat) || !dev_ptr_ok(f) || !dev_ptr_ok(resnorm) ||
+      (uk_opt && !dev_ptr_ok(uk_opt)))
+    return fail(c, TOPO_ERR_INVALID, "topo_rom_error: null or misaligned pointer");
+  double* uk = uk_opt;
+  if (!uk) {
+    topo_status s = ensure_scratch(c, (size_t)N * sizeof(double) + 256);
+    if (s) return s;
+    uk = (double*)c->d_scratch;
+  }
+  gemv_kernel<<<stream_blocks(c, N), 256, k * sizeof(double), c->stream>>>(Phi, ld, k, yhat, uk, N, 0);
+  TOPO_CUDA_TRY(c, cudaGetLastError());
+  return launch_residual64(c, rho, uk, f, nullptr, resnorm);
+}

@@ -1,0 +1,197 @@
+"""Thin Python binding of libtopo.so (include/topo.h): the same entry points, argument
+marshalling only. Device arrays are torch CUDA tensors (PyTorch owns device memory and
+streams); every step of the computation runs in the library's CUDA kernels.
+
+There is no fallback: if libtopo.so is missing or fails to load, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libtopo.so")
+
+TOPO_OK, TOPO_ERR_INVALID, TOPO_ERR_OOM, TOPO_ERR_NOT_CONVERGED, TOPO_ERR_NOT_SPD, TOPO_ERR_TIMEOUT, TOPO_ERR_CUDA = range(7)
+STATUS_NAMES = {0: "TOPO_OK", 1: "TOPO_ERR_INVALID", 2: "TOPO_ERR_OOM", 3: "TOPO_ERR_NOT_CONVERGED",
+                4: "TOPO_ERR_NOT_SPD", 5: "TOPO_ERR_TIMEOUT", 6: "TOPO_ERR_CUDA"}
+TOPO_FP64, TOPO_FP32_REFINED, TOPO_FP32_BF16KE_REFINED = 0, 1, 2
+PREC = {"fp64": TOPO_FP64, "fp32": TOPO_FP32_REFINED, "fp32_bf16ke": TOPO_FP32_BF16KE_REFINED}
+(TOPO_PARAM_INNER_RTOL, TOPO_PARAM_MAX_OUTER, TOPO_PARAM_WAIT_CYCLES, TOPO_PARAM_ROM_REFINE,
+ TOPO_PARAM_TILE_X, TOPO_PARAM_PCG_BLOCKS_PER_SM) = range(6)
+
+# Every entry point declared in include/topo.h (checked by the tests).
+EXPORTS = ["topo_create", "topo_destroy", "topo_last_error", "topo_set_param", "topo_check", "topo_sizes",
+           "topo_filter", "topo_apply_K", "topo_solve_hdm", "topo_rom_build", "topo_rom_solve",
+           "topo_rom_error", "topo_compliance_grad"]
+
+
+class TopoError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class topo_problem(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("E0", ctypes.c_double), ("Emin", ctypes.c_double), ("nu", ctypes.c_double),
+                ("penal", ctypes.c_double), ("rmin", ctypes.c_double),
+                ("fixed_dof_mask", ctypes.POINTER(ctypes.c_ubyte))]
+
+
+class topo_solve_info(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("outer", ctypes.c_int), ("relres", ctypes.c_double),
+                ("status", ctypes.c_int)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load libtopo.so and declare the C signatures. Raises if the library is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libtopo.so not built ({path}); run paper_2004_05756_gb300.build.build()")
+    L = ctypes.CDLL(path)
+    P, I, D, LL = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_longlong
+    sig = {
+        "topo_create": ([ctypes.POINTER(topo_problem), P, ctypes.POINTER(P)], I),
+        "topo_destroy": ([P], I),
+        "topo_last_error": ([P], ctypes.c_char_p),
+        "topo_set_param": ([P, I, D], I),
+        "topo_check": ([P], I),
+        "topo_sizes": ([P, ctypes.POINTER(LL), ctypes.POINTER(LL), ctypes.POINTER(LL)], I),
+        "topo_filter": ([P, P, P, I], I),
+        "topo_apply_K": ([P, P, P, P, I, I, I], I),
+        "topo_solve_hdm": ([P, P, P, P, I, I, D, I, I, ctypes.POINTER(topo_solve_info)], I),
+        "topo_rom_build": ([P, P, P, I, I, P, ctypes.POINTER(I), P, P, P], I),
+        "topo_rom_solve": ([P, P, P, I, I, P, P, P, P, I], I),
+        "topo_rom_error": ([P, P, P, I, I, P, P, P, P], I),
+        "topo_compliance_grad": ([P, P, P, I, I, P, P, P, P], I),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(L, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = L
+    return L
+
+
+def _ptr(t) -> int | None:
+    """Device address of a CUDA tensor (None passes NULL)."""
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise TypeError("libtopo arrays must be CUDA tensors")
+    return t.data_ptr()
+
+
+def _stream_handle(stream) -> int:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return stream.cuda_stream
+
+
+class Topo:
+    """One libtopo context (one problem on one device and stream). Method names follow the
+    C entry points; each method checks dtypes/shapes and forwards raw pointers."""
+
+    def __init__(self, problem, stream=None):
+        self.lib = load()
+        self.problem = problem
+        mask = np.ascontiguousarray(problem.fixed, dtype=np.uint8)
+        self._mask = mask
+        pr = topo_problem(problem.dim, problem.nx, problem.ny, problem.nz if problem.dim == 3 else 1,
+                          problem.E0, problem.Emin, problem.nu, problem.penal, problem.rmin,
+                          mask.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)))
+        self.stream = stream
+        h = ctypes.c_void_p()
+        st = self.lib.topo_create(ctypes.byref(pr), _stream_handle(stream), ctypes.byref(h))
+        if st != TOPO_OK:
+            raise TopoError(st, "topo_create failed")
+        self.h = h
+        self.N = problem.ndof
+        self.Ne = problem.nel
+
+    # -- plumbing ------------------------------------------------------------------------
+    def _chk(self, st: int, what: str):
+        if st != TOPO_OK:
+            raise TopoError(st, f"{what}: {self.lib.topo_last_error(self.h).decode(errors='replace')}")
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.topo_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def topo_set_param(self, which: int, value: float):
+        self._chk(self.lib.topo_set_param(self.h, which, float(value)), "topo_set_param")
+
+    def topo_check(self):
+        self._chk(self.lib.topo_check(self.h), "topo_check")
+
+    # -- the hot path ---------------------------------------------------------------------
+    def topo_filter(self, x, out, adjoint: bool = False):
+        self._chk(self.lib.topo_filter(self.h, _ptr(x), _ptr(out), int(adjoint)), "topo_filter")
+        return out
+
+    def topo_apply_K(self, rho, V, Y, prec: str = "fp64"):
+        m, ld = _cols(V, self.N)
+        self._chk(self.lib.topo_apply_K(self.h, _ptr(rho), _ptr(V), _ptr(Y), m, ld, PREC[prec]), "topo_apply_K")
+        return Y
+
+    def topo_solve_hdm(self, rho, F, U, rtol: float = 1e-8, maxit: int = 100000, prec: str = "fp64",
+                       info: bool = True):
+        m, ld = _cols(F, self.N)
+        inf = topo_solve_info()
+        st = self.lib.topo_solve_hdm(self.h, _ptr(rho), _ptr(F), _ptr(U), m, ld, float(rtol), int(maxit),
+                                     PREC[prec], ctypes.byref(inf) if info else None)
+        if st not in (TOPO_OK, TOPO_ERR_NOT_CONVERGED):
+            self._chk(st, "topo_solve_hdm")
+        return dict(iters=inf.iters, outer=inf.outer, relres=inf.relres, status=inf.status) if info else None
+
+    def topo_rom_build(self, rho, Usnap, Phi, H, b, f):
+        m, ld = _cols(Usnap, self.N)
+        k = ctypes.c_int(0)
+        self._chk(self.lib.topo_rom_build(self.h, _ptr(rho), _ptr(Usnap), m, ld, _ptr(Phi), ctypes.byref(k),
+                                          _ptr(H), _ptr(b), _ptr(f)), "topo_rom_build")
+        return k.value
+
+    def topo_rom_solve(self, rho, Phi, k: int, b, H_work, yhat, Jk, prec: str = "fp64"):
+        ld = _ld(Phi, self.N)
+        self._chk(self.lib.topo_rom_solve(self.h, _ptr(rho), _ptr(Phi), int(k), ld, _ptr(b), _ptr(H_work),
+                                          _ptr(yhat), _ptr(Jk), PREC[prec]), "topo_rom_solve")
+
+    def topo_rom_error(self, rho, Phi, k: int, yhat, f, resnorm, uk=None):
+        ld = _ld(Phi, self.N)
+        self._chk(self.lib.topo_rom_error(self.h, _ptr(rho), _ptr(Phi), int(k), ld, _ptr(yhat), _ptr(f),
+                                          _ptr(resnorm), _ptr(uk)), "topo_rom_error")
+
+    def topo_compliance_grad(self, rho, U, F, J, dc_rho, dc_psi=None):
+        m, ld = _cols(U, self.N)
+        self._chk(self.lib.topo_compliance_grad(self.h, _ptr(rho), _ptr(U), m, ld, _ptr(F), _ptr(J),
+                                                _ptr(dc_rho), _ptr(dc_psi)), "topo_compliance_grad")
+
+
+def _cols(t, N: int):
+    """Column count and leading dimension of an N x m column-major block stored as a torch
+    tensor of shape (m, ld) (row c = column c) or a 1-D vector of length >= N."""
+    if t.dim() == 1:
+        return 1, int(t.shape[0])
+    if t.stride(1) != 1:
+        raise ValueError("column blocks must be (m, ld) tensors with unit stride along ld")
+    return int(t.shape[0]), int(t.stride(0))
+
+
+def _ld(t, N: int) -> int:
+    return _cols(t, N)[1]

@@ -1,0 +1,295 @@
+"""GPU parity: every libtopo call, through the C ABI, against the FP64 CPU oracle on the
+same seeded inputs. Sizes span several tiles plus ragged tails (tiles are 32x8 nodes in 2D,
+8x8x4 in 3D) and the degenerate one-element meshes.
+
+Tolerances: FP64 paths 1e-12 (max-normalised) for single operator applications, 1e-9
+relative on compliance after solves to rtol 1e-10; reduced-precision forms 1e-6 relative
+compliance error (the stated target); FP32 operator applications 2e-6 max-normalised
+(FP32 rounding of K_e, E and the accumulation of 64 (Q4) / 576 (H8) products); BF16 K_e
+applications 8e-3 (BF16 has an 8-bit significand: entry error <= 2^-9)."""
+import numpy as np
+import pytest
+
+from oracle import fem, hatfilter, pipeline, rom
+from paper_2004_05756_gb300 import workloads as w
+from tests.gpu_util import cols, dev, host_cols, relerr, require_cuda
+
+pytestmark = pytest.mark.gpu
+
+CASES = {
+    "q4_60x20": lambda: w.mbb_2d(60, 20),
+    "q4_37x13": lambda: w.mbb_2d(37, 13),
+    "q4_1x1": lambda: w.mbb_2d(1, 1),
+    "h8_6x5x4": lambda: w.cantilever_3d(6, 5, 4),
+    "h8_11x9x6": lambda: w.cantilever_3d(11, 9, 6),
+    "h8_1x1x1": lambda: w.cantilever_3d(1, 1, 1),
+}
+
+
+@pytest.fixture(scope="module")
+def torch():
+    return require_cuda()
+
+
+def ctx_for(p):
+    from paper_2004_05756_gb300.native import Topo
+    return Topo(p)
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_filter(torch, case):
+    p = CASES[case]()
+    T = ctx_for(p)
+    psi = np.random.default_rng(0).uniform(0, 1, p.nel)
+    out = torch.empty(p.nel, dtype=torch.float64, device="cuda")
+    T.topo_filter(dev(psi), out)
+    assert relerr(out.cpu().numpy(), hatfilter.filter_fwd(p, psi)) < 1e-14
+    v = np.random.default_rng(1).standard_normal(p.nel)
+    T.topo_filter(dev(v), out, adjoint=True)
+    assert relerr(out.cpu().numpy(), hatfilter.filter_adj(p, v)) < 1e-14
+
+
+@pytest.mark.parametrize("case", list(CASES))
+@pytest.mark.parametrize("m", [1, 3])
+def test_apply_fp64(torch, case, m):
+    p = CASES[case]()
+    T = ctx_for(p)
+    rng = np.random.default_rng(2)
+    rho = rng.uniform(1e-3, 1, p.nel)
+    V = rng.standard_normal((p.ndof, m))
+    Y = torch.zeros((m, p.ndof), dtype=torch.float64, device="cuda")
+    T.topo_apply_K(dev(rho), cols(V), Y, "fp64")
+    assert relerr(host_cols(Y), fem.apply_K(p, rho, V)) < 1e-13
+
+
+@pytest.mark.parametrize("case", ["q4_60x20", "q4_37x13", "h8_6x5x4", "h8_11x9x6"])
+@pytest.mark.parametrize("prec,tol", [("fp32", 2e-6), ("fp32_bf16ke", 8e-3)])
+def test_apply_fp32(torch, case, prec, tol):
+    p = CASES[case]()
+    T = ctx_for(p)
+    rng = np.random.default_rng(3)
+    rho = rng.uniform(1e-3, 1, p.nel)
+    V = rng.standard_normal((p.ndof, 2)).astype(np.float32)
+    Y = torch.zeros((2, p.ndof), dtype=torch.float32, device="cuda")
+    T.topo_apply_K(dev(rho), cols(V), Y, prec)
+    assert relerr(host_cols(Y), fem.apply_K(p, rho, V.astype(float))) < tol
+
+
+def test_apply_leading_dimension_and_noop(torch):
+    p = CASES["q4_37x13"]()
+    T = ctx_for(p)
+    rng = np.random.default_rng(4)
+    rho = rng.uniform(0.1, 1, p.nel)
+    ld = p.ndof + 7
+    Vb = torch.zeros((3, ld), dtype=torch.float64, device="cuda")
+    V = rng.standard_normal((p.ndof, 3))
+    Vb[:, :p.ndof] = cols(V)
+    Yb = torch.full((3, ld), 7.0, dtype=torch.float64, device="cuda")
+    T.topo_apply_K(dev(rho), Vb, Yb, "fp64")
+    Y = Yb[:, :p.ndof].cpu().numpy().T
+    assert relerr(Y, fem.apply_K(p, rho, V)) < 1e-13
+    assert np.all(Yb[:, p.ndof:].cpu().numpy() == 7.0)  # padding untouched
+    # m = 0 is a no-op
+    from paper_2004_05756_gb300 import native
+    import ctypes
+    st = native.load().topo_apply_K(T.h, dev(rho).data_ptr(), Vb.data_ptr(), Yb.data_ptr(), 0, ld, 0)
+    assert st == 0
+
+
+def test_invalid_arguments(torch):
+    from paper_2004_05756_gb300 import native
+    p = CASES["q4_60x20"]()
+    T = ctx_for(p)
+    L = native.load()
+    rho = dev(np.full(p.nel, 0.5))
+    V = torch.zeros(p.ndof, dtype=torch.float64, device="cuda")
+    assert L.topo_apply_K(T.h, rho.data_ptr(), V.data_ptr(), V.data_ptr(), 1, p.ndof, 0) == native.TOPO_ERR_INVALID
+    assert L.topo_apply_K(T.h, rho.data_ptr(), V.data_ptr(), V.data_ptr() + 8, 1, p.ndof - 1, 0) == native.TOPO_ERR_INVALID
+    assert L.topo_apply_K(T.h, rho.data_ptr(), V.data_ptr() + 4, V.data_ptr(), 1, p.ndof, 0) == native.TOPO_ERR_INVALID
+    assert L.topo_apply_K(T.h, None, V.data_ptr(), V.data_ptr() + 8, 1, p.ndof, 0) == native.TOPO_ERR_INVALID
+    assert L.topo_rom_solve(T.h, rho.data_ptr(), V.data_ptr(), 0, p.ndof, V.data_ptr(), V.data_ptr(),
+                            V.data_ptr(), V.data_ptr(), 0) == native.TOPO_ERR_INVALID
+    T.topo_check()
+
+
+def _design(p, seed=0):
+    psi = w.design_field(p, seed)
+    return psi, hatfilter.filter_fwd(p, psi)
+
+
+@pytest.mark.parametrize("case", ["q4_60x20", "q4_37x13", "q4_1x1", "h8_6x5x4", "h8_11x9x6", "h8_1x1x1"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "fp32_bf16ke"])
+def test_solve_hdm(torch, case, prec):
+    p = CASES[case]()
+    T = ctx_for(p)
+    psi, rho = _design(p)
+    Uo = fem.solve(p, rho)
+    Jo = fem.compliance(p, Uo)
+    U = torch.zeros((1, p.ndof), dtype=torch.float64, device="cuda")
+    info = T.topo_solve_hdm(dev(rho), cols(p.F), U, rtol=1e-10, maxit=200000, prec=prec)
+    assert info["status"] == 0, info
+    assert info["relres"] <= 1e-10
+    Ug = host_cols(U)
+    Jg = fem.compliance(p, Ug)
+    tol = 1e-9 if prec == "fp64" else 1e-6
+    assert abs(Jg - Jo) <= tol * abs(Jo), (Jg, Jo, info)
+    r = p.F[:, 0] - fem.apply_K(p, rho, Ug[:, 0])
+    r[fem.fixed_dofs(p)] = 0
+    assert np.linalg.norm(r) <= 1e-9 * np.linalg.norm(p.F)
+    if prec != "fp64":
+        assert info["outer"] >= 1
+
+
+def test_solve_multiload_and_warm_start(torch):
+    p = w.mbb_2d_multiload(40, 20, 4, seed=5)
+    T = ctx_for(p)
+    psi, rho = _design(p, 3)
+    Uo = fem.solve(p, rho)
+    U = torch.zeros((4, p.ndof), dtype=torch.float64, device="cuda")
+    info = T.topo_solve_hdm(dev(rho), cols(p.F), U, rtol=1e-10, maxit=100000, prec="fp64")
+    assert info["status"] == 0
+    Ug = host_cols(U)
+    for c in range(4):
+        assert abs(fem.compliance(p, Ug[:, c], p.F[:, c]) - fem.compliance(p, Uo[:, c], p.F[:, c])) <= \
+            1e-9 * abs(fem.compliance(p, Uo[:, c], p.F[:, c]))
+    # a converged warm start needs no iterations
+    info2 = T.topo_solve_hdm(dev(rho), cols(p.F), U, rtol=1e-8, prec="fp64")
+    assert info2["iters"] == 0 and info2["status"] == 0
+
+
+def test_solve_not_converged_reports(torch):
+    p = CASES["q4_60x20"]()
+    T = ctx_for(p)
+    psi, rho = _design(p)
+    U = torch.zeros((1, p.ndof), dtype=torch.float64, device="cuda")
+    info = T.topo_solve_hdm(dev(rho), cols(p.F), U, rtol=1e-10, maxit=5, prec="fp64")
+    assert info["status"] == 3 and info["iters"] == 5
+
+
+@pytest.mark.parametrize("case", ["q4_60x20", "q4_37x13", "h8_6x5x4", "h8_11x9x6"])
+@pytest.mark.parametrize("m", [1, 2])
+def test_compliance_grad(torch, case, m):
+    p = CASES[case]()
+    if m == 2:
+        p.F = np.concatenate([p.F, np.roll(p.F, 2 * p.dim, axis=0) * (1 - p.fixed[:, None])], 1)
+    T = ctx_for(p)
+    psi, rho = _design(p)
+    Uo = fem.solve(p, rho, p.F)
+    Jo = fem.compliance(p, Uo, p.F)
+    dco = fem.compliance_grad_rho(p, rho, Uo)
+    dpo = hatfilter.filter_adj(p, dco)
+    J = torch.zeros(1, dtype=torch.float64, device="cuda")
+    dc = torch.zeros(p.nel, dtype=torch.float64, device="cuda")
+    dp = torch.zeros(p.nel, dtype=torch.float64, device="cuda")
+    T.topo_compliance_grad(dev(rho), cols(Uo), cols(p.F), J, dc, dp)
+    assert abs(J.item() - Jo) <= 1e-13 * abs(Jo)
+    assert relerr(dc.cpu().numpy(), dco) < 1e-12
+    assert relerr(dp.cpu().numpy(), dpo) < 1e-12
+
+
+def _snapshots(p, psi, m):
+    snaps = w.perturbed_designs(p, psi, m)
+    return np.stack([pipeline.hdm_eval(p, snaps[:, i])["U"][:, 0] for i in range(m)], 1)
+
+
+@pytest.mark.parametrize("case,m", [("q4_60x20", 5), ("q4_37x13", 8), ("h8_6x5x4", 5), ("h8_11x9x6", 6)])
+def test_rom_build_solve_error(torch, case, m):
+    p = CASES[case]()
+    T = ctx_for(p)
+    psi, rho = _design(p)
+    U = _snapshots(p, psi, m)
+    f = p.F[:, 0]
+    Phi_o = rom.basis(U)
+    k_o = Phi_o.shape[1]
+    Ud = cols(U)
+    Phi = torch.zeros_like(Ud)
+    H = torch.zeros(m * m, dtype=torch.float64, device="cuda")
+    b = torch.zeros(m, dtype=torch.float64, device="cuda")
+    k = T.topo_rom_build(dev(rho), Ud, Phi, H, b, dev(f))
+    assert k == k_o
+    Pg = host_cols(Phi)[:, :k]
+    assert np.abs(Pg.T @ Pg - np.eye(k)).max() < 1e-12
+    x = np.random.default_rng(7).standard_normal(p.ndof)
+    assert relerr(Pg @ (Pg.T @ x), Phi_o @ (Phi_o.T @ x)) < 1e-10
+    Ho, bo = rom.project(p, rho, Phi_o, f)
+    Hg = H[:k * k].cpu().numpy().reshape(k, k)
+    assert relerr(np.linalg.eigvalsh(Hg), np.linalg.eigvalsh(Ho)) < 1e-10
+    assert relerr(Pg @ b[:k].cpu().numpy(), Phi_o @ bo) < 1e-12
+    # reduced solve and residual at a new design
+    psi2 = w.perturbed_designs(p, psi, 1, first_seed=99)[:, 0]
+    rho2 = hatfilter.filter_fwd(p, psi2)
+    ref = rom.rom_eval(p, rho2, Phi_o, f)
+    for prec, tol in [("fp64", 1e-10), ("fp32", 1e-6), ("fp32_bf16ke", 1e-6)]:
+        Hw = torch.zeros(k * k, dtype=torch.float64, device="cuda")
+        y = torch.zeros(k, dtype=torch.float64, device="cuda")
+        Jk = torch.zeros(1, dtype=torch.float64, device="cuda")
+        T.topo_rom_solve(dev(rho2), Phi[:k], k, b[:k].contiguous(), Hw, y, Jk, prec)
+        T.topo_check()
+        assert abs(Jk.item() - ref["Jk"]) <= tol * abs(ref["Jk"]), (prec, Jk.item(), ref["Jk"])
+        rn = torch.zeros(2, dtype=torch.float64, device="cuda")
+        uk = torch.zeros(p.ndof, dtype=torch.float64, device="cuda")
+        T.topo_rom_error(dev(rho2), Phi[:k], k, y, dev(f), rn, uk)
+        assert relerr(uk.cpu().numpy(), ref["uk"]) < (1e-9 if prec == "fp64" else 1e-5)
+        if prec == "fp64":
+            assert abs(rn[0].item() - ref["resnorm"]) <= 1e-8 * ref["resnorm"] + 1e-12 * np.linalg.norm(f)
+            assert abs(rn[1].item() - ref["relres"]) <= 1e-8 * ref["relres"] + 1e-12
+
+
+def test_rom_exact_reproduction(torch):
+    """Remark rom_exact on the GPU: with u(rho) in the basis, J_k = J and ||r|| ~ 0."""
+    p = CASES["q4_37x13"]()
+    T = ctx_for(p)
+    psi, rho = _design(p)
+    U = _snapshots(p, psi, 3)
+    u = fem.solve(p, rho)[:, 0]
+    Ud = cols(np.concatenate([U, u[:, None]], 1))
+    Phi = torch.zeros_like(Ud)
+    H = torch.zeros(16, dtype=torch.float64, device="cuda")
+    b = torch.zeros(4, dtype=torch.float64, device="cuda")
+    f = dev(p.F[:, 0])
+    k = T.topo_rom_build(dev(rho), Ud, Phi, H, b, f)
+    Hw = torch.zeros(k * k, dtype=torch.float64, device="cuda")
+    y = torch.zeros(k, dtype=torch.float64, device="cuda")
+    Jk = torch.zeros(1, dtype=torch.float64, device="cuda")
+    T.topo_rom_solve(dev(rho), Phi[:k], k, b[:k].contiguous(), Hw, y, Jk, "fp64")
+    J = fem.compliance(p, u)
+    assert abs(Jk.item() - J) <= 1e-10 * J
+    rn = torch.zeros(2, dtype=torch.float64, device="cuda")
+    T.topo_rom_error(dev(rho), Phi[:k], k, y, f, rn)
+    assert rn[1].item() < 1e-9
+
+
+def test_rom_not_spd_sets_status(torch):
+    """A zero basis column makes H singular: the Cholesky reports TOPO_ERR_NOT_SPD."""
+    from paper_2004_05756_gb300.native import TopoError
+    p = CASES["q4_37x13"]()
+    T = ctx_for(p)
+    rho = dev(np.full(p.nel, 0.5))
+    Phi = torch.zeros((2, p.ndof), dtype=torch.float64, device="cuda")
+    Phi[0, 10] = 1.0
+    b = torch.ones(2, dtype=torch.float64, device="cuda")
+    Hw = torch.zeros(4, dtype=torch.float64, device="cuda")
+    y = torch.zeros(2, dtype=torch.float64, device="cuda")
+    Jk = torch.zeros(1, dtype=torch.float64, device="cuda")
+    T.topo_rom_solve(rho, Phi, 2, b, Hw, y, Jk, "fp64")
+    with pytest.raises(TopoError) as ei:
+        T.topo_check()
+    assert ei.value.status == 4
+    assert np.isnan(y.cpu().numpy()).all()
+    T.topo_check()  # cleared
+
+
+def test_full_size_apply_600x200(torch):
+    """Full-size parity at 600x200 (the benchmark's mesh) in the launch configuration the
+    benchmark times: m = 1 and m = 64 columns, FP64 and FP32."""
+    p = w.mbb_600x200()
+    T = ctx_for(p)
+    psi, rho = _design(p)
+    rng = np.random.default_rng(8)
+    for m, prec, tol in [(1, "fp64", 1e-13), (64, "fp64", 1e-13), (64, "fp32", 2e-6)]:
+        V = rng.standard_normal((p.ndof, m))
+        dt = torch.float64 if prec == "fp64" else torch.float32
+        Y = torch.zeros((m, p.ndof), dtype=dt, device="cuda")
+        T.topo_apply_K(dev(rho), cols(V, dt), Y, prec)
+        Vin = V if prec == "fp64" else V.astype(np.float32).astype(float)
+        assert relerr(host_cols(Y), fem.apply_K(p, rho, Vin)) < tol
