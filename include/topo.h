@@ -94,6 +94,10 @@ topo_status topo_set_param(topo_ctx* ctx, topo_param which, double value);
 /* Synchronise the context's stream and return (and clear) the sticky device status. */
 topo_status topo_check(topo_ctx* ctx);
 
+/* Diagnostics: total number of CUDA kernel launches issued by the library in this process,
+ * over all contexts (host output). */
+topo_status topo_launch_count(long long* out);
+
 /* Sizes of the context's problem (host outputs; any may be NULL). */
 topo_status topo_sizes(const topo_ctx* ctx, long long* ndof, long long* nel, long long* nnodes);
 

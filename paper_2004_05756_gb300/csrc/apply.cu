@@ -18,15 +18,18 @@ struct ApplyArgs {
   long long ld;
   int m;
   int cols_per_cta;
+  T escale;         // folded into E(rho): 1, or the BF16 table's scale
+  const int* gate;  // optional device flag: the launch does nothing when *gate == 0
 };
 
 template <int DIM, typename T>
 __global__ void __launch_bounds__(TileShape<DIM>::NT) apply_kernel(const __grid_constant__ ApplyArgs<DIM, T> a) {
   __shared__ TileSmem<DIM, T> s;
+  if (a.gate && *a.gate == 0) return;
   const Grid& g = a.g;
   const TileCoord tc = tile_coord<DIM>(g, blockIdx.x);
-  const T E0 = (T)g.E0, Emin = (T)g.Emin;
-  stage_E<DIM, T>(s, g, tc, [&](long long e) { return young<T>((T)a.rho[e], E0, Emin, g.ipenal); });
+  const T E0 = (T)g.E0, Emin = (T)g.Emin, es = a.escale;
+  stage_E<DIM, T>(s, g, tc, [&](long long e) { return es * young<T>((T)a.rho[e], E0, Emin, g.ipenal); });
   int tx, ty, tz;
   long long n = 0;
   const bool own = owned_node<DIM>(g, tc, tx, ty, tz, n);
@@ -52,8 +55,10 @@ __global__ void __launch_bounds__(TileShape<DIM>::NT) apply_kernel(const __grid_
 
 template <int DIM, typename T>
 static topo_status apply_impl(topo_ctx* c, const double* rho, const T* V, T* Y, int m, int ld,
-                              const typename KeOf<DIM, T>::type& ke) {
+                              const typename KeOf<DIM, T>::type& ke, double escale, const int* gate) {
   ApplyArgs<DIM, T> a;
+  a.escale = (T)escale;
+  a.gate = gate;
   a.g = c->g;
   a.ke = ke;
   a.rho = rho;
@@ -73,20 +78,23 @@ static topo_status apply_impl(topo_ctx* c, const double* rho, const T* V, T* Y, 
   groups = (m + a.cols_per_cta - 1) / a.cols_per_cta;
   dim3 grid((unsigned)tiles, (unsigned)groups);
   apply_kernel<DIM, T><<<grid, TileShape<DIM>::NT, 0, c->stream>>>(a);
+  note_launch();
   TOPO_CUDA_TRY(c, cudaGetLastError());
   return TOPO_OK;
 }
 
-topo_status launch_apply(topo_ctx* c, const double* rho, const void* V, void* Y, int m, int ld, topo_prec prec) {
+topo_status launch_apply(topo_ctx* c, const double* rho, const void* V, void* Y, int m, int ld, topo_prec prec,
+                         const int* gate) {
+  const bool bf = prec == TOPO_FP32_BF16KE_REFINED;
+  const double es = bf ? c->bf_scale : 1.0;
   if (c->g.dim == 2) {
     if (prec == TOPO_FP64)
-      return apply_impl<2, double>(c, rho, (const double*)V, (double*)Y, m, ld, c->q4_64);
-    return apply_impl<2, float>(c, rho, (const float*)V, (float*)Y, m, ld,
-                                prec == TOPO_FP32_BF16KE_REFINED ? c->q4_bf : c->q4_32);
+      return apply_impl<2, double>(c, rho, (const double*)V, (double*)Y, m, ld, c->q4_64, 1.0, gate);
+    return apply_impl<2, float>(c, rho, (const float*)V, (float*)Y, m, ld, bf ? c->q4_bf : c->q4_32, es, gate);
   }
-  if (prec == TOPO_FP64) return apply_impl<3, double>(c, rho, (const double*)V, (double*)Y, m, ld, c->h8_64);
-  return apply_impl<3, float>(c, rho, (const float*)V, (float*)Y, m, ld,
-                              prec == TOPO_FP32_BF16KE_REFINED ? c->h8_bf : c->h8_32);
+  if (prec == TOPO_FP64)
+    return apply_impl<3, double>(c, rho, (const double*)V, (double*)Y, m, ld, c->h8_64, 1.0, gate);
+  return apply_impl<3, float>(c, rho, (const float*)V, (float*)Y, m, ld, bf ? c->h8_bf : c->h8_32, es, gate);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -170,7 +178,9 @@ static topo_status residual_impl(topo_ctx* c, const double* rho, const double* u
   a.r = r;
   a.partial = c->d_red;
   residual_kernel<DIM><<<(unsigned)tiles, TileShape<DIM>::NT, 0, c->stream>>>(a);
+  note_launch();
   residual_final_kernel<<<1, 256, 0, c->stream>>>(c->d_red, (int)tiles, out2);
+  note_launch();
   TOPO_CUDA_TRY(c, cudaGetLastError());
   return TOPO_OK;
 }

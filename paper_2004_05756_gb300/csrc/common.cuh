@@ -18,6 +18,33 @@
 namespace topo {
 
 // ---------------------------------------------------------------------------------------
+// Optional self-checking build (-DTOPO_BOUNDS_CHECK): every checked global access verifies
+// its index against the array length, records the first violation (tag, index, length)
+// and skips the access instead of faulting. Off in normal builds.
+// ---------------------------------------------------------------------------------------
+#ifdef TOPO_BOUNDS_CHECK
+struct BoundsLog {
+  int hit;
+  int tag;
+  long long idx;
+  long long n;
+};
+static __device__ BoundsLog g_bounds_log;  // one per translation unit
+__device__ inline bool bounds_ok(long long idx, long long n, int tag) {
+  if (idx >= 0 && idx < n) return true;
+  if (atomicCAS(&g_bounds_log.hit, 0, 1) == 0) {
+    g_bounds_log.tag = tag;
+    g_bounds_log.idx = idx;
+    g_bounds_log.n = n;
+  }
+  return false;
+}
+#define TOPO_OK_IDX(idx, n, tag) topo::bounds_ok((long long)(idx), (long long)(n), (tag))
+#else
+#define TOPO_OK_IDX(idx, n, tag) true
+#endif
+
+// ---------------------------------------------------------------------------------------
 // Element matrices passed by value as __grid_constant__ kernel parameters, so that the
 // FMAs read K_e straight from the constant bank (no load instructions).
 // ---------------------------------------------------------------------------------------
@@ -131,7 +158,7 @@ __device__ inline void stage_E(TileSmem<DIM, T>& s, const Grid& g, TileCoord c, 
       in = in && ek >= 0 && ek < g.nz;
       e += (long long)g.nx * g.ny * ek;
     }
-    s.E[idx] = in ? getE(e) : (T)0;
+    if (TOPO_OK_IDX(idx, TS::NE, 20)) s.E[idx] = in ? getE(e) : (T)0;
   }
 }
 
@@ -158,9 +185,9 @@ __device__ inline void stage_V(TileSmem<DIM, T>& s, const Grid& g, TileCoord c, 
     T val = (T)0;
     if (in) {
       long long dof = DIM * n + comp;
-      if (!is_fixed(g, dof)) val = getV(dof);
+      if (TOPO_OK_IDX(dof, g.ndof, 23) && !is_fixed(g, dof)) val = getV(dof);
     }
-    s.v[idx] = val;
+    if (TOPO_OK_IDX(idx, TS::NH * DIM, 19)) s.v[idx] = val;
   }
 }
 
@@ -390,6 +417,8 @@ struct topo_ctx {
   topo::KeQ4<float> q4_32, q4_bf;
   topo::KeH8<double> h8_64;
   topo::KeH8<float> h8_32, h8_bf;
+  double bf_scale;  // K_e = bf_scale * (BF16 table); folded into E(rho) by the BF16 form
+  int bf_exact;     // 1 when the BF16 table holds K_e / bf_scale exactly
   // filter stencil (host-computed offsets and weights, device copy)
   int nstencil;
   int* d_stencil_off;     // [nstencil * 3]
@@ -414,13 +443,15 @@ struct topo_ctx {
 namespace topo {
 
 topo_status fail(topo_ctx* c, topo_status s, const char* fmt, ...);
+void note_launch();  // counts kernel launches issued by the library (diagnostics)
 topo_status cuda_fail(topo_ctx* c, cudaError_t e, const char* where);
 topo_status ensure_scratch(topo_ctx* c, size_t bytes);
 topo_status ensure_red(topo_ctx* c, size_t bytes);
 bool dev_ptr_ok(const void* p);
 
 // Launch helpers implemented in apply.cu (used by the ROM code as well).
-topo_status launch_apply(topo_ctx* c, const double* rho, const void* V, void* Y, int m, int ld, topo_prec prec);
+topo_status launch_apply(topo_ctx* c, const double* rho, const void* V, void* Y, int m, int ld, topo_prec prec,
+                         const int* gate = nullptr);
 // Residual r = f - K(rho) u on free DOFs (0 on Dirichlet DOFs), FP64, with ||r||^2 and ||f||^2
 // partials reduced to out2[0..1] (device). r may be NULL (norms only).
 topo_status launch_residual64(topo_ctx* c, const double* rho, const double* u, const double* f, double* r,

@@ -5,11 +5,15 @@
 #include <stdarg.h>
 #include <stdlib.h>
 
+#include <atomic>
 #include <vector>
 
 #include "common.cuh"
 
 namespace topo {
+
+static std::atomic<long long> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
 topo_status fail(topo_ctx* c, topo_status s, const char* fmt, ...) {
   if (c) {
@@ -256,7 +260,9 @@ topo_status launch_sum(topo_ctx* c, const double* x, long long n, double* out) {
   topo_status s = ensure_red(c, sizeof(double) * (size_t)(G + 64));
   if (s) return s;
   dot_partial_kernel<<<G, 256, 0, c->stream>>>(x, nullptr, n, c->d_red);
+  note_launch();
   sum_final_kernel<<<1, 256, 0, c->stream>>>(c->d_red, G, out, 0);
+  note_launch();
   TOPO_CUDA_TRY(c, cudaGetLastError());
   return TOPO_OK;
 }
@@ -290,6 +296,7 @@ static topo_status filter_launch(topo_ctx* c, const double* in, double* out, int
   long long blocks = (c->g.nel + 255) / 256;
   if (blocks > 8LL * c->num_sms) blocks = 8LL * c->num_sms;
   filter_kernel<<<(int)blocks, 256, sm, c->stream>>>(a);
+  note_launch();
   TOPO_CUDA_TRY(c, cudaGetLastError());
   return TOPO_OK;
 }
@@ -363,17 +370,34 @@ extern "C" topo_status topo_create(const topo_problem* prob, void* cuda_stream, 
   // element matrices in three arithmetic forms
   double K[576];
   element_stiffness(p.dim, p.nu, K);
-  if (p.dim == 2) {
-    for (int i = 0; i < 64; ++i) {
+  const int nke = p.dim == 2 ? 64 : 576;
+  // BF16 form: if K_e = s * N with N an integer matrix of entries |N| <= 256 (exactly
+  // representable in BF16), store N and fold s into each element's modulus; otherwise
+  // round every entry to BF16 (s = 1).
+  c->bf_scale = 1.0;
+  c->bf_exact = 0;
+  for (int n = 1; n <= 256 && !c->bf_exact; ++n) {
+    const double s = K[0] / n;
+    bool ok = true;
+    for (int i = 0; i < nke && ok; ++i) {
+      const double q = K[i] / s, r = nearbyint(q);
+      ok = fabs(q - r) < 1e-9 && fabs(r) <= 256.0;
+    }
+    if (ok) {
+      c->bf_exact = 1;
+      c->bf_scale = s;
+    }
+  }
+  for (int i = 0; i < nke; ++i) {
+    const float bf = c->bf_exact ? round_bf16((float)nearbyint(K[i] / c->bf_scale)) : round_bf16((float)K[i]);
+    if (p.dim == 2) {
       c->q4_64.k[i] = K[i];
       c->q4_32.k[i] = (float)K[i];
-      c->q4_bf.k[i] = round_bf16((float)K[i]);
-    }
-  } else {
-    for (int i = 0; i < 576; ++i) {
+      c->q4_bf.k[i] = bf;
+    } else {
       c->h8_64.k[i] = K[i];
       c->h8_32.k[i] = (float)K[i];
-      c->h8_bf.k[i] = round_bf16((float)K[i]);
+      c->h8_bf.k[i] = bf;
     }
   }
 
@@ -506,7 +530,9 @@ extern "C" topo_status topo_compliance_grad(topo_ctx* c, const double* rho, cons
   topo_status s = ensure_red(c, sizeof(double) * (size_t)(G * m + 64));
   if (s) return s;
   dot_cols_partial_kernel<<<dim3(G, m), 256, 0, c->stream>>>(F, U, g.ndof, ld, m, c->d_red);
+  note_launch();
   sum_final_kernel<<<1, 256, 0, c->stream>>>(c->d_red, G * m, J, 0);
+  note_launch();
   long long blocks = (g.nel + 127) / 128;
   if (blocks > 16LL * c->num_sms) blocks = 16LL * c->num_sms;
   if (g.dim == 2) {
@@ -519,6 +545,7 @@ extern "C" topo_status topo_compliance_grad(topo_ctx* c, const double* rho, cons
     a.m = m;
     a.dc = dc_rho;
     grad_kernel<2><<<(int)blocks, 128, 0, c->stream>>>(a);
+    note_launch();
   } else {
     GradArgs<3> a;
     a.g = g;
@@ -529,8 +556,16 @@ extern "C" topo_status topo_compliance_grad(topo_ctx* c, const double* rho, cons
     a.m = m;
     a.dc = dc_rho;
     grad_kernel<3><<<(int)blocks, 128, 0, c->stream>>>(a);
+    note_launch();
   }
   TOPO_CUDA_TRY(c, cudaGetLastError());
   if (dc_psi) return filter_launch(c, dc_rho, dc_psi, 2);
+  return TOPO_OK;
+}
+
+
+extern "C" topo_status topo_launch_count(long long* out) {
+  if (!out) return TOPO_ERR_INVALID;
+  *out = topo::g_launches.load(std::memory_order_relaxed);
   return TOPO_OK;
 }

@@ -21,6 +21,23 @@ namespace topo {
 
 constexpr int PCG_MAX_COLS = 32;
 
+#ifdef TOPO_BOUNDS_CHECK
+// Debug builds only: host-mapped progress record written by block 0 (phase, iteration).
+static __device__ volatile int* g_progress = nullptr;
+#define TOPO_PROGRESS(ph, it)                                          \
+  do {                                                                 \
+    if (g_progress && blockIdx.x == 0 && threadIdx.x == 0) {           \
+      g_progress[0] = (ph);                                            \
+      g_progress[1] = (it);                                            \
+      __threadfence_system();                                          \
+    }                                                                  \
+  } while (0)
+#else
+#define TOPO_PROGRESS(ph, it) \
+  do {                        \
+  } while (0)
+#endif
+
 template <int DIM, typename TI>
 struct PcgArgs {
   Grid g;
@@ -48,6 +65,7 @@ struct PcgArgs {
   double rtol, inner_rtol;
   int maxit, max_outer;
   long long wait_cycles;
+  TI escale;  // folded into the inner operator's E(rho): 1, or the BF16 table's scale
   int* info;        // [0] iters, [1] outer, [2] status
   double* info_rr;  // [0] max_c ||r||^2/||f||^2
 };
@@ -98,22 +116,38 @@ __global__ void __launch_bounds__(TileShape<DIM>::NT) pcg_kernel(const __grid_co
   GridSync* gs = a.gs;
   unsigned int my_gen = *(volatile unsigned int*)&gs->gen;
   double* part = a.partial;
+#ifdef TOPO_BOUNDS_CHECK
+  __shared__ double dummy_slot;  // sink for skipped partial writes
+  auto P = [&](int slot, int c) -> double* {
+    long long i = ((long long)(slot * m + c)) * G + blockIdx.x;
+    return TOPO_OK_IDX(i, 3LL * m * G, 16) ? part + i : &dummy_slot;
+  };
+  auto R = [&](int slot, int c) -> double {
+    return TOPO_OK_IDX(slot * m + c, 3 * m, 17) ? __ldcg(a.result + slot * m + c) : 0.0;
+  };
+#else
   auto P = [&](int slot, int c) -> double* { return part + ((size_t)(slot * m + c)) * G + blockIdx.x; };
   auto R = [&](int slot, int c) -> double { return __ldcg(a.result + slot * m + c); };
+#endif
 
   int iters = 0, outer = 0;
   bool ok = true;
 
   // --- P0: element moduli ------------------------------------------------------------
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < g.nel; e += (long long)G * blockDim.x) {
+    if (!TOPO_OK_IDX(e, g.nel, 1)) continue;
     const double rv = a.rho[e];
-    a.E[e] = young<TI>((TI)rv, (TI)g.E0, (TI)g.Emin, g.ipenal);
+    a.E[e] = a.escale * young<TI>((TI)rv, (TI)g.E0, (TI)g.Emin, g.ipenal);
     if constexpr (REFINED) a.E64[e] = young<double>(rv, g.E0, g.Emin, g.ipenal);
   }
+  TOPO_PROGRESS(1, 0);
   ok = grid_sync_reduce(gs, my_gen, part, a.result, 0, a.wait_cycles);
   if (!ok) return;
+  TOPO_PROGRESS(2, 0);
 
-  auto stageE = [&](TileCoord tc) { stage_E<DIM, TI>(s, g, tc, [&](long long e) { return ldcg(a.E + e); }); };
+  auto stageE = [&](TileCoord tc) {
+    stage_E<DIM, TI>(s, g, tc, [&](long long e) { return TOPO_OK_IDX(e, g.nel, 4) ? ldcg(a.E + e) : (TI)0; });
+  };
 
   // --- P1: Jacobi diagonal (owned nodes; read back only by the owner thread) -----------
   for (long long t = blockIdx.x; t < ntiles; t += G) {
@@ -128,7 +162,7 @@ __global__ void __launch_bounds__(TileShape<DIM>::NT) pcg_kernel(const __grid_co
 #pragma unroll
       for (int c = 0; c < DIM; ++c) {
         const long long dof = DIM * n + c;
-        a.dinv[dof] = is_fixed(g, dof) ? (TI)0 : (TI)1 / dg[c];
+        if (TOPO_OK_IDX(dof, N, 3)) a.dinv[dof] = is_fixed(g, dof) ? (TI)0 : (TI)1 / dg[c];
       }
     }
     __syncthreads();
@@ -159,18 +193,23 @@ __global__ void __launch_bounds__(TileShape<DIM>::NT) pcg_kernel(const __grid_co
           const TI* pc = pold + c * N;
           const TI beta = (TI)sh_beta[c];
           if (it == 0)
-            stage_V<DIM, TI>(s, g, tc, [&](long long dof) { return ldcg(zc + dof); });
+            stage_V<DIM, TI>(s, g, tc, [&](long long dof) { return TOPO_OK_IDX(c * N + dof, N * m, 5) ? ldcg(zc + dof) : (TI)0; });
           else
-            stage_V<DIM, TI>(s, g, tc, [&](long long dof) { return fma(beta, ldcg(pc + dof), ldcg(zc + dof)); });
+            stage_V<DIM, TI>(s, g, tc, [&](long long dof) {
+              return TOPO_OK_IDX(c * N + dof, N * m, 6) ? fma(beta, ldcg(pc + dof), ldcg(zc + dof)) : (TI)0;
+            });
           __syncthreads();
           if (own) {
             TI out[DIM];
             node_apply<DIM, TI>(s, tx, ty, tz, a.ke, out);
             using TS = TileSmem<DIM, TI>;
-            const int h = ((tz + 1) * TS::HY + (ty + 1)) * TS::HX + (tx + 1);
+            // centre of the halo'd box: the z halo exists only in 3D
+            const int h = ((DIM == 3 ? tz + 1 : 0) * TS::HY + (ty + 1)) * TS::HX + (tx + 1);
 #pragma unroll
             for (int cc = 0; cc < DIM; ++cc) {
               const long long dof = DIM * n + cc;
+              if (!TOPO_OK_IDX(DIM * h + cc, TS::NH * DIM, 21)) continue;
+              if (!TOPO_OK_IDX(c * N + dof, N * m, 7)) continue;
               const TI pv = s.v[DIM * h + cc];  // 0 on Dirichlet DOFs
               const TI qv = is_fixed(g, dof) ? (TI)0 : out[cc];
               pnew[c * N + dof] = pv;
@@ -185,14 +224,18 @@ __global__ void __launch_bounds__(TileShape<DIM>::NT) pcg_kernel(const __grid_co
         double t = block_sum(pq_acc[c], red);
         if (threadIdx.x == 0) *P(0, c) = t;
       }
+      TOPO_PROGRESS(10, it);
       if (!grid_sync_reduce(gs, my_gen, part, a.result, m, a.wait_cycles)) return false;
+      TOPO_PROGRESS(11, it);
       if (threadIdx.x == 0) {
         for (int c = 0; c < m; ++c) {
           if (sh_done[c]) continue;
           const double pq = R(0, c);
           if (!(pq > 0.0)) {
-            // breakdown: K not SPD on this column (or a NaN)
-            set_status(&gs->status, TOPO_ERR_NOT_SPD);
+            // breakdown: p^T K p <= 0 (or NaN). In FP64 this means K is not SPD; in the refined
+            // form the inner FP32 operator may be slightly indefinite on near-rigid modes of
+            // very soft regions, so the inner solve just stops and the FP64 refinement goes on.
+            if (!REFINED) set_status(&gs->status, TOPO_ERR_NOT_SPD);
             sh_alpha[c] = 0.0;
             sh_done[c] = 1;
           } else {
@@ -216,6 +259,8 @@ __global__ void __launch_bounds__(TileShape<DIM>::NT) pcg_kernel(const __grid_co
           for (int cc = 0; cc < DIM; ++cc) {
             const long long dof = DIM * n + cc;
             const long long o = c * N + dof;
+            if (!TOPO_OK_IDX(o, N * m, 9)) continue;
+            if (!REFINED && !TOPO_OK_IDX(c * ldx + dof, ldx * m, 10)) continue;
             const TI pv = pnew[o];
             const TI rv = a.r[o] - al * a.q[o];
             const TI zv = a.dinv[dof] * rv;
@@ -238,7 +283,9 @@ __global__ void __launch_bounds__(TileShape<DIM>::NT) pcg_kernel(const __grid_co
           *P(1, c) = t2;
         }
       }
+      TOPO_PROGRESS(12, it);
       if (!grid_sync_reduce(gs, my_gen, part, a.result, 2 * m, a.wait_cycles)) return false;
+      TOPO_PROGRESS(13, it);
       if (threadIdx.x == 0) {
         for (int c = 0; c < m; ++c) {
           if (sh_done[c]) continue;
@@ -257,7 +304,11 @@ __global__ void __launch_bounds__(TileShape<DIM>::NT) pcg_kernel(const __grid_co
   };
 
   if constexpr (!REFINED) {
-    // --- P2: r = f - K x0, z = D^-1 r (x0 = caller's U, Dirichlet entries zeroed) ---------
+    // --- true residual r = f - K x, z = D^-1 r (x = caller's U, Dirichlet entries zeroed).
+    // Run first, and again whenever the recursively updated residual reports convergence
+    // (residual replacement): CG then restarts from the true residual, so the reported
+    // relative residual is the true one.
+    auto true_residual = [&](bool first) -> bool {
     double acc[3][PCG_MAX_COLS];
     for (int c = 0; c < m; ++c) acc[0][c] = acc[1][c] = acc[2][c] = 0.0;
     for (long long t = blockIdx.x; t < ntiles; t += G) {
@@ -269,7 +320,7 @@ __global__ void __launch_bounds__(TileShape<DIM>::NT) pcg_kernel(const __grid_co
       for (int c = 0; c < m; ++c) {
         double* uc = a.U + c * a.ldU;
         const double* fc = a.F + c * a.ldF;
-        stage_V<DIM, TI>(s, g, tc, [&](long long dof) { return (TI)ldcg(uc + dof); });
+        stage_V<DIM, TI>(s, g, tc, [&](long long dof) { return TOPO_OK_IDX(c * a.ldU + dof, a.ldU * m, 12) ? (TI)ldcg(uc + dof) : (TI)0; });
         __syncthreads();
         if (own) {
           TI out[DIM];
@@ -278,6 +329,9 @@ __global__ void __launch_bounds__(TileShape<DIM>::NT) pcg_kernel(const __grid_co
           for (int cc = 0; cc < DIM; ++cc) {
             const long long dof = DIM * n + cc;
             const long long o = c * N + dof;
+            if (!TOPO_OK_IDX(o, N * m, 15)) continue;
+            if (!TOPO_OK_IDX(c * a.ldU + dof, a.ldU * m, 13)) continue;
+            if (!TOPO_OK_IDX(c * a.ldF + dof, a.ldF * m, 14)) continue;
             if (is_fixed(g, dof)) {
               uc[dof] = 0.0;
               a.r[o] = (TI)0;
@@ -302,20 +356,30 @@ __global__ void __launch_bounds__(TileShape<DIM>::NT) pcg_kernel(const __grid_co
         double t = block_sum(acc[k][c], red);
         if (threadIdx.x == 0) *P(k, c) = t;
       }
-    if (!grid_sync_reduce(gs, my_gen, part, a.result, 3 * m, a.wait_cycles)) return;
+    TOPO_PROGRESS(3, 0);
+    if (!grid_sync_reduce(gs, my_gen, part, a.result, 3 * m, a.wait_cycles)) return false;
+    TOPO_PROGRESS(4, 0);
     if (threadIdx.x == 0) {
       for (int c = 0; c < m; ++c) {
         sh_rz[c] = R(0, c);
         sh_rr[c] = R(1, c);
-        sh_ff[c] = R(2, c);
+        if (first) sh_ff[c] = R(2, c);
         sh_tol2[c] = a.rtol * a.rtol * sh_ff[c];
         sh_beta[c] = 0.0;
         sh_done[c] = sh_rr[c] <= sh_tol2[c];
       }
     }
     __syncthreads();
-    ok = inner_pcg(a.U, a.ldU, a.maxit);
-    if (!ok) return;
+    return true;
+    };
+    if (!true_residual(true)) return;
+    for (int rep = 0; rep < 50; ++rep) {
+      bool all = true;
+      for (int c = 0; c < m; ++c) all = all && sh_done[c];
+      if (all || iters >= a.maxit) break;
+      if (!inner_pcg(a.U, a.ldU, a.maxit - iters)) return;
+      if (!true_residual(false)) return;
+    }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
       double worst = 0.0;
       bool conv = true;
@@ -437,7 +501,7 @@ __global__ void __launch_bounds__(TileShape<DIM>::NT) pcg_kernel(const __grid_co
 template <int DIM, typename TI>
 static topo_status solve_impl(topo_ctx* c, const double* rho, const double* F, double* U, int m, int ld,
                               double rtol, int maxit, const typename KeOf<DIM, TI>::type& ke,
-                              topo_solve_info* info_host) {
+                              double escale, topo_solve_info* info_host) {
   constexpr bool REFINED = !std::is_same<TI, double>::value;
   const Grid& g = c->g;
   const long long N = g.ndof;
@@ -498,6 +562,7 @@ static topo_status solve_impl(topo_ctx* c, const double* rho, const double* F, d
   a.maxit = maxit;
   a.max_outer = c->max_outer;
   a.wait_cycles = c->wait_cycles;
+  a.escale = (TI)escale;
   // barrier arrival counter must start at zero (a previous aborted launch may have left it)
   TOPO_CUDA_TRY(c, cudaMemsetAsync(c->d_sync, 0, 2 * sizeof(unsigned int), c->stream));  // count, abort
   TOPO_CUDA_TRY(c, cudaMemsetAsync(a.info, 0, 16, c->stream));
@@ -512,6 +577,7 @@ static topo_status solve_impl(topo_ctx* c, const double* rho, const double* F, d
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   TOPO_CUDA_TRY(c, cudaLaunchKernelEx(&cfg, pcg_kernel<DIM, TI>, a));
+  note_launch();
   if (info_host) {
     int hinfo[4];
     double hrr[2];
@@ -549,15 +615,33 @@ extern "C" topo_status topo_solve_hdm(topo_ctx* c, const double* rho, const doub
     return fail(c, TOPO_ERR_INVALID, "topo_solve_hdm: null, misaligned or aliased pointer");
   if (info_host) memset(info_host, 0, sizeof(*info_host));
   if (c->g.dim == 2) {
-    if (prec == TOPO_FP64) return solve_impl<2, double>(c, rho, F, U, m, ld, rtol, maxit, c->q4_64, info_host);
-    if (prec == TOPO_FP32_REFINED) return solve_impl<2, float>(c, rho, F, U, m, ld, rtol, maxit, c->q4_32, info_host);
+    if (prec == TOPO_FP64) return solve_impl<2, double>(c, rho, F, U, m, ld, rtol, maxit, c->q4_64, 1.0, info_host);
+    if (prec == TOPO_FP32_REFINED)
+      return solve_impl<2, float>(c, rho, F, U, m, ld, rtol, maxit, c->q4_32, 1.0, info_host);
     if (prec == TOPO_FP32_BF16KE_REFINED)
-      return solve_impl<2, float>(c, rho, F, U, m, ld, rtol, maxit, c->q4_bf, info_host);
+      return solve_impl<2, float>(c, rho, F, U, m, ld, rtol, maxit, c->q4_bf, c->bf_scale, info_host);
   } else {
-    if (prec == TOPO_FP64) return solve_impl<3, double>(c, rho, F, U, m, ld, rtol, maxit, c->h8_64, info_host);
-    if (prec == TOPO_FP32_REFINED) return solve_impl<3, float>(c, rho, F, U, m, ld, rtol, maxit, c->h8_32, info_host);
+    if (prec == TOPO_FP64) return solve_impl<3, double>(c, rho, F, U, m, ld, rtol, maxit, c->h8_64, 1.0, info_host);
+    if (prec == TOPO_FP32_REFINED)
+      return solve_impl<3, float>(c, rho, F, U, m, ld, rtol, maxit, c->h8_32, 1.0, info_host);
     if (prec == TOPO_FP32_BF16KE_REFINED)
-      return solve_impl<3, float>(c, rho, F, U, m, ld, rtol, maxit, c->h8_bf, info_host);
+      return solve_impl<3, float>(c, rho, F, U, m, ld, rtol, maxit, c->h8_bf, c->bf_scale, info_host);
   }
   return fail(c, TOPO_ERR_INVALID, "topo_solve_hdm: unknown precision");
 }
+
+#ifdef TOPO_BOUNDS_CHECK
+extern "C" int topo_debug_set_progress(int* mapped) {
+  volatile int* p = mapped;
+  return (int)cudaMemcpyToSymbol(topo::g_progress, &p, sizeof(p));
+}
+// Debug builds only: first out-of-range access recorded by this translation unit's kernels.
+extern "C" int topo_debug_bounds_pcg(int* tag, long long* idx, long long* n) {
+  topo::BoundsLog h;
+  cudaMemcpyFromSymbol(&h, topo::g_bounds_log, sizeof(h));
+  *tag = h.tag;
+  *idx = h.idx;
+  *n = h.n;
+  return h.hit;
+}
+#endif

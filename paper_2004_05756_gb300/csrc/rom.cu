@@ -27,8 +27,10 @@ namespace topo {
 template <typename T>
 __global__ void __launch_bounds__(256) atb_partial_kernel(const T* __restrict__ A, long long lda, int k1,
                                                           const T* __restrict__ B, long long ldb, int k2,
-                                                          long long N, long long rows_per_cta, double* partial) {
+                                                          long long N, long long rows_per_cta, double* partial,
+                                                          const int* gate) {
   __shared__ T As[32][64 + 1];
+  if (gate && *gate == 0) return;
   __shared__ T Bs[32][64 + 1];
   const int tiles_j = (k2 + 63) / 64;
   const int ti = blockIdx.y / tiles_j, tj = blockIdx.y % tiles_j;
@@ -75,7 +77,8 @@ __global__ void __launch_bounds__(256) atb_partial_kernel(const T* __restrict__ 
 }
 
 // Sum the G partial k1 x k2 matrices in CTA order. sym: C = (C + C^T)/2 (k1 == k2).
-__global__ void atb_final_kernel(const double* partial, int G, int k1, int k2, double* C, int sym) {
+__global__ void atb_final_kernel(const double* partial, int G, int k1, int k2, double* C, int sym, const int* gate) {
+  if (gate && *gate == 0) return;
   const int KK = k1 * k2;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < KK; e += gridDim.x * blockDim.x) {
     double s = 0.0;
@@ -94,7 +97,8 @@ __global__ void atb_final_kernel(const double* partial, int G, int k1, int k2, d
 // c = A^T v (A: N x k, v: N), per-CTA partials partial[blockIdx.x * k + j]; warp w handles
 // columns w, w+8, ...; lanes stride the CTA's row range.
 __global__ void atv_partial_kernel(const double* __restrict__ A, long long lda, int k, const double* __restrict__ v,
-                                   long long N, long long rows_per_cta, double* partial) {
+                                   long long N, long long rows_per_cta, double* partial, const int* gate) {
+  if (gate && *gate == 0) return;
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
   const long long r_begin = blockIdx.x * rows_per_cta;
   const long long r_end = min(N, r_begin + rows_per_cta);
@@ -108,7 +112,9 @@ __global__ void atv_partial_kernel(const double* __restrict__ A, long long lda, 
 }
 
 // out[j] = (subtract ? base[j] - s : s), s = sum_g partial[g * k + j] (fixed order).
-__global__ void atv_final_kernel(const double* partial, int G, int k, double* out, const double* base) {
+__global__ void atv_final_kernel(const double* partial, int G, int k, double* out, const double* base,
+                                 const int* gate) {
+  if (gate && *gate == 0) return;
   for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < k; j += gridDim.x * blockDim.x) {
     double s = 0.0;
     for (int g = 0; g < G; ++g) s += partial[(size_t)g * k + j];
@@ -118,8 +124,9 @@ __global__ void atv_final_kernel(const double* partial, int G, int k, double* ou
 
 // y = A c (mode 0), or y -= A c (mode 1); A: N x k, c FP64[k] (device).
 __global__ void gemv_kernel(const double* __restrict__ A, long long lda, int k, const double* __restrict__ cvec,
-                            double* y, long long N, int mode) {
+                            double* y, long long N, int mode, const int* gate) {
   extern __shared__ double sc[];
+  if (gate && *gate == 0) return;
   for (int j = threadIdx.x; j < k; j += blockDim.x) sc[j] = cvec[j];
   __syncthreads();
   for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < N; r += (long long)gridDim.x * blockDim.x) {
@@ -165,9 +172,10 @@ __global__ void to_float_kernel(const double* __restrict__ A, long long lda, int
 // the lower triangle), then y = H^{-1} b and J = b^T y. A pivot <= 0 (or NaN) sets
 // TOPO_ERR_NOT_SPD and writes NaN to y and J.
 // ---------------------------------------------------------------------------------------
-__global__ void cholesky_kernel(double* H, int k, int* status, int* ok_flag) {
+__global__ void cholesky_kernel(double* H, int k, int* status, int* ok_flag, const int* gate) {
   extern __shared__ double A[];  // k * k
   __shared__ int bad;
+  if (gate && *gate == 0) return;
   for (int e = threadIdx.x; e < k * k; e += blockDim.x) A[e] = H[e];
   if (threadIdx.x == 0) bad = 0;
   __syncthreads();
@@ -198,18 +206,18 @@ __global__ void cholesky_kernel(double* H, int k, int* status, int* ok_flag) {
   }
   if (threadIdx.x == 0) {
     *ok_flag = !bad;
-    if (bad) atomicCAS(status, 0, (int)TOPO_ERR_NOT_SPD);
+    if (bad && status) atomicCAS(status, 0, (int)TOPO_ERR_NOT_SPD);
   }
 }
 
 // Solve L L^T x = rhs (L lower, row-major). mode 0: y = x; mode 1: y += x. Skipped (y left
 // unchanged) when *skip is non-zero; NaN output when the factorisation failed.
 __global__ void chol_solve_kernel(const double* L, int k, const double* rhs, double* y, int mode, const int* ok_flag,
-                                  const int* skip) {
+                                  const int* gate) {
   extern __shared__ double sm[];
   double* Ls = sm;          // k*k
   double* z = sm + k * k;   // k
-  if (skip && *skip) return;
+  if (gate && *gate == 0) return;
   if (!*ok_flag) {
     for (int i = threadIdx.x; i < k; i += blockDim.x) y[i] = nan("");
     return;
@@ -245,9 +253,11 @@ __global__ void dot_small_kernel(const double* b, const double* y, int k, double
   if (threadIdx.x == 0) *J = t;
 }
 
-// Convergence flag of the reduced refinement: skip = ||g|| <= tol * ||b||.
-__global__ void refine_flag_kernel(const double* g, const double* b, int k, double tol, int* skip) {
+// Convergence test of the reduced refinement (runs while flags[2] "active" is set):
+// ||g|| <= tol ||b|| sets flags[1] "converged" and clears "active".
+__global__ void refine_flag_kernel(const double* g, const double* b, int k, double tol, int* flags) {
   __shared__ double red[32];
+  if (flags[2] == 0) return;
   double a = 0.0, c = 0.0;
   for (int i = threadIdx.x; i < k; i += blockDim.x) {
     a = fma(g[i], g[i], a);
@@ -255,7 +265,17 @@ __global__ void refine_flag_kernel(const double* g, const double* b, int k, doub
   }
   const double ta = block_sum(a, red);
   const double tc = block_sum(c, red);
-  if (threadIdx.x == 0) *skip = (sqrt(ta) <= tol * sqrt(tc)) ? 1 : *skip;
+  if (threadIdx.x == 0 && sqrt(ta) <= tol * sqrt(tc)) {
+    flags[1] = 1;
+    flags[2] = 0;
+  }
+}
+
+// flags[2] = active = Cholesky of the FP32 matrix succeeded (flags[0]).
+__global__ void refine_start_kernel(int* flags) { flags[2] = flags[0]; }
+// flags[3] = fallback to FP64: the FP32 matrix was not SPD, or refinement did not converge.
+__global__ void refine_end_kernel(int* flags, int require_conv) {
+  flags[3] = (!flags[0] || (require_conv && !flags[1])) ? 1 : 0;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -277,23 +297,30 @@ static RowSplit row_split(topo_ctx* c, long long N, int per_sm) {
 
 template <typename T>
 static topo_status launch_atb(topo_ctx* c, const T* A, long long lda, int k1, const T* B, long long ldb, int k2,
-                              long long N, double* partial_buf, size_t partial_cap, double* C, int sym) {
+                              long long N, double* partial_buf, size_t partial_cap, double* C, int sym,
+                              const int* gate = nullptr) {
   RowSplit rs = row_split(c, N, 2);
   size_t need = (size_t)rs.G * k1 * k2;
   if (need > partial_cap) return fail(c, TOPO_ERR_INVALID, "internal: atb partial buffer too small");
   const int tiles = ((k1 + 63) / 64) * ((k2 + 63) / 64);
-  atb_partial_kernel<T><<<dim3(rs.G, tiles), 256, 0, c->stream>>>(A, lda, k1, B, ldb, k2, N, rs.rows, partial_buf);
-  atb_final_kernel<<<(k1 * k2 + 255) / 256, 256, 0, c->stream>>>(partial_buf, rs.G, k1, k2, C, sym);
+  atb_partial_kernel<T><<<dim3(rs.G, tiles), 256, 0, c->stream>>>(A, lda, k1, B, ldb, k2, N, rs.rows, partial_buf,
+                                                                    gate);
+  note_launch();
+  atb_final_kernel<<<(k1 * k2 + 255) / 256, 256, 0, c->stream>>>(partial_buf, rs.G, k1, k2, C, sym, gate);
+  note_launch();
   TOPO_CUDA_TRY(c, cudaGetLastError());
   return TOPO_OK;
 }
 
 static topo_status launch_atv(topo_ctx* c, const double* A, long long lda, int k, const double* v, long long N,
-                              double* partial_buf, size_t partial_cap, double* out, const double* base) {
+                              double* partial_buf, size_t partial_cap, double* out, const double* base,
+                              const int* gate = nullptr) {
   RowSplit rs = row_split(c, N, 4);
   if ((size_t)rs.G * k > partial_cap) return fail(c, TOPO_ERR_INVALID, "internal: atv partial buffer too small");
-  atv_partial_kernel<<<rs.G, 256, 0, c->stream>>>(A, lda, k, v, N, rs.rows, partial_buf);
-  atv_final_kernel<<<1, 128, 0, c->stream>>>(partial_buf, rs.G, k, out, base);
+  atv_partial_kernel<<<rs.G, 256, 0, c->stream>>>(A, lda, k, v, N, rs.rows, partial_buf, gate);
+  note_launch();
+  atv_final_kernel<<<1, 128, 0, c->stream>>>(partial_buf, rs.G, k, out, base, gate);
+  note_launch();
   TOPO_CUDA_TRY(c, cudaGetLastError());
   return TOPO_OK;
 }
@@ -311,22 +338,23 @@ static size_t partial_capacity(topo_ctx* c, long long N, int k) {
 
 // Projection H = Phi^T K Phi (and optionally b = Phi^T f) into H (k x k, row-major).
 static topo_status project(topo_ctx* c, const double* rho, const double* Phi, int k, long long ld, topo_prec prec,
-                           double* H, double* b, const double* f, char* scratch) {
+                           double* H, double* b, const double* f, char* scratch, const int* gate = nullptr) {
   const long long N = c->g.ndof;
   size_t pcap = partial_capacity(c, N, k);
   double* partial = (double*)scratch;
   char* p = scratch + ((pcap * sizeof(double) + 255) & ~(size_t)255);
   if (prec == TOPO_FP64) {
     double* W = (double*)p;
-    topo_status s = launch_apply(c, rho, Phi, W, k, (int)ld, TOPO_FP64);
+    topo_status s = launch_apply(c, rho, Phi, W, k, (int)ld, TOPO_FP64, gate);
     if (s) return s;
     // W has leading dimension ld (same as Phi)
-    s = launch_atb<double>(c, Phi, ld, k, W, ld, k, N, partial, pcap, H, 1);
+    s = launch_atb<double>(c, Phi, ld, k, W, ld, k, N, partial, pcap, H, 1, gate);
     if (s) return s;
   } else {
     float* P32 = (float*)p;
     float* W32 = P32 + (size_t)N * k;
     to_float_kernel<<<stream_blocks(c, N * k), 256, 0, c->stream>>>(Phi, ld, k, P32, N);
+    note_launch();
     topo_status s = launch_apply(c, rho, P32, W32, k, (int)N, prec);
     if (s) return s;
     s = launch_atb<float>(c, P32, N, k, W32, N, k, N, partial, pcap, H, 1);
@@ -375,7 +403,9 @@ extern "C" topo_status topo_rom_build(topo_ctx* c, const double* rho, const doub
   std::vector<double> norms(m);
   for (int j = 0; j < m; ++j) {
     nrm2_partial_kernel<<<rs.G, 256, 0, c->stream>>>(Usnap + (long long)j * ld, N, partial);
+    note_launch();
     nrm2_final_kernel<<<1, 256, 0, c->stream>>>(partial, rs.G, nrm + (j % 64));
+    note_launch();
     if (j % 64 == 63 || j == m - 1) {
       int base = (j / 64) * 64, cnt = j - base + 1;
       TOPO_CUDA_TRY(c, cudaMemcpyAsync(norms.data() + base, nrm, cnt * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
@@ -393,15 +423,19 @@ extern "C" topo_status topo_rom_build(topo_ctx* c, const double* rho, const doub
       for (int pass = 0; pass < 2 && k > 0; ++pass) {
         s = launch_atv(c, Phi, ld, k, v, N, partial, pcap, coef, nullptr);
         if (s) return s;
-        gemv_kernel<<<nb, 256, k * sizeof(double), c->stream>>>(Phi, ld, k, coef, v, N, 1);
+        gemv_kernel<<<nb, 256, k * sizeof(double), c->stream>>>(Phi, ld, k, coef, v, N, 1, nullptr);
+        note_launch();
       }
       nrm2_partial_kernel<<<rs.G, 256, 0, c->stream>>>(v, N, partial);
+      note_launch();
       nrm2_final_kernel<<<1, 256, 0, c->stream>>>(partial, rs.G, nrm);
+      note_launch();
       double hn = 0.0;
       TOPO_CUDA_TRY(c, cudaMemcpyAsync(&hn, nrm, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
       TOPO_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
       if (hn >= 1e-10 * scale) {
         scale_kernel<<<nb, 256, 0, c->stream>>>(v, N, nrm);
+        note_launch();
         ++k;
       }
     }
@@ -423,46 +457,72 @@ extern "C" topo_status topo_rom_solve(topo_ctx* c, const double* rho, const doub
   if (!dev_ptr_ok(rho) || !dev_ptr_ok(Phi) || !dev_ptr_ok(b) || !dev_ptr_ok(H_work) || !dev_ptr_ok(yhat) ||
       !dev_ptr_ok(Jk))
     return fail(c, TOPO_ERR_INVALID, "topo_rom_solve: null or misaligned pointer");
-  const bool refine = prec != TOPO_FP64 && c->rom_refine > 0;
   size_t pcap = partial_capacity(c, N, k);
-  size_t extra = refine ? (2 * (size_t)N + 4 * 128 + 64) * sizeof(double) : 256;
-  size_t need = project_scratch(c, k, ld, prec) + extra + 1024;
+  // the mixed forms may fall back to the FP64 projection, which needs its own (larger) W
+  const size_t proj = std::max(project_scratch(c, k, ld, prec), project_scratch(c, k, ld, TOPO_FP64));
+  const size_t extra = (2 * (size_t)N + 4 * 128 + 64) * sizeof(double);
+  size_t need = proj + 256 + extra + 1024;
   topo_status s = ensure_scratch(c, need);
   if (s) return s;
   char* scratch = (char*)c->d_scratch;
   s = project(c, rho, Phi, k, ld, prec, H_work, nullptr, nullptr, scratch);
   if (s) return s;
   // flags live after the projection scratch
-  char* tail = scratch + project_scratch(c, k, ld, prec);
-  int* flags = (int*)tail;  // [0] ok, [1] skip
+  char* tail = scratch + proj;
+  int* flags = (int*)tail;  // [0] ok32 [1] converged [2] active [3] fallback [4] ok64
   double* tailD = (double*)(tail + 256);
-  TOPO_CUDA_TRY(c, cudaMemsetAsync(flags, 0, 2 * sizeof(int), c->stream));
+  TOPO_CUDA_TRY(c, cudaMemsetAsync(flags, 0, 8 * sizeof(int), c->stream));
   const size_t sm_chol = (size_t)k * k * sizeof(double);
   const size_t sm_solve = sm_chol + k * sizeof(double);
   if (sm_solve > 48 * 1024) {
     TOPO_CUDA_TRY(c, cudaFuncSetAttribute(cholesky_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_solve));
     TOPO_CUDA_TRY(c, cudaFuncSetAttribute(chol_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_solve));
   }
-  cholesky_kernel<<<1, 256, sm_chol, c->stream>>>(H_work, k, &c->d_sync->status, flags);
-  chol_solve_kernel<<<1, 128, sm_solve, c->stream>>>(H_work, k, b, yhat, 0, flags, nullptr);
-  if (refine) {
+  if (prec == TOPO_FP64) {
+    cholesky_kernel<<<1, 256, sm_chol, c->stream>>>(H_work, k, &c->d_sync->status, flags + 4, nullptr);
+    note_launch();
+    chol_solve_kernel<<<1, 128, sm_solve, c->stream>>>(H_work, k, b, yhat, 0, flags + 4, nullptr);
+    note_launch();
+  } else {
+    // FP32 reduced matrix: factor it (a failure is not an error here), solve, then refine
+    // yhat with FP64 reduced residuals g = b - Phi^T K(rho) (Phi yhat).
+    cholesky_kernel<<<1, 256, sm_chol, c->stream>>>(H_work, k, nullptr, flags + 0, nullptr);
+    note_launch();
+    chol_solve_kernel<<<1, 128, sm_solve, c->stream>>>(H_work, k, b, yhat, 0, flags + 0, flags + 0);
+    note_launch();
+    refine_start_kernel<<<1, 1, 0, c->stream>>>(flags);
+    note_launch();
     double* u = tailD;
     double* w = u + N;
     double* g = w + N;  // [k]
     double* partial = (double*)scratch;  // projection partials are dead now
     const int nb = stream_blocks(c, N);
+    const int* active = flags + 2;
     for (int it = 0; it < c->rom_refine; ++it) {
-      // g = b - Phi^T K (Phi yhat), all FP64
-      gemv_kernel<<<nb, 256, k * sizeof(double), c->stream>>>(Phi, ld, k, yhat, u, N, 0);
-      s = launch_apply(c, rho, u, w, 1, (int)N, TOPO_FP64);
+      gemv_kernel<<<nb, 256, k * sizeof(double), c->stream>>>(Phi, ld, k, yhat, u, N, 0, active);
+      note_launch();
+      s = launch_apply(c, rho, u, w, 1, (int)N, TOPO_FP64, active);
       if (s) return s;
-      s = launch_atv(c, Phi, ld, k, w, N, partial, pcap, g, b);
+      s = launch_atv(c, Phi, ld, k, w, N, partial, pcap, g, b, active);
       if (s) return s;
-      refine_flag_kernel<<<1, 128, 0, c->stream>>>(g, b, k, 1e-14, flags + 1);
-      chol_solve_kernel<<<1, 128, sm_solve, c->stream>>>(H_work, k, g, yhat, 1, flags, flags + 1);
+      refine_flag_kernel<<<1, 128, 0, c->stream>>>(g, b, k, 1e-11, flags);
+      note_launch();
+      chol_solve_kernel<<<1, 128, sm_solve, c->stream>>>(H_work, k, g, yhat, 1, flags + 0, active);
+      note_launch();
     }
+    refine_end_kernel<<<1, 1, 0, c->stream>>>(flags, c->rom_refine > 0 ? 1 : 0);
+    note_launch();
+    // FP64 fallback, executed on the device only when flags[3] is set
+    const int* fb = flags + 3;
+    s = project(c, rho, Phi, k, ld, TOPO_FP64, H_work, nullptr, nullptr, scratch, fb);
+    if (s) return s;
+    cholesky_kernel<<<1, 256, sm_chol, c->stream>>>(H_work, k, &c->d_sync->status, flags + 4, fb);
+    note_launch();
+    chol_solve_kernel<<<1, 128, sm_solve, c->stream>>>(H_work, k, b, yhat, 0, flags + 4, fb);
+    note_launch();
   }
   dot_small_kernel<<<1, 128, 0, c->stream>>>(b, yhat, k, Jk);
+  note_launch();
   TOPO_CUDA_TRY(c, cudaGetLastError());
   return TOPO_OK;
 }
@@ -482,7 +542,8 @@ extern "C" topo_status topo_rom_error(topo_ctx* c, const double* rho, const doub
     if (s) return s;
     uk = (double*)c->d_scratch;
   }
-  gemv_kernel<<<stream_blocks(c, N), 256, k * sizeof(double), c->stream>>>(Phi, ld, k, yhat, uk, N, 0);
+  gemv_kernel<<<stream_blocks(c, N), 256, k * sizeof(double), c->stream>>>(Phi, ld, k, yhat, uk, N, 0, nullptr);
+  note_launch();
   TOPO_CUDA_TRY(c, cudaGetLastError());
   return launch_residual64(c, rho, uk, f, nullptr, resnorm);
 }

@@ -25,7 +25,7 @@ PREC = {"fp64": TOPO_FP64, "fp32": TOPO_FP32_REFINED, "fp32_bf16ke": TOPO_FP32_B
 # Every entry point declared in include/topo.h (checked by the tests).
 EXPORTS = ["topo_create", "topo_destroy", "topo_last_error", "topo_set_param", "topo_check", "topo_sizes",
            "topo_filter", "topo_apply_K", "topo_solve_hdm", "topo_rom_build", "topo_rom_solve",
-           "topo_rom_error", "topo_compliance_grad"]
+           "topo_rom_error", "topo_compliance_grad", "topo_launch_count"]
 
 
 class TopoError(RuntimeError):
@@ -72,6 +72,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "topo_rom_solve": ([P, P, P, I, I, P, P, P, P, I], I),
         "topo_rom_error": ([P, P, P, I, I, P, P, P, P], I),
         "topo_compliance_grad": ([P, P, P, I, I, P, P, P, P], I),
+        "topo_launch_count": ([ctypes.POINTER(LL)], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -79,6 +80,13 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         fn.restype = res
     _lib = L
     return L
+
+
+def launch_count() -> int:
+    """Kernel launches issued by libtopo so far in this process."""
+    n = ctypes.c_longlong(0)
+    load().topo_launch_count(ctypes.byref(n))
+    return int(n.value)
 
 
 def _ptr(t) -> int | None:
@@ -188,8 +196,10 @@ def _cols(t, N: int):
     tensor of shape (m, ld) (row c = column c) or a 1-D vector of length >= N."""
     if t.dim() == 1:
         return 1, int(t.shape[0])
-    if t.stride(1) != 1:
+    if t.shape[1] > 1 and t.stride(1) != 1:
         raise ValueError("column blocks must be (m, ld) tensors with unit stride along ld")
+    if t.shape[0] == 1:  # a single column: its stride along dim 0 is meaningless
+        return 1, int(t.shape[1])
     return int(t.shape[0]), int(t.stride(0))
 
 

@@ -63,9 +63,13 @@ def test_apply_fp64(torch, case, m):
 
 
 @pytest.mark.parametrize("case", ["q4_60x20", "q4_37x13", "h8_6x5x4", "h8_11x9x6"])
-@pytest.mark.parametrize("prec,tol", [("fp32", 2e-6), ("fp32_bf16ke", 8e-3)])
-def test_apply_fp32(torch, case, prec, tol):
+@pytest.mark.parametrize("prec,tol,nu", [("fp32", 2e-6, 0.3), ("fp32_bf16ke", 2e-6, 0.3), ("fp32_bf16ke", 8e-3, 0.27)])
+def test_apply_fp32(torch, case, prec, tol, nu):
+    """At nu = 0.3 the unit K_e is an integer matrix (|entries| <= 36 for Q4, 88 for H8) times a
+    scalar, so its BF16 table is exact and the BF16 form matches FP32; at nu = 0.27 the table
+    is rounded to BF16."""
     p = CASES[case]()
+    p.nu = nu
     T = ctx_for(p)
     rng = np.random.default_rng(3)
     rho = rng.uniform(1e-3, 1, p.nel)
@@ -183,8 +187,15 @@ def test_compliance_grad(torch, case, m):
     dp = torch.zeros(p.nel, dtype=torch.float64, device="cuda")
     T.topo_compliance_grad(dev(rho), cols(Uo), cols(p.F), J, dc, dp)
     assert abs(J.item() - Jo) <= 1e-13 * abs(Jo)
-    assert relerr(dc.cpu().numpy(), dco) < 1e-12
-    assert relerr(dp.cpu().numpy(), dpo) < 1e-12
+    # u_e^T K_e u_e cancels when u_e is dominated by a rigid motion, so two correct FP64
+    # evaluations differ by up to ~ 2 n eps E'(rho) sum_c |u_e|^T |K_e| |u_e| (n = ndof_e).
+    from oracle import element
+    Ka = np.abs(element.ke(p.dim, p.nu))
+    ed = fem.edof(p)
+    absq = sum(np.einsum("ei,ij,ej->e", np.abs(Uo[ed, c]), Ka, np.abs(Uo[ed, c])) for c in range(Uo.shape[1]))
+    bound = 2 * Ka.shape[0] * np.finfo(float).eps * fem.dyoung(rho, p.E0, p.Emin, p.penal) * absq
+    assert np.all(np.abs(dc.cpu().numpy() - dco) <= bound + 1e-300)
+    assert np.abs(dp.cpu().numpy() - dpo).max() <= hatfilter.filter_adj(p, bound).max() + 1e-300
 
 
 def _snapshots(p, psi, m):
