@@ -197,7 +197,7 @@ def run_ours(args, rank, world):
         # initial snapshot window: HDM solves of k seeded designs (setup, untimed)
         for i in range(k):
             T.topo_filter(torch.as_tensor(snaps[:, i].copy()).to(**f64), rho)
-            T.topo_solve_hdm(rho, F, Usnap[i:i + 1], rtol=1e-8, prec=prec)
+            T.topo_solve_hdm(rho, F, Usnap[i:i + 1], rtol=1e-8, maxit=400000, prec=prec)
         stream.synchronize()
 
     ev = lambda: torch.cuda.Event(enable_timing=True)
@@ -213,7 +213,8 @@ def run_ours(args, rank, world):
             d_cand.copy_(hin["cands"], non_blocking=True)
         T.topo_filter(d_cent[s], rho)
         Uc.zero_()
-        info = T.topo_solve_hdm(rho, F, Uc, rtol=1e-8, maxit=200000, prec=prec)
+        info = T.topo_solve_hdm(rho, F, Uc, rtol=1e-8, maxit=400000, prec=prec)
+        assert info["status"] == 0, info
         T.topo_compliance_grad(rho, Uc, F, J, dc, dpsi)
         e1.record(stream)
         Usnap[s % k].copy_(Uc[0])
@@ -307,7 +308,7 @@ def run_ours(args, rank, world):
         # mixed HDM J vs FP64 HDM J at the last centre
         T.topo_filter(d_cent[args.warmup + min(2, args.steps) - 1], rho)
         Umx = torch.zeros((1, N), **f64)
-        T.topo_solve_hdm(rho, F, Umx, rtol=1e-8, maxit=200000, prec=prec)
+        T.topo_solve_hdm(rho, F, Umx, rtol=1e-8, maxit=400000, prec=prec)
         Jmx = torch.zeros(1, **f64)
         T.topo_compliance_grad(rho, Umx, F, Jmx, dc, dpsi)
         hdm_rel = abs(Jmx.item() - J64.item()) / abs(J64.item())
@@ -387,7 +388,8 @@ def main():
     ap.add_argument("--config", default="mbb600x200", choices=list(CONFIGS))
     ap.add_argument("--k", type=int, default=16)
     ap.add_argument("--rom-evals", type=int, default=100)
-    ap.add_argument("--prec", default="fp32", choices=["fp64", "fp32", "fp32_bf16ke"])
+    ap.add_argument("--prec", default="fp32", choices=["fp64", "fp32", "fp32_bf16ke"],
+                    help="arithmetic of the reduced solves and of the HDM solve's inner iterations")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -79,7 +79,8 @@ typedef enum {
   TOPO_PARAM_WAIT_CYCLES = 2,  /* spin limit of device-side waits, in SM clock cycles (default 2e9) */
   TOPO_PARAM_ROM_REFINE = 3,   /* max FP64 refinement steps of the reduced solve (default 8) */
   TOPO_PARAM_TILE_X = 4,       /* apply tile width in nodes (autotuner hint; 0 = default) */
-  TOPO_PARAM_PCG_BLOCKS_PER_SM = 5 /* CTAs per SM of the persistent PCG (0 = occupancy) */
+  TOPO_PARAM_PCG_BLOCKS_PER_SM = 5, /* CTAs per SM of the persistent PCG (0 = occupancy) */
+  TOPO_PARAM_INNER_CAP = 6         /* max FP32 inner iterations per refinement step (default 2000) */
 } topo_param;
 
 /* Create a context for one problem; computes K_e (2x2(x2) Gauss quadrature), the filter
@@ -117,7 +118,10 @@ topo_status topo_apply_K(topo_ctx* ctx, const double* rho, const void* V, void* 
 
 /* State solve K(rho) u = f (Eq. linelastsoln) for m load cases by Jacobi-preconditioned CG
  * in one persistent cooperative launch, to ||f - K u||_2 <= rtol ||f||_2 over free DOFs
- * (each column separately). F, U: FP64 N x m, ld; U holds the initial guess on entry and
+ * (each column separately; the reported residual is the true FP64 one). The FP32 forms run
+ * FP32 inner PCG inside FP64 iterative refinement; a refinement step that fails to halve the
+ * FP64 residual norm (eps_32 * cond(K) too large for the design) stops the refinement and
+ * the call finishes with FP64 PCG from the current iterate, so those forms synchronise. F, U: FP64 N x m, ld; U holds the initial guess on entry and
  * the solution on exit (Dirichlet DOFs set to 0). maxit bounds the (inner) iterations.
  * info_host (host, may be NULL): if non-NULL the call synchronises and fills it, and
  * returns TOPO_ERR_NOT_CONVERGED when rtol was not reached. */

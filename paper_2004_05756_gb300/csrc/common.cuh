@@ -437,6 +437,7 @@ struct topo_ctx {
   long long wait_cycles;
   int rom_refine;
   int pcg_blocks_per_sm;
+  int inner_cap;
   char err[512];
 };
 

@@ -335,6 +335,7 @@ extern "C" topo_status topo_create(const topo_problem* prob, void* cuda_stream, 
   c->wait_cycles = 2000000000LL;
   c->rom_refine = 8;
   c->pcg_blocks_per_sm = 0;
+  c->inner_cap = 2000;
   cudaGetDevice(&c->device);
   cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
   if (c->num_sms <= 0) c->num_sms = 1;
@@ -479,6 +480,10 @@ extern "C" topo_status topo_set_param(topo_ctx* c, topo_param which, double v) {
       return TOPO_OK;
     case TOPO_PARAM_TILE_X:
       return TOPO_OK;  // fixed tile shapes in this build; accepted for API stability
+    case TOPO_PARAM_INNER_CAP:
+      if (!(v >= 1 && v <= 1e7)) return fail(c, TOPO_ERR_INVALID, "inner cap must be in [1,1e7]");
+      c->inner_cap = (int)v;
+      return TOPO_OK;
     case TOPO_PARAM_PCG_BLOCKS_PER_SM:
       if (!(v >= 0 && v <= 8)) return fail(c, TOPO_ERR_INVALID, "blocks per SM must be in [0,8]");
       c->pcg_blocks_per_sm = (int)v;

@@ -66,7 +66,8 @@ struct PcgArgs {
   int maxit, max_outer;
   long long wait_cycles;
   TI escale;  // folded into the inner operator's E(rho): 1, or the BF16 table's scale
-  int* info;        // [0] iters, [1] outer, [2] status
+  int inner_cap;    // max inner FP32 iterations per refinement step
+  int* info;        // [0] iters, [1] outer, [2] status, [3] refinement stalled
   double* info_rr;  // [0] max_c ||r||^2/||f||^2
 };
 
@@ -107,6 +108,8 @@ __global__ void __launch_bounds__(TileShape<DIM>::NT) pcg_kernel(const __grid_co
   __shared__ double sh_rz[PCG_MAX_COLS], sh_alpha[PCG_MAX_COLS], sh_beta[PCG_MAX_COLS], sh_tol2[PCG_MAX_COLS],
       sh_ff[PCG_MAX_COLS], sh_rr[PCG_MAX_COLS];
   __shared__ int sh_done[PCG_MAX_COLS], sh_odone[PCG_MAX_COLS];
+  __shared__ double sh_prev[PCG_MAX_COLS];
+  __shared__ int sh_stall;
 
   const Grid& g = a.g;
   const int m = a.m;
@@ -450,12 +453,21 @@ __global__ void __launch_bounds__(TileShape<DIM>::NT) pcg_kernel(const __grid_co
       }
     if (!grid_sync_reduce(gs, my_gen, part, a.result, 3 * m, a.wait_cycles)) return;
     if (threadIdx.x == 0) {
+      if (outer == 0) sh_stall = 0;
       for (int c = 0; c < m; ++c) {
         if (outer > 0 && sh_odone[c]) continue;
         const double rz = R(0, c), rr = R(1, c), ff = R(2, c);
         if (outer == 0) sh_ff[c] = ff;
         sh_rr[c] = rr;
         sh_odone[c] = rr <= a.rtol * a.rtol * sh_ff[c];
+        // A refinement step that did not cut the FP64 residual norm at least in half means
+        // the FP32 inner operator is too far from K for this design (eps_32 * cond(K) > 1):
+        // stop refining this column; the host finishes it with FP64 PCG.
+        if (!sh_odone[c] && outer > 0 && !(rr <= 0.25 * sh_prev[c])) {
+          sh_odone[c] = 1;
+          sh_stall = 1;
+        }
+        sh_prev[c] = rr;
         sh_rz[c] = rz;
         sh_tol2[c] = a.inner_rtol * a.inner_rtol * rr;
         sh_beta[c] = 0.0;
@@ -471,7 +483,7 @@ __global__ void __launch_bounds__(TileShape<DIM>::NT) pcg_kernel(const __grid_co
     }
     if (conv || outer >= a.max_outer || iters >= a.maxit) break;
     // inner FP32 PCG on K d = r
-    if (!inner_pcg(nullptr, 0, a.maxit - iters)) return;
+    if (!inner_pcg(nullptr, 0, min(a.inner_cap, a.maxit - iters))) return;
     // Phase U: u += d on free DOFs
     for (long long t = blockIdx.x; t < ntiles; t += G) {
       const TileCoord tc = tile_coord<DIM>(g, t);
@@ -493,10 +505,16 @@ __global__ void __launch_bounds__(TileShape<DIM>::NT) pcg_kernel(const __grid_co
     a.info[0] = iters;
     a.info[1] = outer;
     a.info[2] = conv ? 0 : TOPO_ERR_NOT_CONVERGED;
+    a.info[3] = sh_stall;
     a.info_rr[0] = worst;
   }
   }
 }
+
+template <int DIM, typename TI>
+static topo_status solve_impl(topo_ctx* c, const double* rho, const double* F, double* U, int m, int ld,
+                              double rtol, int maxit, const typename KeOf<DIM, TI>::type& ke,
+                              double escale, topo_solve_info* info_host);
 
 template <int DIM, typename TI>
 static topo_status solve_impl(topo_ctx* c, const double* rho, const double* F, double* U, int m, int ld,
@@ -563,6 +581,7 @@ static topo_status solve_impl(topo_ctx* c, const double* rho, const double* F, d
   a.max_outer = c->max_outer;
   a.wait_cycles = c->wait_cycles;
   a.escale = (TI)escale;
+  a.inner_cap = c->inner_cap;
   // barrier arrival counter must start at zero (a previous aborted launch may have left it)
   TOPO_CUDA_TRY(c, cudaMemsetAsync(c->d_sync, 0, 2 * sizeof(unsigned int), c->stream));  // count, abort
   TOPO_CUDA_TRY(c, cudaMemsetAsync(a.info, 0, 16, c->stream));
@@ -578,6 +597,46 @@ static topo_status solve_impl(topo_ctx* c, const double* rho, const double* F, d
   cfg.numAttrs = 1;
   TOPO_CUDA_TRY(c, cudaLaunchKernelEx(&cfg, pcg_kernel<DIM, TI>, a));
   note_launch();
+  if (REFINED) {
+    // The refined form finishes any column whose refinement stalled with FP64 PCG from the
+    // current iterate. This needs the stall flag on the host: synchronise.
+    int hinfo[4];
+    double hrr[2];
+    TOPO_CUDA_TRY(c, cudaMemcpyAsync(hinfo, a.info, 16, cudaMemcpyDeviceToHost, c->stream));
+    TOPO_CUDA_TRY(c, cudaMemcpyAsync(hrr, a.info_rr, 16, cudaMemcpyDeviceToHost, c->stream));
+    TOPO_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    if (hinfo[2] != 0 && hinfo[0] < maxit) {
+      topo_solve_info sub;
+      memset(&sub, 0, sizeof(sub));
+      const typename KeOf<DIM, double>::type& ke64 = *reinterpret_cast<const typename KeOf<DIM, double>::type*>(
+          DIM == 2 ? (const void*)&c->q4_64 : (const void*)&c->h8_64);
+      topo_status st2 = solve_impl<DIM, double>(c, rho, F, U, m, ld, rtol, maxit - hinfo[0], ke64, 1.0, &sub);
+      if (info_host) {
+        info_host->iters = hinfo[0] + sub.iters;
+        info_host->outer = hinfo[1];
+        info_host->relres = sub.relres;
+        info_host->status = sub.status;
+      }
+      if (st2 == TOPO_ERR_NOT_CONVERGED && !info_host) return TOPO_OK;
+      return st2;
+    }
+    if (info_host) {
+      info_host->iters = hinfo[0];
+      info_host->outer = hinfo[1];
+      info_host->relres = sqrt(hrr[0]);
+      info_host->status = hinfo[2];
+      int dev_status = 0;
+      TOPO_CUDA_TRY(c, cudaMemcpy(&dev_status, &c->d_sync->status, sizeof(int), cudaMemcpyDeviceToHost));
+      if (dev_status) {
+        info_host->status = dev_status;
+        int zero = 0;
+        cudaMemcpy(&c->d_sync->status, &zero, sizeof(int), cudaMemcpyHostToDevice);
+        return fail(c, (topo_status)dev_status, "topo_solve_hdm: device status %d", dev_status);
+      }
+      if (hinfo[2]) return fail(c, TOPO_ERR_NOT_CONVERGED, "topo_solve_hdm: relres %.3e", info_host->relres);
+    }
+    return TOPO_OK;
+  }
   if (info_host) {
     int hinfo[4];
     double hrr[2];
