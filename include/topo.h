@@ -151,6 +151,20 @@ topo_status topo_rom_solve(topo_ctx* ctx, const double* rho, const double* Phi, 
                            const double* b, double* H_work, double* yhat, double* Jk,
                            topo_prec prec);
 
+/* Element reduced matrices of a basis (Eq. hatkbm written per element, Remark rom_assemble):
+ * Hel[e] = (P_e^T Phi)^T K_e (P_e^T Phi) at unit density, independent of rho. Stored as
+ * (N_e + 1) rows of npair = k(k+1)/2 FP64 words (upper triangle, row-major packed); row N_e
+ * is Phi_D^T Phi_D over the Dirichlet DOFs (the identity part of the operator convention).
+ * Phi: FP64 N x k, ld. Hel: caller-owned, (N_e + 1) * npair FP64. 1 <= k <= 128. Compute once
+ * per basis; every later density needs only topo_rom_solve_elem. */
+topo_status topo_rom_elem(topo_ctx* ctx, const double* Phi, int k, int ld, double* Hel);
+
+/* Reduced solve from element reduced matrices: H(rho) = sum_e E(rho_e) Hel[e] + Hel[N_e] (a
+ * streaming, deterministic reduction over the elements), then the FP64 Cholesky solve of
+ * topo_rom_solve: H_work (k*k, on exit L), yhat[k], Jk (device scalar). */
+topo_status topo_rom_solve_elem(topo_ctx* ctx, const double* rho, const double* Hel, int k, const double* b,
+                                double* H_work, double* yhat, double* Jk);
+
 /* A posteriori residual (Section 3.3; the trust-region constraint of Eq. trcon-topopt):
  * u_k = Phi yhat, r = f - K(rho) u_k on the free DOFs, resnorm[0] = ||r||_2,
  * resnorm[1] = ||r||_2 / ||f||_2 (device FP64[2]). uk_opt (FP64[N], may be NULL) receives

@@ -413,6 +413,8 @@ struct topo_ctx {
   cudaStream_t stream;
   int device, num_sms;
   uint32_t* d_fixed_bits;
+  int* d_fixed_list;      // Dirichlet DOF indices, ascending
+  int nfixed;
   topo::KeQ4<double> q4_64;
   topo::KeQ4<float> q4_32, q4_bf;
   topo::KeH8<double> h8_64;

@@ -5,6 +5,7 @@
 #include <stdarg.h>
 #include <stdlib.h>
 
+#include <algorithm>
 #include <atomic>
 #include <vector>
 
@@ -367,6 +368,16 @@ extern "C" topo_status topo_create(const topo_problem* prob, void* cuda_stream, 
   }
   cudaMemcpy(c->d_fixed_bits, bits.data(), nwords * sizeof(uint32_t), cudaMemcpyHostToDevice);
   g.fixed_bits = c->d_fixed_bits;
+  std::vector<int> flist;
+  for (long long d = 0; d < ndof; ++d)
+    if (p.fixed_dof_mask[d]) flist.push_back((int)d);
+  c->nfixed = (int)flist.size();
+  e = cudaMalloc(&c->d_fixed_list, std::max<size_t>(1, flist.size()) * sizeof(int));
+  if (e != cudaSuccess) {
+    topo_destroy(c);
+    return TOPO_ERR_OOM;
+  }
+  if (!flist.empty()) cudaMemcpy(c->d_fixed_list, flist.data(), flist.size() * sizeof(int), cudaMemcpyHostToDevice);
 
   // element matrices in three arithmetic forms
   double K[576];
@@ -447,6 +458,7 @@ extern "C" topo_status topo_destroy(topo_ctx* c) {
   if (!c) return TOPO_OK;
   if (c->stream || true) cudaStreamSynchronize(c->stream);
   cudaFree(c->d_fixed_bits);
+  cudaFree(c->d_fixed_list);
   cudaFree(c->d_stencil_off);
   cudaFree(c->d_stencil_w);
   cudaFree(c->d_Hs);

@@ -477,11 +477,13 @@ __global__ void __launch_bounds__(TileShape<DIM>::NT) pcg_kernel(const __grid_co
     __syncthreads();
     worst = 0.0;
     conv = true;
+    bool stop = true;
     for (int c = 0; c < m; ++c) {
       worst = fmax(worst, sh_ff[c] > 0 ? sh_rr[c] / sh_ff[c] : 0.0);
-      conv = conv && sh_odone[c];
+      conv = conv && (sh_rr[c] <= a.rtol * a.rtol * sh_ff[c]);  // converged, not merely stopped
+      stop = stop && sh_odone[c];
     }
-    if (conv || outer >= a.max_outer || iters >= a.maxit) break;
+    if (stop || outer >= a.max_outer || iters >= a.maxit) break;
     // inner FP32 PCG on K d = r
     if (!inner_pcg(nullptr, 0, min(a.inner_cap, a.maxit - iters))) return;
     // Phase U: u += d on free DOFs

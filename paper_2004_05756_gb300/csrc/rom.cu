@@ -22,30 +22,33 @@ namespace topo {
 // ---------------------------------------------------------------------------------------
 // C = A^T B over N rows (A: N x k1, B: N x k2, column-major, leading dims lda, ldb), written as
 // per-CTA partial sums partial[blockIdx.x][i * k2 + j] (FP64). A CTA owns a contiguous row
-// range and one 64 x 64 output tile (blockIdx.y); each thread accumulates a 4 x 4 block.
+// range and one TILE x TILE output tile (blockIdx.y); its 256 threads each accumulate a
+// (TILE/16) x (TILE/16) block. TILE follows k (16, 32 or 64) so small bases waste no FMAs.
 // ---------------------------------------------------------------------------------------
-template <typename T>
+template <typename T, int TILE>
 __global__ void __launch_bounds__(256) atb_partial_kernel(const T* __restrict__ A, long long lda, int k1,
                                                           const T* __restrict__ B, long long ldb, int k2,
                                                           long long N, long long rows_per_cta, double* partial,
                                                           const int* gate) {
-  __shared__ T As[32][64 + 1];
+  constexpr int RB = 32;          // rows staged per pass
+  constexpr int PT = TILE / 16;   // outputs per thread per direction
+  __shared__ T As[RB][TILE + 1];
+  __shared__ T Bs[RB][TILE + 1];
   if (gate && *gate == 0) return;
-  __shared__ T Bs[32][64 + 1];
-  const int tiles_j = (k2 + 63) / 64;
+  const int tiles_j = (k2 + TILE - 1) / TILE;
   const int ti = blockIdx.y / tiles_j, tj = blockIdx.y % tiles_j;
-  const int i0 = ti * 64, j0 = tj * 64;
+  const int i0 = ti * TILE, j0 = tj * TILE;
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-  T acc[4][4];
+  T acc[PT][PT];
 #pragma unroll
-  for (int u = 0; u < 4; ++u)
+  for (int u = 0; u < PT; ++u)
 #pragma unroll
-    for (int v = 0; v < 4; ++v) acc[u][v] = (T)0;
+    for (int v = 0; v < PT; ++v) acc[u][v] = (T)0;
   const long long r_begin = blockIdx.x * rows_per_cta;
   const long long r_end = min(N, r_begin + rows_per_cta);
-  for (long long r0 = r_begin; r0 < r_end; r0 += 32) {
-    for (int idx = threadIdx.x; idx < 32 * 64; idx += 256) {
-      const int col = idx / 32, row = idx % 32;
+  for (long long r0 = r_begin; r0 < r_end; r0 += RB) {
+    for (int idx = threadIdx.x; idx < RB * TILE; idx += 256) {
+      const int col = idx / RB, row = idx % RB;
       const long long r = r0 + row;
       const bool rin = r < r_end;
       As[row][col] = (rin && i0 + col < k1) ? A[(long long)(i0 + col) * lda + r] : (T)0;
@@ -53,25 +56,25 @@ __global__ void __launch_bounds__(256) atb_partial_kernel(const T* __restrict__ 
     }
     __syncthreads();
 #pragma unroll 8
-    for (int row = 0; row < 32; ++row) {
-      T av[4], bv[4];
+    for (int row = 0; row < RB; ++row) {
+      T av[PT], bv[PT];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) av[u] = As[row][ty * 4 + u];
+      for (int u = 0; u < PT; ++u) av[u] = As[row][ty * PT + u];
 #pragma unroll
-      for (int v = 0; v < 4; ++v) bv[v] = Bs[row][tx * 4 + v];
+      for (int v = 0; v < PT; ++v) bv[v] = Bs[row][tx * PT + v];
 #pragma unroll
-      for (int u = 0; u < 4; ++u)
+      for (int u = 0; u < PT; ++u)
 #pragma unroll
-        for (int v = 0; v < 4; ++v) acc[u][v] = fma(av[u], bv[v], acc[u][v]);
+        for (int v = 0; v < PT; ++v) acc[u][v] = fma(av[u], bv[v], acc[u][v]);
     }
     __syncthreads();
   }
   double* out = partial + (size_t)blockIdx.x * k1 * k2;
 #pragma unroll
-  for (int u = 0; u < 4; ++u)
+  for (int u = 0; u < PT; ++u)
 #pragma unroll
-    for (int v = 0; v < 4; ++v) {
-      const int i = i0 + ty * 4 + u, j = j0 + tx * 4 + v;
+    for (int v = 0; v < PT; ++v) {
+      const int i = i0 + ty * PT + u, j = j0 + tx * PT + v;
       if (i < k1 && j < k2) out[i * k2 + j] = (double)acc[u][v];
     }
 }
@@ -302,9 +305,16 @@ static topo_status launch_atb(topo_ctx* c, const T* A, long long lda, int k1, co
   RowSplit rs = row_split(c, N, 2);
   size_t need = (size_t)rs.G * k1 * k2;
   if (need > partial_cap) return fail(c, TOPO_ERR_INVALID, "internal: atb partial buffer too small");
-  const int tiles = ((k1 + 63) / 64) * ((k2 + 63) / 64);
-  atb_partial_kernel<T><<<dim3(rs.G, tiles), 256, 0, c->stream>>>(A, lda, k1, B, ldb, k2, N, rs.rows, partial_buf,
-                                                                    gate);
+  const int kmax = std::max(k1, k2);
+  if (kmax <= 16) {
+    atb_partial_kernel<T, 16><<<dim3(rs.G, 1), 256, 0, c->stream>>>(A, lda, k1, B, ldb, k2, N, rs.rows, partial_buf, gate);
+  } else if (kmax <= 32) {
+    atb_partial_kernel<T, 32><<<dim3(rs.G, 1), 256, 0, c->stream>>>(A, lda, k1, B, ldb, k2, N, rs.rows, partial_buf, gate);
+  } else {
+    const int tiles = ((k1 + 63) / 64) * ((k2 + 63) / 64);
+    atb_partial_kernel<T, 64><<<dim3(rs.G, tiles), 256, 0, c->stream>>>(A, lda, k1, B, ldb, k2, N, rs.rows, partial_buf,
+                                                                        gate);
+  }
   note_launch();
   atb_final_kernel<<<(k1 * k2 + 255) / 256, 256, 0, c->stream>>>(partial_buf, rs.G, k1, k2, C, sym, gate);
   note_launch();
@@ -373,6 +383,28 @@ static size_t project_scratch(topo_ctx* c, int k, long long ld, topo_prec prec) 
   else
     s += 2 * (size_t)N * k * sizeof(float);
   return s + 256;
+}
+
+// FP64 Cholesky of H_work (overwritten with L), yhat = H^{-1} b, Jk = b^T yhat. A non-positive
+// pivot sets TOPO_ERR_NOT_SPD in the device status and writes NaN.
+topo_status reduced_solve(topo_ctx* c, int k, const double* b, double* H_work, double* yhat, double* Jk) {
+  topo_status s = ensure_red(c, 256);
+  if (s) return s;
+  int* ok = (int*)c->d_red;
+  const size_t sm_chol = (size_t)k * k * sizeof(double);
+  const size_t sm_solve = sm_chol + k * sizeof(double);
+  if (sm_solve > 48 * 1024) {
+    TOPO_CUDA_TRY(c, cudaFuncSetAttribute(cholesky_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_solve));
+    TOPO_CUDA_TRY(c, cudaFuncSetAttribute(chol_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_solve));
+  }
+  cholesky_kernel<<<1, 256, sm_chol, c->stream>>>(H_work, k, &c->d_sync->status, ok, nullptr);
+  note_launch();
+  chol_solve_kernel<<<1, 128, sm_solve, c->stream>>>(H_work, k, b, yhat, 0, ok, nullptr);
+  note_launch();
+  dot_small_kernel<<<1, 128, 0, c->stream>>>(b, yhat, k, Jk);
+  note_launch();
+  TOPO_CUDA_TRY(c, cudaGetLastError());
+  return TOPO_OK;
 }
 
 }  // namespace topo

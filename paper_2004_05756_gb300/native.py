@@ -25,7 +25,8 @@ PREC = {"fp64": TOPO_FP64, "fp32": TOPO_FP32_REFINED, "fp32_bf16ke": TOPO_FP32_B
 # Every entry point declared in include/topo.h (checked by the tests).
 EXPORTS = ["topo_create", "topo_destroy", "topo_last_error", "topo_set_param", "topo_check", "topo_sizes",
            "topo_filter", "topo_apply_K", "topo_solve_hdm", "topo_rom_build", "topo_rom_solve",
-           "topo_rom_error", "topo_compliance_grad", "topo_launch_count"]
+           "topo_rom_error", "topo_compliance_grad", "topo_launch_count", "topo_rom_elem",
+           "topo_rom_solve_elem"]
 
 
 class TopoError(RuntimeError):
@@ -73,6 +74,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "topo_rom_error": ([P, P, P, I, I, P, P, P, P], I),
         "topo_compliance_grad": ([P, P, P, I, I, P, P, P, P], I),
         "topo_launch_count": ([ctypes.POINTER(LL)], I),
+        "topo_rom_elem": ([P, P, I, I, P], I),
+        "topo_rom_solve_elem": ([P, P, P, I, P, P, P, P], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -179,6 +182,15 @@ class Topo:
         ld = _ld(Phi, self.N)
         self._chk(self.lib.topo_rom_solve(self.h, _ptr(rho), _ptr(Phi), int(k), ld, _ptr(b), _ptr(H_work),
                                           _ptr(yhat), _ptr(Jk), PREC[prec]), "topo_rom_solve")
+
+    def topo_rom_elem(self, Phi, k: int, Hel):
+        ld = _ld(Phi, self.N)
+        self._chk(self.lib.topo_rom_elem(self.h, _ptr(Phi), int(k), ld, _ptr(Hel)), "topo_rom_elem")
+        return Hel
+
+    def topo_rom_solve_elem(self, rho, Hel, k: int, b, H_work, yhat, Jk):
+        self._chk(self.lib.topo_rom_solve_elem(self.h, _ptr(rho), _ptr(Hel), int(k), _ptr(b), _ptr(H_work),
+                                               _ptr(yhat), _ptr(Jk)), "topo_rom_solve_elem")
 
     def topo_rom_error(self, rho, Phi, k: int, yhat, f, resnorm, uk=None):
         ld = _ld(Phi, self.N)
