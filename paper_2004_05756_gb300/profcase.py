@@ -1,0 +1,103 @@
+"""Run one hot libtopo call on a named workload, a few times, for profiler captures.
+
+    python -m paper_2004_05756_gb300.profcase --call pcg --prec fp64 --maxit 200
+    python -m paper_2004_05756_gb300.profcase --call apply --prec fp32 --m 64
+    python -m paper_2004_05756_gb300.profcase --call rom_solve_elem --k 16
+
+Workloads are the seeded benchmark problems (MBB 600x200 Q4 by default). Prints the mean
+CUDA-event time of the call, measured after one warm-up call.
+"""
+from __future__ import annotations
+
+import argparse
+import os
+import sys
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--call", required=True, choices=["pcg", "apply", "rom_elem", "rom_solve_elem", "rom_solve",
+                                                      "rom_error", "grad", "filter"])
+    ap.add_argument("--shape", default="600x200")
+    ap.add_argument("--prec", default="fp64")
+    ap.add_argument("--m", type=int, default=1)
+    ap.add_argument("--k", type=int, default=16)
+    ap.add_argument("--maxit", type=int, default=200)
+    ap.add_argument("--reps", type=int, default=3)
+    a = ap.parse_args(argv)
+    import torch
+
+    from paper_2004_05756_gb300 import build, native
+    from paper_2004_05756_gb300 import workloads as w
+
+    build.build()
+    dims = [int(x) for x in a.shape.split("x")]
+    p = w.mbb_2d(*dims) if len(dims) == 2 else w.cantilever_3d(*dims)
+    T = native.Topo(p)
+    f64 = dict(dtype=torch.float64, device="cuda")
+    psi = torch.as_tensor(w.design_field(p, 0)).to(**f64)
+    rho = torch.empty(p.nel, **f64)
+    T.topo_filter(psi, rho)
+    F = torch.as_tensor(p.F.T.copy()).to(**f64)
+    rng = np.random.default_rng(0)
+    k = a.k
+    Phi = None
+    if a.call.startswith("rom"):
+        Q, _ = np.linalg.qr(rng.standard_normal((p.ndof, k)))
+        Q[p.fixed == 1] = 0.0
+        Phi = torch.as_tensor(Q.T.copy()).to(**f64)
+        Hel = torch.zeros((p.nel + 1) * k * (k + 1) // 2, **f64)
+        b = torch.as_tensor(Q.T @ p.F[:, 0]).to(**f64)
+        Hw = torch.zeros(k * k, **f64)
+        y = torch.zeros(k, **f64)
+        Jk = torch.zeros(1, **f64)
+        rn = torch.zeros(2, **f64)
+        if a.call != "rom_elem":
+            T.topo_rom_elem(Phi, k, Hel)
+    dt = torch.float64 if a.prec == "fp64" else torch.float32
+    V = torch.randn((a.m, p.ndof), dtype=dt, device="cuda")
+    Y = torch.empty_like(V)
+    U = torch.zeros((1, p.ndof), **f64)
+    J = torch.zeros(1, **f64)
+    dc = torch.empty(p.nel, **f64)
+    dp = torch.empty(p.nel, **f64)
+
+    def call():
+        if a.call == "pcg":
+            U.zero_()
+            T.topo_solve_hdm(rho, F, U, rtol=1e-30, maxit=a.maxit, prec=a.prec, info=False)
+        elif a.call == "apply":
+            T.topo_apply_K(rho, V, Y, a.prec)
+        elif a.call == "rom_elem":
+            T.topo_rom_elem(Phi, k, Hel)
+        elif a.call == "rom_solve_elem":
+            T.topo_rom_solve_elem(rho, Hel, k, b, Hw, y, Jk)
+        elif a.call == "rom_solve":
+            T.topo_rom_solve(rho, Phi, k, b, Hw, y, Jk, a.prec)
+        elif a.call == "rom_error":
+            T.topo_rom_error(rho, Phi, k, y, F[0], rn)
+        elif a.call == "grad":
+            T.topo_compliance_grad(rho, F, F, J, dc, dp)
+        elif a.call == "filter":
+            T.topo_filter(psi, rho)
+
+    call()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(a.reps):
+        call()
+    e1.record()
+    e1.synchronize()
+    print(f"{a.call} {a.prec} shape={a.shape} m={a.m} k={k}: {e0.elapsed_time(e1) / a.reps * 1e3:.1f} us/call")
+    T.topo_check()
+
+
+if __name__ == "__main__":
+    main()
