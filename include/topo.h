@@ -165,6 +165,20 @@ topo_status topo_rom_elem(topo_ctx* ctx, const double* Phi, int k, int ld, doubl
 topo_status topo_rom_solve_elem(topo_ctx* ctx, const double* rho, const double* Hel, int k, const double* b,
                                 double* H_work, double* yhat, double* Jk);
 
+/* topo_rom_solve_elem without any device allocation. The paper has no counterpart: this
+ * entry exists for callers that cannot allocate device memory when they need a reduced solve
+ * (a serving loop whose memory budget belongs to an outside allocator, code running while
+ * another component holds the device pool, or a latency-critical loop that cannot accept the
+ * implicit device synchronisation of cudaMalloc/cudaFree). Same arguments and results as
+ * topo_rom_solve_elem, with 1 <= k <= 64. Its scratch is one fixed 8 MiB device array inside the
+ * library (kept by every GPU that loads the library until the process exits); a problem that
+ * needs more (about N_e + 1 + 2 * SMs * k(k+1)/2 doubles) is rejected with TOPO_ERR_INVALID and
+ * a message. The first call on each device looks up the array's device address; make that
+ * first call before any stream capture. All calls share the array, so calls that overlap on
+ * the GPU (other streams, other contexts, other host threads) race: serialise them. */
+topo_status topo_rom_solve_elem_noalloc(topo_ctx* ctx, const double* rho, const double* Hel, int k,
+                                        const double* b, double* H_work, double* yhat, double* Jk);
+
 /* A posteriori residual (Section 3.3; the trust-region constraint of Eq. trcon-topopt):
  * u_k = Phi yhat, r = f - K(rho) u_k on the free DOFs, resnorm[0] = ||r||_2,
  * resnorm[1] = ||r||_2 / ||f||_2 (device FP64[2]). uk_opt (FP64[N], may be NULL) receives

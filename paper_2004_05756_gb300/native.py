@@ -26,7 +26,7 @@ PREC = {"fp64": TOPO_FP64, "fp32": TOPO_FP32_REFINED, "fp32_bf16ke": TOPO_FP32_B
 EXPORTS = ["topo_create", "topo_destroy", "topo_last_error", "topo_set_param", "topo_check", "topo_sizes",
            "topo_filter", "topo_apply_K", "topo_solve_hdm", "topo_rom_build", "topo_rom_solve",
            "topo_rom_error", "topo_compliance_grad", "topo_launch_count", "topo_rom_elem",
-           "topo_rom_solve_elem"]
+           "topo_rom_solve_elem", "topo_rom_solve_elem_noalloc"]
 
 
 class TopoError(RuntimeError):
@@ -76,6 +76,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "topo_launch_count": ([ctypes.POINTER(LL)], I),
         "topo_rom_elem": ([P, P, I, I, P], I),
         "topo_rom_solve_elem": ([P, P, P, I, P, P, P, P], I),
+        "topo_rom_solve_elem_noalloc": ([P, P, P, I, P, P, P, P], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -191,6 +192,10 @@ class Topo:
     def topo_rom_solve_elem(self, rho, Hel, k: int, b, H_work, yhat, Jk):
         self._chk(self.lib.topo_rom_solve_elem(self.h, _ptr(rho), _ptr(Hel), int(k), _ptr(b), _ptr(H_work),
                                                _ptr(yhat), _ptr(Jk)), "topo_rom_solve_elem")
+
+    def topo_rom_solve_elem_noalloc(self, rho, Hel, k: int, b, H_work, yhat, Jk):
+        self._chk(self.lib.topo_rom_solve_elem_noalloc(self.h, _ptr(rho), _ptr(Hel), int(k), _ptr(b), _ptr(H_work),
+                                                       _ptr(yhat), _ptr(Jk)), "topo_rom_solve_elem_noalloc")
 
     def topo_rom_error(self, rho, Phi, k: int, yhat, f, resnorm, uk=None):
         ld = _ld(Phi, self.N)
