@@ -440,6 +440,7 @@ struct topo_ctx {
   int rom_refine;
   int pcg_blocks_per_sm;
   int inner_cap;
+  int hdm_kernel;  // 0: assembled-stencil Chronopoulos-Gear PCG (FP64); 1: element-form PCG
   char err[512];
 };
 

@@ -337,6 +337,7 @@ extern "C" topo_status topo_create(const topo_problem* prob, void* cuda_stream, 
   c->rom_refine = 8;
   c->pcg_blocks_per_sm = 0;
   c->inner_cap = 2000;
+  c->hdm_kernel = 0;
   cudaGetDevice(&c->device);
   cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
   if (c->num_sms <= 0) c->num_sms = 1;
@@ -495,6 +496,10 @@ extern "C" topo_status topo_set_param(topo_ctx* c, topo_param which, double v) {
     case TOPO_PARAM_INNER_CAP:
       if (!(v >= 1 && v <= 1e7)) return fail(c, TOPO_ERR_INVALID, "inner cap must be in [1,1e7]");
       c->inner_cap = (int)v;
+      return TOPO_OK;
+    case TOPO_PARAM_HDM_KERNEL:
+      if (!(v == 0 || v == 1)) return fail(c, TOPO_ERR_INVALID, "hdm kernel must be 0 or 1");
+      c->hdm_kernel = (int)v;
       return TOPO_OK;
     case TOPO_PARAM_PCG_BLOCKS_PER_SM:
       if (!(v >= 0 && v <= 8)) return fail(c, TOPO_ERR_INVALID, "blocks per SM must be in [0,8]");

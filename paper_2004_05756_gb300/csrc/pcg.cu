@@ -21,6 +21,10 @@ namespace topo {
 
 constexpr int PCG_MAX_COLS = 32;
 
+template <int DIM>
+topo_status solve_stencil_fp64(topo_ctx* c, const double* rho, const double* F, double* U, int m, int ld, double rtol,
+                               int maxit, topo_solve_info* info_host);
+
 #ifdef TOPO_BOUNDS_CHECK
 // Debug builds only: host-mapped progress record written by block 0 (phase, iteration).
 static __device__ volatile int* g_progress = nullptr;
@@ -612,7 +616,9 @@ static topo_status solve_impl(topo_ctx* c, const double* rho, const double* F, d
       memset(&sub, 0, sizeof(sub));
       const typename KeOf<DIM, double>::type& ke64 = *reinterpret_cast<const typename KeOf<DIM, double>::type*>(
           DIM == 2 ? (const void*)&c->q4_64 : (const void*)&c->h8_64);
-      topo_status st2 = solve_impl<DIM, double>(c, rho, F, U, m, ld, rtol, maxit - hinfo[0], ke64, 1.0, &sub);
+      topo_status st2 = c->hdm_kernel == 0
+                            ? solve_stencil_fp64<DIM>(c, rho, F, U, m, ld, rtol, maxit - hinfo[0], &sub)
+                            : solve_impl<DIM, double>(c, rho, F, U, m, ld, rtol, maxit - hinfo[0], ke64, 1.0, &sub);
       if (info_host) {
         info_host->iters = hinfo[0] + sub.iters;
         info_host->outer = hinfo[1];
@@ -675,6 +681,10 @@ extern "C" topo_status topo_solve_hdm(topo_ctx* c, const double* rho, const doub
   if (!dev_ptr_ok(rho) || !dev_ptr_ok(F) || !dev_ptr_ok(U) || F == U)
     return fail(c, TOPO_ERR_INVALID, "topo_solve_hdm: null, misaligned or aliased pointer");
   if (info_host) memset(info_host, 0, sizeof(*info_host));
+  if (prec == TOPO_FP64 && c->hdm_kernel == 0) {
+    if (c->g.dim == 2) return solve_stencil_fp64<2>(c, rho, F, U, m, ld, rtol, maxit, info_host);
+    return solve_stencil_fp64<3>(c, rho, F, U, m, ld, rtol, maxit, info_host);
+  }
   if (c->g.dim == 2) {
     if (prec == TOPO_FP64) return solve_impl<2, double>(c, rho, F, U, m, ld, rtol, maxit, c->q4_64, 1.0, info_host);
     if (prec == TOPO_FP32_REFINED)

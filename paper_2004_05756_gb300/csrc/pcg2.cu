@@ -1,0 +1,463 @@
+// FP64 state solve K(rho) u = f with K assembled per node, Chronopoulos-Gear PCG, one persistent
+// cooperative launch.
+//
+// GB300's FP64 rate is 1/61 of its FP32 rate, so in FP64 the element-by-element product
+// (72 FMAs per node in 2D, 600 in 3D) is the bottleneck of every CG iteration. The density is
+// fixed during a solve, so this kernel first assembles the stencil of K(rho) once per node:
+// for each of the 3^d neighbour offsets a dim x dim block sum_e E(rho_e) K_e[node, neighbour],
+// stored structure-of-arrays (coefficient-major, node fastest) so that warps read it coalesced.
+// Every CG iteration then costs 36 (2D) / 243 (3D) FMAs per node instead of 72 / 600. The
+// Dirichlet convention (identity rows and columns) is folded into the stencil.
+//
+// Work split: a unit is 32 consecutive nodes of one x-row, one warp. Each CTA owns a contiguous,
+// equal share of the units (balanced to one unit), so partial sums are accumulated in a fixed
+// order and every result is deterministic. Each iteration has two grid-wide barriers with the
+// reductions folded in (Chronopoulos-Gear: both dot products of an iteration in one pass).
+#include <algorithm>
+#include <type_traits>
+
+#include "common.cuh"
+
+namespace topo {
+
+constexpr int P2_MAX_COLS = 32;
+constexpr int P2_THREADS = 256;
+
+template <int DIM>
+struct Pcg2Args {
+  Grid g;
+  typename KeOf<DIM, double>::type ke;
+  const double* rho;
+  const double* F;
+  double* U;
+  long long ld;
+  int m;
+  long long N;       // scratch leading dimension (= ndof)
+  long long nunits;  // ceil(nnx / 32) * nny * nnz
+  double* C;         // [NB*DIM*DIM][nnodes]
+  double* dinv;      // [N]
+  double* r;         // N x m
+  double* z;
+  double* w;
+  double* p;
+  double* s;
+  double* partial;
+  double* result;
+  GridSync* gs;
+  double rtol;
+  int maxit;
+  long long wait_cycles;
+  int* info;
+  double* info_rr;
+};
+
+template <int DIM>
+struct StencilGeom {
+  static constexpr int NB = DIM == 2 ? 9 : 27;
+  static constexpr int NC = NB * DIM * DIM;  // coefficients per node
+};
+
+__device__ __forceinline__ void unit_coords(const Grid& g, long long u, int& i0, int& j, int& kz) {
+  const int ux = (g.nnx + 31) / 32;
+  i0 = (int)(u % ux) * 32;
+  const long long r = u / ux;
+  j = (int)(r % g.nny);
+  kz = (int)(r / g.nny);
+}
+
+// Assemble the stencil rows of node (i, j, k). Element (a, b, c) in {0,1}^d has its lower
+// corner at node - 1 + (a, b, c); the node is its local corner (1-a, 1-b, 1-c), and the
+// neighbour at offset (dx, dy, dz) is its local corner (dx+1-a, dy+1-b, dz+1-c) when that lies
+// in {0,1}^d. Each neighbour block sums E_e K_e[node rows, neighbour columns] over those
+// elements. Dirichlet convention: a fixed row is the identity, a fixed neighbour column zero.
+template <int DIM>
+__device__ void assemble_node(const Grid& g, const typename KeOf<DIM, double>::type& ke, const double* rho,
+                              int i, int j, int k, long long n, double* C) {
+  constexpr int NB = StencilGeom<DIM>::NB, ND = DIM == 2 ? 8 : 24, NE = DIM == 2 ? 4 : 8;
+  double E[NE];
+#pragma unroll
+  for (int q = 0; q < NE; ++q) {
+    const int a = q & 1, b = (q >> 1) & 1, c = q >> 2;
+    const int ei = i - 1 + a, ej = j - 1 + b, ek = k - 1 + c;
+    const bool in = ei >= 0 && ei < g.nx && ej >= 0 && ej < g.ny && (DIM == 2 || (ek >= 0 && ek < g.nz));
+    const long long e = in ? ei + (long long)g.nx * (ej + (long long)g.ny * (DIM == 3 ? ek : 0)) : 0;
+    E[q] = in ? young<double>(__ldg(rho + e), g.E0, g.Emin, g.ipenal) : 0.0;
+  }
+  const int centre = DIM == 2 ? 4 : 13;
+  bool rfix[DIM];
+#pragma unroll
+  for (int r = 0; r < DIM; ++r) rfix[r] = is_fixed(g, DIM * n + r);
+#pragma unroll 1
+  for (int nb = 0; nb < NB; ++nb) {
+    const int dx = nb % 3 - 1, dy = (nb / 3) % 3 - 1, dz = DIM == 3 ? nb / 9 - 1 : 0;
+    double acc[DIM * DIM];
+#pragma unroll
+    for (int q = 0; q < DIM * DIM; ++q) acc[q] = 0.0;
+#pragma unroll
+    for (int q = 0; q < NE; ++q) {
+      const int a = q & 1, b = (q >> 1) & 1, c = q >> 2;
+      const int cx = dx + 1 - a, cy = dy + 1 - b, cz = DIM == 3 ? dz + 1 - c : 0;
+      if (cx < 0 || cx > 1 || cy < 0 || cy > 1 || cz < 0 || cz > 1) continue;
+      const int L = DIM == 2 ? lidx2(1 - a, 1 - b) : lidx3(1 - a, 1 - b, 1 - c);
+      const int M = DIM == 2 ? lidx2(cx, cy) : lidx3(cx, cy, cz);
+#pragma unroll
+      for (int r = 0; r < DIM; ++r)
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) acc[r * DIM + d] = fma(E[q], ke.k[(DIM * L + r) * ND + DIM * M + d], acc[r * DIM + d]);
+    }
+    const int ii = i + dx, jj = j + dy, kk = k + dz;
+    const bool nin = ii >= 0 && ii < g.nnx && jj >= 0 && jj < g.nny && (DIM == 2 || (kk >= 0 && kk < g.nnz));
+    const long long m = nin ? ii + (long long)g.nnx * (jj + (long long)g.nny * kk) : 0;
+#pragma unroll
+    for (int r = 0; r < DIM; ++r)
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) {
+        double v = acc[r * DIM + d];
+        if (!nin || is_fixed(g, DIM * m + d)) v = 0.0;
+        if (rfix[r]) v = (nb == centre && r == d) ? 1.0 : 0.0;
+        C[(long long)((nb * DIM + r) * DIM + d) * g.nnodes + n] = v;
+      }
+  }
+}
+
+// y = C v for node (i, j, k); neighbour values read from L2 (written by other CTAs).
+template <int DIM>
+__device__ __forceinline__ void stencil_apply(const Grid& g, const double* __restrict__ C, const double* v, int i,
+                                              int j, int k, long long n, double* y) {
+  constexpr int NB = StencilGeom<DIM>::NB;
+#pragma unroll
+  for (int r = 0; r < DIM; ++r) y[r] = 0.0;
+#pragma unroll
+  for (int nb = 0; nb < NB; ++nb) {
+    const int dx = nb % 3 - 1, dy = (nb / 3) % 3 - 1, dz = DIM == 3 ? nb / 9 - 1 : 0;
+    const int ii = i + dx, jj = j + dy, kk = k + dz;
+    const bool nin = ii >= 0 && ii < g.nnx && jj >= 0 && jj < g.nny && (DIM == 2 || (kk >= 0 && kk < g.nnz));
+    if (!nin) continue;
+    const long long m = ii + (long long)g.nnx * (jj + (long long)g.nny * kk);
+    double vv[DIM];
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) vv[d] = __ldcg(v + DIM * m + d);
+#pragma unroll
+    for (int r = 0; r < DIM; ++r)
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) y[r] = fma(__ldg(C + (long long)((nb * DIM + r) * DIM + d) * g.nnodes + n), vv[d], y[r]);
+  }
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(P2_THREADS) pcg2_kernel(const __grid_constant__ Pcg2Args<DIM> a) {
+  __shared__ double red[32];
+  __shared__ double sh_gamma[P2_MAX_COLS], sh_alpha[P2_MAX_COLS], sh_beta[P2_MAX_COLS], sh_tol2[P2_MAX_COLS],
+      sh_ff[P2_MAX_COLS], sh_rr[P2_MAX_COLS];
+  __shared__ int sh_done[P2_MAX_COLS];
+  const Grid& g = a.g;
+  const int m = a.m;
+  const unsigned G = gridDim.x;
+  const long long N = a.N;
+  GridSync* gs = a.gs;
+  unsigned my_gen = *(volatile unsigned*)&gs->gen;
+  double* part = a.partial;
+  auto P = [&](int slot, int c) -> double* { return part + ((size_t)(slot * m + c)) * G + blockIdx.x; };
+  auto R = [&](int slot, int c) -> double { return __ldcg(a.result + slot * m + c); };
+  // this CTA's units: a contiguous, balanced range
+  const long long u0 = a.nunits * blockIdx.x / G, u1 = a.nunits * (blockIdx.x + 1) / G;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  // iterate over the owned nodes of this CTA: fn(i, j, k, n)
+  auto for_owned = [&](auto fn) {
+    for (long long u = u0 + warp; u < u1; u += nwarps) {
+      int i0, j, kz;
+      unit_coords(g, u, i0, j, kz);
+      const int i = i0 + lane;
+      if (i >= g.nnx) continue;
+      const long long n = i + (long long)g.nnx * (j + (long long)g.nny * kz);
+      fn(i, j, kz, n);
+    }
+  };
+
+  // --- stencil assembly and Jacobi diagonal ----------------------------------------------
+  for_owned([&](int i, int j, int k, long long n) {
+    assemble_node<DIM>(g, a.ke, a.rho, i, j, k, n, a.C);
+    const int centre = DIM == 2 ? 4 : 13;
+#pragma unroll
+    for (int r = 0; r < DIM; ++r) {
+      const double d = a.C[(long long)((centre * DIM + r) * DIM + r) * g.nnodes + n];
+      a.dinv[DIM * n + r] = 1.0 / d;
+    }
+  });
+  if (!grid_sync_reduce(gs, my_gen, part, a.result, 0, a.wait_cycles)) return;
+
+  // --- true residual r = f - K x, z = D^-1 r, w = K z (two phases) ------------------------
+  // Phase T1: r, z for owned nodes (x = caller's U, Dirichlet entries zeroed), partial gamma,
+  // r.r, f.f.
+  auto true_residual = [&](bool first) -> bool {
+    double acc[3][P2_MAX_COLS];
+    for (int c = 0; c < m; ++c) acc[0][c] = acc[1][c] = acc[2][c] = 0.0;
+    for (int c = 0; c < m; ++c) {
+      double* x = a.U + c * a.ld;
+      const double* f = a.F + c * a.ld;
+      for_owned([&](int i, int j, int k, long long n) {
+        double y[DIM];
+        stencil_apply<DIM>(g, a.C, x, i, j, k, n, y);
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) {
+          const long long dof = DIM * n + d;
+          double rv = 0.0;
+          if (!is_fixed(g, dof)) {
+            const double fv = f[dof];
+            rv = fv - y[d];
+            acc[1][c] = fma(rv, rv, acc[1][c]);
+            acc[2][c] = fma(fv, fv, acc[2][c]);
+          } else if (first) {
+            x[dof] = 0.0;  // Dirichlet entries of the solution are zero (their columns are zero)
+          }
+          const double zv = __ldg(a.dinv + dof) * rv;
+          a.r[c * N + dof] = rv;
+          a.z[c * N + dof] = zv;
+          acc[0][c] = fma(rv, zv, acc[0][c]);
+        }
+      });
+    }
+    for (int c = 0; c < m; ++c)
+      for (int q = 0; q < 3; ++q) {
+        const double t = block_sum(acc[q][c], red);
+        if (threadIdx.x == 0) *P(q, c) = t;
+      }
+    if (!grid_sync_reduce(gs, my_gen, part, a.result, 3 * m, a.wait_cycles)) return false;
+    if (threadIdx.x == 0) {
+      for (int c = 0; c < m; ++c) {
+        sh_gamma[c] = R(0, c);
+        sh_rr[c] = R(1, c);
+        if (first) sh_ff[c] = R(2, c);
+        sh_tol2[c] = a.rtol * a.rtol * sh_ff[c];
+        sh_done[c] = sh_rr[c] <= sh_tol2[c];
+      }
+    }
+    __syncthreads();
+    return true;
+  };
+
+  // Phase W: w = K z for owned nodes, partial delta = w.z; then alpha (first step: beta = 0).
+  auto phase_w = [&](bool restart) -> bool {
+    double acc[P2_MAX_COLS];
+    for (int c = 0; c < m; ++c) acc[c] = 0.0;
+    for (int c = 0; c < m; ++c) {
+      if (sh_done[c]) continue;
+      const double* zc = a.z + c * N;
+      for_owned([&](int i, int j, int k, long long n) {
+        double y[DIM];
+        stencil_apply<DIM>(g, a.C, zc, i, j, k, n, y);
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) {
+          const long long dof = DIM * n + d;
+          a.w[c * N + dof] = y[d];
+          acc[c] = fma(y[d], __ldcg(zc + dof), acc[c]);
+        }
+      });
+    }
+    for (int c = 0; c < m; ++c) {
+      const double t = block_sum(acc[c], red);
+      if (threadIdx.x == 0) *P(0, c) = t;
+    }
+    if (!grid_sync_reduce(gs, my_gen, part, a.result, m, a.wait_cycles)) return false;
+    if (threadIdx.x == 0) {
+      for (int c = 0; c < m; ++c) {
+        if (sh_done[c]) continue;
+        const double delta = R(0, c);
+        if (restart) {
+          sh_beta[c] = 0.0;
+          sh_alpha[c] = sh_gamma[c] / delta;
+        } else {
+          const double den = delta - sh_beta[c] * sh_gamma[c] / sh_alpha[c];
+          sh_alpha[c] = sh_gamma[c] / den;
+        }
+        if (!(sh_alpha[c] > 0.0) || !isfinite(sh_alpha[c])) {
+          set_status(&gs->status, TOPO_ERR_NOT_SPD);
+          sh_done[c] = 1;
+        }
+      }
+    }
+    __syncthreads();
+    return true;
+  };
+
+  // Phase U: p = z + beta p, s = w + beta s, x += alpha p, r -= alpha s, z = D^-1 r; partial
+  // gamma = r.z and r.r; then beta for the next step.
+  auto phase_u = [&](bool restart) -> bool {
+    double accg[P2_MAX_COLS], accr[P2_MAX_COLS];
+    for (int c = 0; c < m; ++c) accg[c] = accr[c] = 0.0;
+    for (int c = 0; c < m; ++c) {
+      if (sh_done[c]) continue;
+      const double al = sh_alpha[c], be = restart ? 0.0 : sh_beta[c];
+      double* x = a.U + c * a.ld;
+      for_owned([&](int i, int j, int k, long long n) {
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) {
+          const long long dof = DIM * n + d, o = c * N + dof;
+          // on a restart p and s hold stale (possibly non-finite) data: take z and w exactly
+          const double pv = restart ? a.z[o] : fma(be, a.p[o], a.z[o]);
+          const double sv = restart ? a.w[o] : fma(be, a.s[o], a.w[o]);
+          a.p[o] = pv;
+          a.s[o] = sv;
+          x[dof] = fma(al, pv, x[dof]);
+          const double rv = fma(-al, sv, a.r[o]);
+          const double zv = __ldg(a.dinv + dof) * rv;
+          a.r[o] = rv;
+          a.z[o] = zv;
+          accg[c] = fma(rv, zv, accg[c]);
+          accr[c] = fma(rv, rv, accr[c]);
+        }
+      });
+    }
+    for (int c = 0; c < m; ++c) {
+      const double t1 = block_sum(accg[c], red);
+      const double t2 = block_sum(accr[c], red);
+      if (threadIdx.x == 0) {
+        *P(0, c) = t1;
+        *P(1, c) = t2;
+      }
+    }
+    if (!grid_sync_reduce(gs, my_gen, part, a.result, 2 * m, a.wait_cycles)) return false;
+    if (threadIdx.x == 0) {
+      for (int c = 0; c < m; ++c) {
+        if (sh_done[c]) continue;
+        const double gnew = R(0, c);
+        sh_beta[c] = gnew / sh_gamma[c];
+        sh_gamma[c] = gnew;
+        sh_rr[c] = R(1, c);
+        if (sh_rr[c] <= sh_tol2[c]) sh_done[c] = 1;
+      }
+    }
+    __syncthreads();
+    return true;
+  };
+
+  int iters = 0;
+  if (!true_residual(true)) return;
+  for (int rep = 0; rep < 50; ++rep) {
+    bool all = true;
+    for (int c = 0; c < m; ++c) all = all && sh_done[c];
+    if (all || iters >= a.maxit) break;
+    bool restart = true;
+    while (iters < a.maxit) {
+      bool any = false;
+      for (int c = 0; c < m; ++c) any = any || !sh_done[c];
+      if (!any) break;
+      if (!phase_w(restart)) return;
+      if (!phase_u(restart)) return;
+      restart = false;
+      ++iters;
+    }
+    if (!true_residual(false)) return;  // residual replacement: restart from the true residual
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    double worst = 0.0;
+    bool conv = true;
+    for (int c = 0; c < m; ++c) {
+      worst = fmax(worst, sh_ff[c] > 0 ? sh_rr[c] / sh_ff[c] : 0.0);
+      conv = conv && (sh_rr[c] <= sh_tol2[c]);
+    }
+    a.info[0] = iters;
+    a.info[1] = 0;
+    a.info[2] = conv ? 0 : TOPO_ERR_NOT_CONVERGED;
+    a.info[3] = 0;
+    a.info_rr[0] = worst;
+  }
+}
+
+template <int DIM>
+topo_status solve_stencil_fp64(topo_ctx* c, const double* rho, const double* F, double* U, int m, int ld, double rtol,
+                               int maxit, topo_solve_info* info_host) {
+  const Grid& g = c->g;
+  const long long N = g.ndof;
+  const long long nunits = (long long)((g.nnx + 31) / 32) * g.nny * g.nnz;
+  int occ = 0;
+  TOPO_CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pcg2_kernel<DIM>, P2_THREADS, 0));
+  if (occ < 1) return fail(c, TOPO_ERR_CUDA, "pcg2 kernel cannot be resident");
+  const int per_sm = c->pcg_blocks_per_sm > 0 ? std::min(c->pcg_blocks_per_sm, occ) : std::min(occ, 2);
+  long long G = (long long)per_sm * c->num_sms;
+  const long long maxG = (nunits + 7) / 8;  // at least one unit per warp
+  if (G > maxG) G = std::max(1LL, maxG);
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off += (bytes + 255) & ~(size_t)255;
+    return o;
+  };
+  const size_t oC = take((size_t)StencilGeom<DIM>::NC * g.nnodes * 8), oD = take(N * 8);
+  const size_t orr = take(N * m * 8), oz = take(N * m * 8), ow = take(N * m * 8), op = take(N * m * 8),
+               os = take(N * m * 8);
+  const size_t opart = take(sizeof(double) * 3 * m * G), ores = take(sizeof(double) * 3 * m), oinfo = take(64);
+  topo_status st = ensure_scratch(c, off);
+  if (st) return st;
+  char* base = (char*)c->d_scratch;
+  Pcg2Args<DIM> a;
+  a.g = g;
+  if (DIM == 2)
+    memcpy(&a.ke, &c->q4_64, sizeof(a.ke));
+  else
+    memcpy(&a.ke, &c->h8_64, sizeof(a.ke));
+  a.rho = rho;
+  a.F = F;
+  a.U = U;
+  a.ld = ld;
+  a.m = m;
+  a.N = N;
+  a.nunits = nunits;
+  a.C = (double*)(base + oC);
+  a.dinv = (double*)(base + oD);
+  a.r = (double*)(base + orr);
+  a.z = (double*)(base + oz);
+  a.w = (double*)(base + ow);
+  a.p = (double*)(base + op);
+  a.s = (double*)(base + os);
+  a.partial = (double*)(base + opart);
+  a.result = (double*)(base + ores);
+  a.info = (int*)(base + oinfo);
+  a.info_rr = (double*)(base + oinfo + 16);
+  a.gs = c->d_sync;
+  a.rtol = rtol;
+  a.maxit = maxit;
+  a.wait_cycles = c->wait_cycles;
+  TOPO_CUDA_TRY(c, cudaMemsetAsync(c->d_sync, 0, 2 * sizeof(unsigned int), c->stream));  // count, abort
+  TOPO_CUDA_TRY(c, cudaMemsetAsync(a.info, 0, 32, c->stream));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)G);
+  cfg.blockDim = dim3(P2_THREADS);
+  cfg.stream = c->stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  TOPO_CUDA_TRY(c, cudaLaunchKernelEx(&cfg, pcg2_kernel<DIM>, a));
+  note_launch();
+  if (info_host) {
+    int hinfo[4];
+    double hrr[2];
+    TOPO_CUDA_TRY(c, cudaMemcpyAsync(hinfo, a.info, 16, cudaMemcpyDeviceToHost, c->stream));
+    TOPO_CUDA_TRY(c, cudaMemcpyAsync(hrr, a.info_rr, 16, cudaMemcpyDeviceToHost, c->stream));
+    TOPO_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    int dev_status = 0;
+    TOPO_CUDA_TRY(c, cudaMemcpy(&dev_status, &c->d_sync->status, sizeof(int), cudaMemcpyDeviceToHost));
+    info_host->iters = hinfo[0];
+    info_host->outer = 0;
+    info_host->relres = sqrt(hrr[0]);
+    info_host->status = dev_status ? dev_status : hinfo[2];
+    if (dev_status) {
+      int zero = 0;
+      cudaMemcpy(&c->d_sync->status, &zero, sizeof(int), cudaMemcpyHostToDevice);
+      return fail(c, (topo_status)dev_status, "topo_solve_hdm: device status %d", dev_status);
+    }
+    if (hinfo[2])
+      return fail(c, TOPO_ERR_NOT_CONVERGED, "topo_solve_hdm: relres %.3e after %d iterations", info_host->relres,
+                  hinfo[0]);
+  }
+  return TOPO_OK;
+}
+
+template topo_status solve_stencil_fp64<2>(topo_ctx*, const double*, const double*, double*, int, int, double, int,
+                                           topo_solve_info*);
+template topo_status solve_stencil_fp64<3>(topo_ctx*, const double*, const double*, double*, int, int, double, int,
+                                           topo_solve_info*);
+
+}  // namespace topo

@@ -30,6 +30,8 @@ def main(argv=None):
     ap.add_argument("--k", type=int, default=16)
     ap.add_argument("--maxit", type=int, default=200)
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--hdm-kernel", type=int, default=0, help="FP64 solve: 0 stencil C-G PCG, 1 element-form PCG")
+    ap.add_argument("--blocks-per-sm", type=int, default=0, help="CTAs per SM of the persistent solve (0 = default)")
     a = ap.parse_args(argv)
     import torch
 
@@ -40,6 +42,8 @@ def main(argv=None):
     dims = [int(x) for x in a.shape.split("x")]
     p = w.mbb_2d(*dims) if len(dims) == 2 else w.cantilever_3d(*dims)
     T = native.Topo(p)
+    T.topo_set_param(native.TOPO_PARAM_HDM_KERNEL, a.hdm_kernel)
+    T.topo_set_param(native.TOPO_PARAM_PCG_BLOCKS_PER_SM, a.blocks_per_sm)
     f64 = dict(dtype=torch.float64, device="cuda")
     psi = torch.as_tensor(w.design_field(p, 0)).to(**f64)
     rho = torch.empty(p.nel, **f64)
@@ -95,7 +99,8 @@ def main(argv=None):
         call()
     e1.record()
     e1.synchronize()
-    print(f"{a.call} {a.prec} shape={a.shape} m={a.m} k={k}: {e0.elapsed_time(e1) / a.reps * 1e3:.1f} us/call")
+    print(f"{a.call} {a.prec} shape={a.shape} m={a.m} k={k} hdm_kernel={a.hdm_kernel} bps={a.blocks_per_sm}: "
+          f"{e0.elapsed_time(e1) / a.reps * 1e3:.1f} us/call")
     T.topo_check()
 
 
