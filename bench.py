@@ -399,8 +399,9 @@ def main():
     ap.add_argument("--config", default="mbb600x200", choices=list(CONFIGS))
     ap.add_argument("--k", type=int, default=16)
     ap.add_argument("--rom-evals", type=int, default=100)
-    ap.add_argument("--prec", default="fp32", choices=["fp64", "fp32", "fp32_bf16ke"],
-                    help="arithmetic of the reduced solves and of the HDM solve's inner iterations")
+    ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32", "fp32_bf16ke"],
+                    help="arithmetic of the HDM solve (fp32 forms: FP32 inner PCG in FP64 refinement, which "
+                         "stalls on these designs and completes in FP64) and of the Phi-path reduced solves")
     ap.add_argument("--rom-path", default="elem", choices=["elem", "phi"],
                     help="reduced matrix from cached element reduced matrices, or from K(rho) Phi")
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -7,6 +7,7 @@
 // shared-memory tile with a one-node halo: no atomics, no scatter, deterministic results.
 #pragma once
 
+#include <cuda/atomic>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -401,6 +402,75 @@ __device__ inline bool grid_sync_reduce(GridSync* gs, unsigned int& my_gen, cons
   return s_ok && (*(volatile int*)&gs->abort == 0);
 }
 
+// ---------------------------------------------------------------------------------------
+// Grid barrier, second form: a monotonically increasing 64-bit arrival counter with release
+// semantics and a generation word polled with acquire semantics (both reset before every
+// launch), so no CTA resets anything inside the launch. Barrier number b completes when the
+// counter reaches b * G. Bounded wait as above; on expiry a per-launch abort word is set.
+// Reductions are not folded in: after the barrier every CTA reduces the per-CTA partials
+// itself (reduce_slots), in parallel, in a fixed order.
+// ---------------------------------------------------------------------------------------
+struct GridBar {
+  unsigned long long count;
+  unsigned long long gen;
+  int abort;
+  int pad;
+};
+
+__device__ inline bool grid_barrier(GridBar* gb, int* status, unsigned long long& b, long long wait_cycles) {
+  __shared__ int s_ok;
+  __syncthreads();
+  b += 1;
+  if (threadIdx.x == 0) {
+    s_ok = 1;
+    cuda::atomic_ref<unsigned long long, cuda::thread_scope_device> cnt(gb->count);
+    cuda::atomic_ref<unsigned long long, cuda::thread_scope_device> gen(gb->gen);
+    const unsigned long long target = b * (unsigned long long)gridDim.x;
+    const unsigned long long old = cnt.fetch_add(1ull, cuda::memory_order_release);
+    if (old == target - 1) {
+      gen.store(b, cuda::memory_order_release);
+    } else {
+      const long long t0 = clock64();
+      while (gen.load(cuda::memory_order_acquire) < b) {
+        __nanosleep(20);
+        if (*(volatile int*)&gb->abort) {
+          s_ok = 0;
+          break;
+        }
+        if (clock64() - t0 > wait_cycles) {
+          atomicCAS(status, 0, (int)TOPO_ERR_TIMEOUT);
+          atomicExch(&gb->abort, 1);
+          s_ok = 0;
+          break;
+        }
+      }
+    }
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// out[j] = sum over g < G of partial[j * G + g], j < nslots, summed lane-strided then by a
+// shuffle tree (an order fixed by G alone). One warp per slot. Result in shared memory.
+__device__ inline void reduce_slots(const double* partial, unsigned G, int nslots, double* out) {
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int j = w; j < nslots; j += nw) {
+    const double* pj = partial + (size_t)j * G;
+    double t0 = 0.0, t1 = 0.0, t2 = 0.0, t3 = 0.0;
+    unsigned g = l;
+    for (; g + 96 < G; g += 128) {
+      t0 += __ldcg(pj + g);
+      t1 += __ldcg(pj + g + 32);
+      t2 += __ldcg(pj + g + 64);
+      t3 += __ldcg(pj + g + 96);
+    }
+    for (; g < G; g += 32) t0 += __ldcg(pj + g);
+    double t = warp_sum((t0 + t1) + (t2 + t3));
+    if (l == 0) out[j] = t;
+  }
+  __syncthreads();
+}
+
 }  // namespace topo
 
 // ---------------------------------------------------------------------------------------
@@ -428,6 +498,7 @@ struct topo_ctx {
   double* d_Hs;           // [nel]
   // device status word + grid barrier state
   topo::GridSync* d_sync;
+  topo::GridBar* d_bar;    // state of the second barrier form
   // generic scratch (grown on demand)
   void* d_scratch;
   size_t scratch_bytes;

@@ -435,6 +435,7 @@ extern "C" topo_status topo_create(const topo_problem* prob, void* cuda_stream, 
   if (e == cudaSuccess) e = cudaMalloc(&c->d_stencil_w, w.size() * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&c->d_Hs, g.nel * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&c->d_sync, sizeof(GridSync));
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_bar, sizeof(GridBar));
   if (e != cudaSuccess) {
     topo_destroy(c);
     return TOPO_ERR_OOM;
@@ -442,6 +443,7 @@ extern "C" topo_status topo_create(const topo_problem* prob, void* cuda_stream, 
   cudaMemcpy(c->d_stencil_off, off.data(), off.size() * sizeof(int), cudaMemcpyHostToDevice);
   cudaMemcpy(c->d_stencil_w, w.data(), w.size() * sizeof(double), cudaMemcpyHostToDevice);
   cudaMemset(c->d_sync, 0, sizeof(GridSync));
+  cudaMemset(c->d_bar, 0, sizeof(GridBar));
   topo_status s = filter_launch(c, nullptr, c->d_Hs, 0);
   if (s == TOPO_OK) {
     e = cudaStreamSynchronize(c->stream);
@@ -464,6 +466,7 @@ extern "C" topo_status topo_destroy(topo_ctx* c) {
   cudaFree(c->d_stencil_w);
   cudaFree(c->d_Hs);
   cudaFree(c->d_sync);
+  cudaFree(c->d_bar);
   cudaFree(c->d_scratch);
   cudaFree(c->d_red);
   free(c);

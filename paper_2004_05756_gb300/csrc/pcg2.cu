@@ -11,8 +11,11 @@
 //
 // Work split: a unit is 32 consecutive nodes of one x-row, one warp. Each CTA owns a contiguous,
 // equal share of the units (balanced to one unit), so partial sums are accumulated in a fixed
-// order and every result is deterministic. Each iteration has two grid-wide barriers with the
-// reductions folded in (Chronopoulos-Gear: both dot products of an iteration in one pass).
+// order and every result is deterministic. Each iteration has two grid-wide barriers; after
+// each one every CTA reduces the per-CTA partial dot products itself, in a fixed order
+// (Chronopoulos-Gear: both dot products of an iteration in one reduction). The pipelined CG
+// recurrences (one barrier per iteration) were tried and rejected: on these high-contrast
+// designs they diverge, and periodic residual replacement makes them stagnate.
 #include <algorithm>
 #include <type_traits>
 
@@ -36,14 +39,14 @@ struct Pcg2Args {
   long long nunits;  // ceil(nnx / 32) * nny * nnz
   double* C;         // [NB*DIM*DIM][nnodes]
   double* dinv;      // [N]
-  double* r;         // N x m
+  double* r;         // N x m each
   double* z;
   double* w;
   double* p;
   double* s;
   double* partial;
-  double* result;
-  GridSync* gs;
+  GridSync* gs;      // sticky status
+  GridBar* gb;
   double rtol;
   int maxit;
   long long wait_cycles;
@@ -150,15 +153,22 @@ __global__ void __launch_bounds__(P2_THREADS) pcg2_kernel(const __grid_constant_
   __shared__ double sh_gamma[P2_MAX_COLS], sh_alpha[P2_MAX_COLS], sh_beta[P2_MAX_COLS], sh_tol2[P2_MAX_COLS],
       sh_ff[P2_MAX_COLS], sh_rr[P2_MAX_COLS];
   __shared__ int sh_done[P2_MAX_COLS];
+  __shared__ double sh_sum[3 * P2_MAX_COLS];
   const Grid& g = a.g;
   const int m = a.m;
   const unsigned G = gridDim.x;
   const long long N = a.N;
   GridSync* gs = a.gs;
-  unsigned my_gen = *(volatile unsigned*)&gs->gen;
+  unsigned long long bar = 0;
   double* part = a.partial;
   auto P = [&](int slot, int c) -> double* { return part + ((size_t)(slot * m + c)) * G + blockIdx.x; };
-  auto R = [&](int slot, int c) -> double { return __ldcg(a.result + slot * m + c); };
+  auto R = [&](int slot, int c) -> double { return sh_sum[slot * m + c]; };
+  // grid barrier, then every CTA reduces the per-CTA partials of nred slots itself
+  auto sync_reduce = [&](int nred) -> bool {
+    if (!grid_barrier(a.gb, &gs->status, bar, a.wait_cycles)) return false;
+    if (nred > 0) reduce_slots(part, G, nred, sh_sum);
+    return true;
+  };
   // this CTA's units: a contiguous, balanced range
   const long long u0 = a.nunits * blockIdx.x / G, u1 = a.nunits * (blockIdx.x + 1) / G;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
@@ -184,7 +194,7 @@ __global__ void __launch_bounds__(P2_THREADS) pcg2_kernel(const __grid_constant_
       a.dinv[DIM * n + r] = 1.0 / d;
     }
   });
-  if (!grid_sync_reduce(gs, my_gen, part, a.result, 0, a.wait_cycles)) return;
+  if (!sync_reduce(0)) return;
 
   // --- true residual r = f - K x, z = D^-1 r, w = K z (two phases) ------------------------
   // Phase T1: r, z for owned nodes (x = caller's U, Dirichlet entries zeroed), partial gamma,
@@ -222,7 +232,7 @@ __global__ void __launch_bounds__(P2_THREADS) pcg2_kernel(const __grid_constant_
         const double t = block_sum(acc[q][c], red);
         if (threadIdx.x == 0) *P(q, c) = t;
       }
-    if (!grid_sync_reduce(gs, my_gen, part, a.result, 3 * m, a.wait_cycles)) return false;
+    if (!sync_reduce(3 * m)) return false;
     if (threadIdx.x == 0) {
       for (int c = 0; c < m; ++c) {
         sh_gamma[c] = R(0, c);
@@ -258,7 +268,7 @@ __global__ void __launch_bounds__(P2_THREADS) pcg2_kernel(const __grid_constant_
       const double t = block_sum(acc[c], red);
       if (threadIdx.x == 0) *P(0, c) = t;
     }
-    if (!grid_sync_reduce(gs, my_gen, part, a.result, m, a.wait_cycles)) return false;
+    if (!sync_reduce(m)) return false;
     if (threadIdx.x == 0) {
       for (int c = 0; c < m; ++c) {
         if (sh_done[c]) continue;
@@ -316,7 +326,7 @@ __global__ void __launch_bounds__(P2_THREADS) pcg2_kernel(const __grid_constant_
         *P(1, c) = t2;
       }
     }
-    if (!grid_sync_reduce(gs, my_gen, part, a.result, 2 * m, a.wait_cycles)) return false;
+    if (!sync_reduce(2 * m)) return false;
     if (threadIdx.x == 0) {
       for (int c = 0; c < m; ++c) {
         if (sh_done[c]) continue;
@@ -384,9 +394,9 @@ topo_status solve_stencil_fp64(topo_ctx* c, const double* rho, const double* F, 
     return o;
   };
   const size_t oC = take((size_t)StencilGeom<DIM>::NC * g.nnodes * 8), oD = take(N * 8);
-  const size_t orr = take(N * m * 8), oz = take(N * m * 8), ow = take(N * m * 8), op = take(N * m * 8),
-               os = take(N * m * 8);
-  const size_t opart = take(sizeof(double) * 3 * m * G), ores = take(sizeof(double) * 3 * m), oinfo = take(64);
+  size_t ov[5];
+  for (int t = 0; t < 5; ++t) ov[t] = take(N * m * 8);
+  const size_t opart = take(sizeof(double) * 3 * m * G), oinfo = take(64);
   topo_status st = ensure_scratch(c, off);
   if (st) return st;
   char* base = (char*)c->d_scratch;
@@ -405,20 +415,17 @@ topo_status solve_stencil_fp64(topo_ctx* c, const double* rho, const double* F, 
   a.nunits = nunits;
   a.C = (double*)(base + oC);
   a.dinv = (double*)(base + oD);
-  a.r = (double*)(base + orr);
-  a.z = (double*)(base + oz);
-  a.w = (double*)(base + ow);
-  a.p = (double*)(base + op);
-  a.s = (double*)(base + os);
+  double** vecs[5] = {&a.r, &a.z, &a.w, &a.p, &a.s};
+  for (int t = 0; t < 5; ++t) *vecs[t] = (double*)(base + ov[t]);
   a.partial = (double*)(base + opart);
-  a.result = (double*)(base + ores);
   a.info = (int*)(base + oinfo);
   a.info_rr = (double*)(base + oinfo + 16);
   a.gs = c->d_sync;
+  a.gb = c->d_bar;
   a.rtol = rtol;
   a.maxit = maxit;
   a.wait_cycles = c->wait_cycles;
-  TOPO_CUDA_TRY(c, cudaMemsetAsync(c->d_sync, 0, 2 * sizeof(unsigned int), c->stream));  // count, abort
+  TOPO_CUDA_TRY(c, cudaMemsetAsync(c->d_bar, 0, sizeof(GridBar), c->stream));  // counter, generation, abort
   TOPO_CUDA_TRY(c, cudaMemsetAsync(a.info, 0, 32, c->stream));
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)G);
