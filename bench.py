@@ -347,22 +347,21 @@ def run_ours(args, rank, world):
     evals = (1 + R) * K * world
     value = evals / t_max
     e2e_value = evals / times[2]
-    # dominant kernel: the persistent PCG launch (one per HDM solve); algorithmic bytes per
-    # launch from the iteration counts (50 B/DOF per inner FP32 iteration,
-    # 32 B/DOF per FP64 refinement residual, 8-byte FP64 / 4-byte FP32 words)
+    # Dominant kernel: the persistent PCG launch (one per HDM solve), FP64-ALU bound at this size
+    # (the whole working set sits in L2). FP64 flops it performs per DOF and iteration: stencil
+    # apply 2 * 3^d * d (36 in 2D, 162 in 3D), delta 2, the five updates, z and the two dots 13.
     hdm_ms = statistics.fmean(stats["hdm"])
     iters = statistics.fmean(stats["iters"])
-    outer = statistics.fmean(stats["outer"])
-    if prec == "fp64":
-        bytes_launch = N * (100.0 * iters + 48.0)
-    else:
-        bytes_launch = N * (50.0 * iters + 32.0 * (outer + 1))
+    flop_dof = 51.0 if p.dim == 2 else 177.0
+    flops_launch = N * flop_dof * iters
+    # FP64 peak derived from unit counts and clocks: 152 SMs x 2 FP64 FMA/clk (4 flop) x 2.07 GHz
+    # (NVIDIA's nominal FP64 rate is 1.25 TFLOP/s; this build's own FMA microbenchmark measured 1.19).
+    fp64_peak = 152 * 4 * 2.07e9 / 1e12
+    achieved = flops_launch / (hdm_ms * 1e-3) / 1e12
     try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-        hbm_peak, peak_src = float(peaks["hbm_gbs"]), "measured"
+        hbm_peak = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
     except Exception:
-        hbm_peak, peak_src = 6800.0, "fallback"
-    achieved = bytes_launch / (hdm_ms * 1e-3) / 1e9
+        hbm_peak = 6800.0
     rom_ms = sorted(stats["rom"])
     pct = lambda q: rom_ms[min(len(rom_ms) - 1, int(q * len(rom_ms)))] if rom_ms else None
     out = {
@@ -381,9 +380,11 @@ def run_ours(args, rank, world):
         "basis_update_ms": statistics.fmean(stats["build"]),
         "pcg": {"inner_iters": iters, "outer": outer, "relres": max(stats["relres"]), "fp64_iters": info64["iters"]},
         "accuracy": {"hdm_J_vs_fp64_rel": hdm_rel, "rom_Jk_vs_fp64_phi_path_rel": rom_rel, "J_centre": J_centre},
-        "roofline": {"kernel": "pcg_kernel (persistent Jacobi-PCG, one launch per HDM solve)", "bound": "hbm",
-                     "achieved": achieved, "peak": hbm_peak, "unit": "GB/s", "frac": achieved / hbm_peak,
-                     "traffic": None, "peak_source": peak_src},
+        "roofline": {"kernel": "pcg2_kernel (assembled-stencil Chronopoulos-Gear PCG, one launch per HDM solve)",
+                     "bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+                     "frac": achieved / fp64_peak, "traffic": None,
+                     "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2.07 GHz (measured FMA peak 1.19)",
+                     "flop_per_dof_iter": flop_dof, "hbm_peak_gbs": hbm_peak},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches, "clocks": clocks, "wall_s_timed": t_wall,
     }
