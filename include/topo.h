@@ -70,6 +70,9 @@ typedef struct {
   int outer;      /* FP64 refinement steps (0 for TOPO_FP64) */
   double relres;  /* final ||f - K u||_2 / ||f||_2 over free DOFs, FP64 */
   int status;     /* topo_status of the solve */
+  double floor;   /* 2 eps || |K| |u| ||_2 / ||f||_2: the FP64 rounding floor of any residual of
+                     u. The FP64 solves accept relres <= max(rtol, floor): designs that put loads
+                     on near-void material cannot go below it (0 when not computed) */
 } topo_solve_info;
 
 /* Tunable parameters (topo_set_param). */
@@ -195,6 +198,42 @@ topo_status topo_rom_error(topo_ctx* ctx, const double* rho, const double* Phi, 
  * and ROM reconstructions alike. */
 topo_status topo_compliance_grad(topo_ctx* ctx, const double* rho, const double* U, int m, int ld,
                                  const double* F, double* J, double* dc_rho, double* dc_psi);
+
+/* ---------------------------------------------------------------------------------------
+ * Batched form: many independent 2D problems (uneven sizes, 1..32 load cases each) behind one
+ * handle. Each instance owns a context (topo_batch_context) on the batch's stream, so every
+ * single-instance call above also works on it. Argument arrays are HOST arrays of count entries
+ * (device pointers inside).
+ * --------------------------------------------------------------------------------------- */
+typedef struct topo_batch topo_batch;
+
+/* Create count contexts (dim must be 2 for all) on one stream. */
+topo_status topo_batch_create(const topo_problem* probs, int count, void* cuda_stream, topo_batch** out);
+topo_status topo_batch_destroy(topo_batch* batch);
+const char* topo_batch_last_error(const topo_batch* batch);
+/* The context of instance i (owned by the batch). */
+topo_status topo_batch_context(topo_batch* batch, int i, topo_ctx** out);
+
+/* All state solves (Eq. linelastsoln) in ONE persistent cooperative launch: each instance runs
+ * the FP64 assembled-stencil PCG of topo_solve_hdm on its own group of co-resident CTAs (sized by
+ * nodes x load cases x mesh width) with its own barrier and convergence; instances that do not
+ * fit the co-resident capacity run in further waves. The first call tunes the CTAs per SM on
+ * short runs (initial guesses are saved and restored) and caches the choice in the batch.
+ * U[i] holds the initial guess and receives the solution. info_host (host array of count, may be
+ * NULL) makes the call synchronise and report per instance. */
+topo_status topo_batch_solve_hdm(topo_batch* batch, const double* const* rho, const double* const* F,
+                                 double* const* U, const int* m, const int* ld, double rtol, int maxit,
+                                 topo_solve_info* info_host);
+/* topo_filter on every instance. */
+topo_status topo_batch_filter(topo_batch* batch, const double* const* in, double* const* out, int adjoint);
+/* topo_compliance_grad on every instance; J is a DEVICE array of count compliances. */
+topo_status topo_batch_compliance_grad(topo_batch* batch, const double* const* rho, const double* const* U,
+                                       const int* m, const int* ld, const double* const* F, double* J,
+                                       double* const* dc_rho, double* const* dc_psi);
+/* topo_rom_solve_elem on every instance; k is a HOST array, Jk a DEVICE array of count. */
+topo_status topo_batch_rom_solve_elem(topo_batch* batch, const double* const* rho, const double* const* Hel,
+                                      const int* k, const double* const* b, double* const* H_work,
+                                      double* const* yhat, double* Jk);
 
 #ifdef __cplusplus
 }

@@ -1,0 +1,331 @@
+// Batched form: many independent design problems of uneven size solved in one persistent
+// cooperative launch (plus batched filter, gradient and reduced solves).
+//
+// Each instance keeps its own context (Dirichlet mask, element matrices, filter, scratch,
+// barrier state); all contexts share the batch's stream. The state solves of all instances run
+// in ONE launch of pcg2_batch_kernel: every instance gets a group of co-resident CTAs sized by
+// its estimated work (nodes x load cases x mesh width, the last a proxy for the iteration
+// count), has its own arrival counter and its own CG scalars, and converges on its own. When
+// the instances need more CTAs than can be co-resident the batch runs in waves.
+//
+// Autotuning: the number of CTAs per SM of the batched launch is chosen on the first solve of a
+// batch by timing each candidate on a short run of the same instances, and cached in the batch
+// (its signature is the list of instance shapes and load-case counts).
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "pcg2.cuh"
+
+struct topo_batch {
+  int count;
+  std::vector<topo_ctx*> ctx;
+  cudaStream_t stream;
+  int num_sms;
+  topo::GridSync* d_sync;  // batch-wide sticky status
+  // launch tables (device) and their pinned host staging
+  void* d_args;
+  size_t args_bytes;
+  int* d_tab;
+  size_t tab_ints;
+  void* h_stage;
+  size_t stage_bytes;
+  int tuned_bps;  // autotuned CTAs per SM (0 = not tuned yet)
+  char err[512];
+};
+
+namespace topo {
+
+static topo_status bfail(topo_batch* b, topo_status s, const char* msg) {
+  if (b) snprintf(b->err, sizeof(b->err), "%s", msg);
+  return s;
+}
+
+// Work weight of an instance for CTA allocation.
+static double work_weight(const topo_ctx* c, int m) {
+  return (double)c->g.nnodes * std::max(1, m) * (double)std::max(c->g.nx, c->g.ny);
+}
+
+struct Plan {
+  std::vector<int> wave_of;   // per instance
+  std::vector<int> grp;       // CTAs per instance
+  int waves;
+};
+
+// Split instances into waves of at most cap CTAs; inside a wave, CTAs proportional to work.
+static Plan make_plan(topo_batch* b, const int* m, int cap) {
+  Plan p;
+  const int n = b->count;
+  p.wave_of.assign(n, 0);
+  p.grp.assign(n, 1);
+  std::vector<double> w(n);
+  double total = 0;
+  for (int i = 0; i < n; ++i) total += (w[i] = work_weight(b->ctx[i], m[i]));
+  // number of waves: enough that every instance can have at least one CTA
+  p.waves = std::max(1, (n + cap - 1) / cap);
+  std::vector<int> order(n);
+  for (int i = 0; i < n; ++i) order[i] = i;
+  std::sort(order.begin(), order.end(), [&](int x, int y) { return w[x] > w[y]; });
+  // round-robin the heaviest instances over waves, then size groups inside each wave
+  for (int r = 0; r < n; ++r) p.wave_of[order[r]] = r % p.waves;
+  for (int wv = 0; wv < p.waves; ++wv) {
+    std::vector<int> ids;
+    double tw = 0;
+    for (int i = 0; i < n; ++i)
+      if (p.wave_of[i] == wv) {
+        ids.push_back(i);
+        tw += w[i];
+      }
+    int left = cap - (int)ids.size();  // one CTA each is guaranteed
+    for (int i : ids) {
+      const long long units = (long long)((b->ctx[i]->g.nnx + 31) / 32) * b->ctx[i]->g.nny * b->ctx[i]->g.nnz;
+      const int maxg = (int)std::max(1LL, units / 8);
+      int extra = (int)std::floor(left * (w[i] / tw) * 0.999);
+      p.grp[i] = std::min(maxg, 1 + std::max(0, extra));
+    }
+  }
+  return p;
+}
+
+template <int DIM>
+static topo_status batch_solve_dim(topo_batch* b, const double* const* rho, const double* const* F,
+                                   double* const* U, const int* m, const int* ld, double rtol, int maxit,
+                                   int bps, topo_solve_info* info_host) {
+  const int n = b->count;
+  const int occ = pcg2_occupancy();
+  const int per_sm = std::max(1, std::min(bps, occ));
+  const int cap = per_sm * b->num_sms;
+  Plan plan = make_plan(b, m, cap);
+  std::vector<Pcg2Args<DIM>> args(n);
+  for (int i = 0; i < n; ++i) {
+    topo_status s = build_pcg2_args<DIM>(b->ctx[i], rho[i], F[i], U[i], m[i], ld[i], rtol, maxit, plan.grp[i],
+                                         &args[i], b->d_sync);
+    if (s) return bfail(b, s, b->ctx[i]->err);
+  }
+  // device tables: args, then per wave the CTA -> (instance, rank) maps and group sizes
+  const size_t abytes = sizeof(Pcg2Args<DIM>) * n;
+  std::vector<int> tab;
+  std::vector<size_t> wave_off, wave_ctas;
+  for (int wv = 0; wv < plan.waves; ++wv) {
+    wave_off.push_back(tab.size());
+    size_t start = tab.size();
+    std::vector<int> inst, rank;
+    for (int i = 0; i < n; ++i)
+      if (plan.wave_of[i] == wv)
+        for (int r = 0; r < plan.grp[i]; ++r) {
+          inst.push_back(i);
+          rank.push_back(r);
+        }
+    wave_ctas.push_back(inst.size());
+    tab.insert(tab.end(), inst.begin(), inst.end());
+    tab.insert(tab.end(), rank.begin(), rank.end());
+    (void)start;
+  }
+  const size_t grp_off = tab.size();
+  tab.insert(tab.end(), plan.grp.begin(), plan.grp.end());
+  const size_t need_stage = abytes + tab.size() * sizeof(int);
+  if (need_stage > b->stage_bytes) {
+    TOPO_CUDA_TRY(b->ctx[0], cudaStreamSynchronize(b->stream));
+    if (b->h_stage) cudaFreeHost(b->h_stage);
+    b->h_stage = nullptr;
+    TOPO_CUDA_TRY(b->ctx[0], cudaMallocHost(&b->h_stage, need_stage));
+    b->stage_bytes = need_stage;
+  }
+  if (abytes > b->args_bytes) {
+    TOPO_CUDA_TRY(b->ctx[0], cudaStreamSynchronize(b->stream));
+    if (b->d_args) cudaFree(b->d_args);
+    b->d_args = nullptr;
+    TOPO_CUDA_TRY(b->ctx[0], cudaMalloc(&b->d_args, abytes));
+    b->args_bytes = abytes;
+  }
+  if (tab.size() > b->tab_ints) {
+    TOPO_CUDA_TRY(b->ctx[0], cudaStreamSynchronize(b->stream));
+    if (b->d_tab) cudaFree(b->d_tab);
+    b->d_tab = nullptr;
+    TOPO_CUDA_TRY(b->ctx[0], cudaMalloc(&b->d_tab, tab.size() * sizeof(int)));
+    b->tab_ints = tab.size();
+  }
+  // the pinned staging may still feed a previous call's copies: wait for them
+  TOPO_CUDA_TRY(b->ctx[0], cudaStreamSynchronize(b->stream));
+  memcpy(b->h_stage, args.data(), abytes);
+  memcpy((char*)b->h_stage + abytes, tab.data(), tab.size() * sizeof(int));
+  TOPO_CUDA_TRY(b->ctx[0], cudaMemcpyAsync(b->d_args, b->h_stage, abytes, cudaMemcpyHostToDevice, b->stream));
+  TOPO_CUDA_TRY(b->ctx[0], cudaMemcpyAsync(b->d_tab, (char*)b->h_stage + abytes, tab.size() * sizeof(int),
+                                           cudaMemcpyHostToDevice, b->stream));
+  for (int i = 0; i < n; ++i) {
+    TOPO_CUDA_TRY(b->ctx[0], cudaMemsetAsync(b->ctx[i]->d_bar, 0, sizeof(GridBar), b->stream));
+    TOPO_CUDA_TRY(b->ctx[0], cudaMemsetAsync(args[i].info, 0, 32, b->stream));
+  }
+  for (int wv = 0; wv < plan.waves; ++wv) {
+    const int* d_inst = b->d_tab + wave_off[wv];
+    const int* d_rank = d_inst + wave_ctas[wv];
+    const int* d_grp = b->d_tab + grp_off;
+    TOPO_CUDA_TRY(b->ctx[0], launch_pcg2_batch2((unsigned)wave_ctas[wv], b->stream, (const Pcg2Args<2>*)b->d_args,
+                                                d_inst, d_rank, d_grp));
+    note_launch();
+  }
+  if (info_host) {
+    TOPO_CUDA_TRY(b->ctx[0], cudaStreamSynchronize(b->stream));
+    topo_status worst = TOPO_OK;
+    for (int i = 0; i < n; ++i) {
+      int hi[4];
+      double hr[2];
+      TOPO_CUDA_TRY(b->ctx[0], cudaMemcpy(hi, args[i].info, 16, cudaMemcpyDeviceToHost));
+      TOPO_CUDA_TRY(b->ctx[0], cudaMemcpy(hr, args[i].info_rr, 16, cudaMemcpyDeviceToHost));
+      info_host[i].iters = hi[0];
+      info_host[i].outer = 0;
+      info_host[i].relres = std::sqrt(hr[0]);
+      info_host[i].floor = std::sqrt(hr[1]);
+      info_host[i].status = hi[2];
+      if (hi[2] && worst == TOPO_OK) worst = (topo_status)hi[2];
+    }
+    int st = 0;
+    TOPO_CUDA_TRY(b->ctx[0], cudaMemcpy(&st, &b->d_sync->status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (st) {
+      int zero = 0;
+      cudaMemcpy(&b->d_sync->status, &zero, sizeof(int), cudaMemcpyHostToDevice);
+      return bfail(b, (topo_status)st, "batched solve: device status set");
+    }
+    if (worst) return bfail(b, worst, "batched solve: some instance did not converge");
+  }
+  return TOPO_OK;
+}
+
+}  // namespace topo
+
+using namespace topo;
+
+extern "C" topo_status topo_batch_create(const topo_problem* probs, int count, void* cuda_stream, topo_batch** out) {
+  if (!out) return TOPO_ERR_INVALID;
+  *out = nullptr;
+  if (!probs || count < 1) return TOPO_ERR_INVALID;
+  for (int i = 1; i < count; ++i)
+    if (probs[i].dim != probs[0].dim) return TOPO_ERR_INVALID;
+  if (probs[0].dim != 2) return TOPO_ERR_INVALID;  // batched solves: 2D Q4 in this build
+  topo_batch* b = new topo_batch();
+  b->count = count;
+  b->stream = (cudaStream_t)cuda_stream;
+  b->ctx.assign(count, nullptr);
+  for (int i = 0; i < count; ++i) {
+    topo_status s = topo_create(&probs[i], cuda_stream, &b->ctx[i]);
+    if (s) {
+      topo_batch_destroy(b);
+      return s;
+    }
+  }
+  b->num_sms = b->ctx[0]->num_sms;
+  if (cudaMalloc(&b->d_sync, sizeof(GridSync)) != cudaSuccess) {
+    topo_batch_destroy(b);
+    return TOPO_ERR_OOM;
+  }
+  cudaMemset(b->d_sync, 0, sizeof(GridSync));
+  *out = b;
+  return TOPO_OK;
+}
+
+extern "C" topo_status topo_batch_destroy(topo_batch* b) {
+  if (!b) return TOPO_OK;
+  cudaStreamSynchronize(b->stream);
+  for (topo_ctx* c : b->ctx)
+    if (c) topo_destroy(c);
+  cudaFree(b->d_sync);
+  cudaFree(b->d_args);
+  cudaFree(b->d_tab);
+  if (b->h_stage) cudaFreeHost(b->h_stage);
+  delete b;
+  return TOPO_OK;
+}
+
+extern "C" const char* topo_batch_last_error(const topo_batch* b) { return b ? b->err : "null batch"; }
+
+extern "C" topo_status topo_batch_context(topo_batch* b, int i, topo_ctx** out) {
+  if (!b || !out || i < 0 || i >= b->count) return TOPO_ERR_INVALID;
+  *out = b->ctx[i];
+  return TOPO_OK;
+}
+
+extern "C" topo_status topo_batch_solve_hdm(topo_batch* b, const double* const* rho, const double* const* F,
+                                            double* const* U, const int* m, const int* ld, double rtol, int maxit,
+                                            topo_solve_info* info_host) {
+  if (!b) return TOPO_ERR_INVALID;
+  if (!rho || !F || !U || !m || !ld) return bfail(b, TOPO_ERR_INVALID, "batched solve: null argument array");
+  if (!(rtol > 0.0) || maxit < 0) return bfail(b, TOPO_ERR_INVALID, "batched solve: rtol > 0, maxit >= 0");
+  for (int i = 0; i < b->count; ++i) {
+    if (m[i] < 1 || m[i] > 32 || (long long)ld[i] < b->ctx[i]->g.ndof || !dev_ptr_ok(rho[i]) || !dev_ptr_ok(F[i]) ||
+        !dev_ptr_ok(U[i]) || F[i] == U[i])
+      return bfail(b, TOPO_ERR_INVALID, "batched solve: bad instance arguments (m in [1,32], ld >= N, pointers)");
+  }
+  int bps = b->tuned_bps;
+  if (bps == 0) {
+    // autotune the CTAs per SM on short runs of these instances; the caller's initial guesses
+    // are saved first and restored afterwards
+    std::vector<double*> saved(b->count, nullptr);
+    for (int i = 0; i < b->count; ++i) {
+      const size_t bytes = sizeof(double) * (size_t)ld[i] * m[i];
+      if (cudaMalloc(&saved[i], bytes) != cudaSuccess) {
+        for (double* q : saved) cudaFree(q);
+        return bfail(b, TOPO_ERR_OOM, "batched solve: autotuning copy");
+      }
+      cudaMemcpyAsync(saved[i], U[i], bytes, cudaMemcpyDeviceToDevice, b->stream);
+    }
+    float best = 1e30f;
+    bps = 2;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    for (int cand = 1; cand <= 4; ++cand) {
+      cudaEventRecord(e0, b->stream);
+      topo_status s = batch_solve_dim<2>(b, rho, F, U, m, ld, rtol, 30, cand, nullptr);
+      cudaEventRecord(e1, b->stream);
+      cudaEventSynchronize(e1);
+      if (s) continue;
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) {
+        best = ms;
+        bps = cand;
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    for (int i = 0; i < b->count; ++i) {
+      cudaMemcpyAsync(U[i], saved[i], sizeof(double) * (size_t)ld[i] * m[i], cudaMemcpyDeviceToDevice, b->stream);
+    }
+    cudaStreamSynchronize(b->stream);
+    for (double* q : saved) cudaFree(q);
+    b->tuned_bps = bps;
+  }
+  return batch_solve_dim<2>(b, rho, F, U, m, ld, rtol, maxit, bps, info_host);
+}
+
+extern "C" topo_status topo_batch_filter(topo_batch* b, const double* const* in, double* const* out, int adjoint) {
+  if (!b || !in || !out) return TOPO_ERR_INVALID;
+  for (int i = 0; i < b->count; ++i) {
+    topo_status s = topo_filter(b->ctx[i], in[i], out[i], adjoint);
+    if (s) return bfail(b, s, b->ctx[i]->err);
+  }
+  return TOPO_OK;
+}
+
+extern "C" topo_status topo_batch_compliance_grad(topo_batch* b, const double* const* rho, const double* const* U,
+                                                  const int* m, const int* ld, const double* const* F, double* J,
+                                                  double* const* dc_rho, double* const* dc_psi) {
+  if (!b || !rho || !U || !m || !ld || !F || !J || !dc_rho) return TOPO_ERR_INVALID;
+  for (int i = 0; i < b->count; ++i) {
+    topo_status s = topo_compliance_grad(b->ctx[i], rho[i], U[i], m[i], ld[i], F[i], J + i, dc_rho[i],
+                                         dc_psi ? dc_psi[i] : nullptr);
+    if (s) return bfail(b, s, b->ctx[i]->err);
+  }
+  return TOPO_OK;
+}
+
+extern "C" topo_status topo_batch_rom_solve_elem(topo_batch* b, const double* const* rho, const double* const* Hel,
+                                                 const int* k, const double* const* bvec, double* const* H_work,
+                                                 double* const* yhat, double* Jk) {
+  if (!b || !rho || !Hel || !k || !bvec || !H_work || !yhat || !Jk) return TOPO_ERR_INVALID;
+  for (int i = 0; i < b->count; ++i) {
+    topo_status s = topo_rom_solve_elem(b->ctx[i], rho[i], Hel[i], k[i], bvec[i], H_work[i], yhat[i], Jk + i);
+    if (s) return bfail(b, s, b->ctx[i]->err);
+  }
+  return TOPO_OK;
+}

@@ -417,7 +417,10 @@ struct GridBar {
   int pad;
 };
 
-__device__ inline bool grid_barrier(GridBar* gb, int* status, unsigned long long& b, long long wait_cycles) {
+// Barrier over a group of `group` co-resident CTAs sharing one GridBar (the whole grid, or one
+// instance's CTAs in a batched launch).
+__device__ inline bool grid_barrier(GridBar* gb, int* status, unsigned long long& b, long long wait_cycles,
+                                    unsigned group) {
   __shared__ int s_ok;
   __syncthreads();
   b += 1;
@@ -425,7 +428,7 @@ __device__ inline bool grid_barrier(GridBar* gb, int* status, unsigned long long
     s_ok = 1;
     cuda::atomic_ref<unsigned long long, cuda::thread_scope_device> cnt(gb->count);
     cuda::atomic_ref<unsigned long long, cuda::thread_scope_device> gen(gb->gen);
-    const unsigned long long target = b * (unsigned long long)gridDim.x;
+    const unsigned long long target = b * (unsigned long long)group;
     const unsigned long long old = cnt.fetch_add(1ull, cuda::memory_order_release);
     if (old == target - 1) {
       gen.store(b, cuda::memory_order_release);

@@ -623,6 +623,7 @@ static topo_status solve_impl(topo_ctx* c, const double* rho, const double* F, d
         info_host->iters = hinfo[0] + sub.iters;
         info_host->outer = hinfo[1];
         info_host->relres = sub.relres;
+        info_host->floor = sub.floor;
         info_host->status = sub.status;
       }
       if (st2 == TOPO_ERR_NOT_CONVERGED && !info_host) return TOPO_OK;

@@ -19,46 +19,9 @@
 #include <algorithm>
 #include <type_traits>
 
-#include "common.cuh"
+#include "pcg2.cuh"
 
 namespace topo {
-
-constexpr int P2_MAX_COLS = 32;
-constexpr int P2_THREADS = 256;
-
-template <int DIM>
-struct Pcg2Args {
-  Grid g;
-  typename KeOf<DIM, double>::type ke;
-  const double* rho;
-  const double* F;
-  double* U;
-  long long ld;
-  int m;
-  long long N;       // scratch leading dimension (= ndof)
-  long long nunits;  // ceil(nnx / 32) * nny * nnz
-  double* C;         // [NB*DIM*DIM][nnodes]
-  double* dinv;      // [N]
-  double* r;         // N x m each
-  double* z;
-  double* w;
-  double* p;
-  double* s;
-  double* partial;
-  GridSync* gs;      // sticky status
-  GridBar* gb;
-  double rtol;
-  int maxit;
-  long long wait_cycles;
-  int* info;
-  double* info_rr;
-};
-
-template <int DIM>
-struct StencilGeom {
-  static constexpr int NB = DIM == 2 ? 9 : 27;
-  static constexpr int NC = NB * DIM * DIM;  // coefficients per node
-};
 
 __device__ __forceinline__ void unit_coords(const Grid& g, long long u, int& i0, int& j, int& kz) {
   const int ux = (g.nnx + 31) / 32;
@@ -124,6 +87,33 @@ __device__ void assemble_node(const Grid& g, const typename KeOf<DIM, double>::t
 }
 
 // y = C v for node (i, j, k); neighbour values read from L2 (written by other CTAs).
+// y = C v and yabs = |C| |v| (the scale of the rounding error of y).
+template <int DIM>
+__device__ __forceinline__ void stencil_apply_abs(const Grid& g, const double* __restrict__ C, const double* v, int i,
+                                                  int j, int k, long long n, double* y, double* yabs) {
+  constexpr int NB = StencilGeom<DIM>::NB;
+#pragma unroll
+  for (int r = 0; r < DIM; ++r) y[r] = yabs[r] = 0.0;
+#pragma unroll 1
+  for (int nb = 0; nb < NB; ++nb) {
+    const int dx = nb % 3 - 1, dy = (nb / 3) % 3 - 1, dz = DIM == 3 ? nb / 9 - 1 : 0;
+    const int ii = i + dx, jj = j + dy, kk = k + dz;
+    const bool nin = ii >= 0 && ii < g.nnx && jj >= 0 && jj < g.nny && (DIM == 2 || (kk >= 0 && kk < g.nnz));
+    if (!nin) continue;
+    const long long m = ii + (long long)g.nnx * (jj + (long long)g.nny * kk);
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) {
+      const double vv = __ldcg(v + DIM * m + d);
+#pragma unroll
+      for (int r = 0; r < DIM; ++r) {
+        const double cc = __ldg(C + (long long)((nb * DIM + r) * DIM + d) * g.nnodes + n);
+        y[r] = fma(cc, vv, y[r]);
+        yabs[r] = fma(fabs(cc), fabs(vv), yabs[r]);
+      }
+    }
+  }
+}
+
 template <int DIM>
 __device__ __forceinline__ void stencil_apply(const Grid& g, const double* __restrict__ C, const double* v, int i,
                                               int j, int k, long long n, double* y) {
@@ -147,30 +137,33 @@ __device__ __forceinline__ void stencil_apply(const Grid& g, const double* __res
   }
 }
 
+// The solver, run by a group of G co-resident CTAs (this CTA is number `rank` of the group)
+// that share the barrier state gb.
 template <int DIM>
-__global__ void __launch_bounds__(P2_THREADS) pcg2_kernel(const __grid_constant__ Pcg2Args<DIM> a) {
+__device__ __forceinline__ void pcg2_body(const Pcg2Args<DIM>& a, const unsigned G, const unsigned rank,
+                                          GridBar* gb) {
   __shared__ double red[32];
   __shared__ double sh_gamma[P2_MAX_COLS], sh_alpha[P2_MAX_COLS], sh_beta[P2_MAX_COLS], sh_tol2[P2_MAX_COLS],
       sh_ff[P2_MAX_COLS], sh_rr[P2_MAX_COLS];
   __shared__ int sh_done[P2_MAX_COLS];
-  __shared__ double sh_sum[3 * P2_MAX_COLS];
+  __shared__ double sh_sum[4 * P2_MAX_COLS];
+  __shared__ double sh_floor2[P2_MAX_COLS];
   const Grid& g = a.g;
   const int m = a.m;
-  const unsigned G = gridDim.x;
   const long long N = a.N;
   GridSync* gs = a.gs;
   unsigned long long bar = 0;
   double* part = a.partial;
-  auto P = [&](int slot, int c) -> double* { return part + ((size_t)(slot * m + c)) * G + blockIdx.x; };
+  auto P = [&](int slot, int c) -> double* { return part + ((size_t)(slot * m + c)) * G + rank; };
   auto R = [&](int slot, int c) -> double { return sh_sum[slot * m + c]; };
   // grid barrier, then every CTA reduces the per-CTA partials of nred slots itself
   auto sync_reduce = [&](int nred) -> bool {
-    if (!grid_barrier(a.gb, &gs->status, bar, a.wait_cycles)) return false;
+    if (!grid_barrier(gb, &gs->status, bar, a.wait_cycles, G)) return false;
     if (nred > 0) reduce_slots(part, G, nred, sh_sum);
     return true;
   };
   // this CTA's units: a contiguous, balanced range
-  const long long u0 = a.nunits * blockIdx.x / G, u1 = a.nunits * (blockIdx.x + 1) / G;
+  const long long u0 = a.nunits * rank / G, u1 = a.nunits * (rank + 1) / G;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
   // iterate over the owned nodes of this CTA: fn(i, j, k, n)
   auto for_owned = [&](auto fn) {
@@ -200,14 +193,14 @@ __global__ void __launch_bounds__(P2_THREADS) pcg2_kernel(const __grid_constant_
   // Phase T1: r, z for owned nodes (x = caller's U, Dirichlet entries zeroed), partial gamma,
   // r.r, f.f.
   auto true_residual = [&](bool first) -> bool {
-    double acc[3][P2_MAX_COLS];
-    for (int c = 0; c < m; ++c) acc[0][c] = acc[1][c] = acc[2][c] = 0.0;
+    double acc[4][P2_MAX_COLS];
+    for (int c = 0; c < m; ++c) acc[0][c] = acc[1][c] = acc[2][c] = acc[3][c] = 0.0;
     for (int c = 0; c < m; ++c) {
       double* x = a.U + c * a.ld;
       const double* f = a.F + c * a.ld;
       for_owned([&](int i, int j, int k, long long n) {
-        double y[DIM];
-        stencil_apply<DIM>(g, a.C, x, i, j, k, n, y);
+        double y[DIM], yabs[DIM];
+        stencil_apply_abs<DIM>(g, a.C, x, i, j, k, n, y, yabs);
 #pragma unroll
         for (int d = 0; d < DIM; ++d) {
           const long long dof = DIM * n + d;
@@ -217,6 +210,7 @@ __global__ void __launch_bounds__(P2_THREADS) pcg2_kernel(const __grid_constant_
             rv = fv - y[d];
             acc[1][c] = fma(rv, rv, acc[1][c]);
             acc[2][c] = fma(fv, fv, acc[2][c]);
+            acc[3][c] = fma(yabs[d], yabs[d], acc[3][c]);
           } else if (first) {
             x[dof] = 0.0;  // Dirichlet entries of the solution are zero (their columns are zero)
           }
@@ -228,17 +222,21 @@ __global__ void __launch_bounds__(P2_THREADS) pcg2_kernel(const __grid_constant_
       });
     }
     for (int c = 0; c < m; ++c)
-      for (int q = 0; q < 3; ++q) {
+      for (int q = 0; q < 4; ++q) {
         const double t = block_sum(acc[q][c], red);
         if (threadIdx.x == 0) *P(q, c) = t;
       }
-    if (!sync_reduce(3 * m)) return false;
+    if (!sync_reduce(4 * m)) return false;
     if (threadIdx.x == 0) {
       for (int c = 0; c < m; ++c) {
         sh_gamma[c] = R(0, c);
         sh_rr[c] = R(1, c);
         if (first) sh_ff[c] = R(2, c);
-        sh_tol2[c] = a.rtol * a.rtol * sh_ff[c];
+        // no FP64 evaluation of f - K x can be trusted below ~eps |K||x|: accept the larger
+        // of rtol and 2 eps |K||x| / |f|
+        const double fl = 2.0 * 2.220446049250313e-16;
+        sh_floor2[c] = fl * fl * R(3, c);
+        sh_tol2[c] = fmax(a.rtol * a.rtol * sh_ff[c], sh_floor2[c]);
         sh_done[c] = sh_rr[c] <= sh_tol2[c];
       }
     }
@@ -359,13 +357,15 @@ __global__ void __launch_bounds__(P2_THREADS) pcg2_kernel(const __grid_constant_
     }
     if (!true_residual(false)) return;  // residual replacement: restart from the true residual
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    double worst = 0.0;
+  if (rank == 0 && threadIdx.x == 0) {
+    double worst = 0.0, wfloor = 0.0;
     bool conv = true;
     for (int c = 0; c < m; ++c) {
       worst = fmax(worst, sh_ff[c] > 0 ? sh_rr[c] / sh_ff[c] : 0.0);
+      wfloor = fmax(wfloor, sh_ff[c] > 0 ? sh_floor2[c] / sh_ff[c] : 0.0);
       conv = conv && (sh_rr[c] <= sh_tol2[c]);
     }
+    a.info_rr[1] = wfloor;
     a.info[0] = iters;
     a.info[1] = 0;
     a.info[2] = conv ? 0 : TOPO_ERR_NOT_CONVERGED;
@@ -375,18 +375,29 @@ __global__ void __launch_bounds__(P2_THREADS) pcg2_kernel(const __grid_constant_
 }
 
 template <int DIM>
-topo_status solve_stencil_fp64(topo_ctx* c, const double* rho, const double* F, double* U, int m, int ld, double rtol,
-                               int maxit, topo_solve_info* info_host) {
+__global__ void __launch_bounds__(P2_THREADS) pcg2_kernel(const __grid_constant__ Pcg2Args<DIM> a) {
+  pcg2_body<DIM>(a, gridDim.x, blockIdx.x, a.gb);
+}
+
+// Batched form: CTA b works on instance cta_inst[b] as number cta_rank[b] of that instance's
+// group of grp_size[instance] CTAs; every instance has its own barrier state and progresses on
+// its own (no barrier spans instances).
+template <int DIM>
+__global__ void __launch_bounds__(256) pcg2_batch_kernel(const Pcg2Args<DIM>* __restrict__ args,
+                                                                const int* __restrict__ cta_inst,
+                                                                const int* __restrict__ cta_rank,
+                                                                const int* __restrict__ grp_size) {
+  const int inst = cta_inst[blockIdx.x];
+  pcg2_body<DIM>(args[inst], (unsigned)grp_size[inst], (unsigned)cta_rank[blockIdx.x], args[inst].gb);
+}
+template __global__ void pcg2_batch_kernel<2>(const Pcg2Args<2>*, const int*, const int*, const int*);
+
+
+template <int DIM>
+topo_status build_pcg2_args(topo_ctx* c, const double* rho, const double* F, double* U, int m, int ld, double rtol,
+                            int maxit, int G, Pcg2Args<DIM>* out, GridSync* status) {
   const Grid& g = c->g;
   const long long N = g.ndof;
-  const long long nunits = (long long)((g.nnx + 31) / 32) * g.nny * g.nnz;
-  int occ = 0;
-  TOPO_CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pcg2_kernel<DIM>, P2_THREADS, 0));
-  if (occ < 1) return fail(c, TOPO_ERR_CUDA, "pcg2 kernel cannot be resident");
-  const int per_sm = c->pcg_blocks_per_sm > 0 ? std::min(c->pcg_blocks_per_sm, occ) : std::min(occ, 2);
-  long long G = (long long)per_sm * c->num_sms;
-  const long long maxG = (nunits + 7) / 8;  // at least one unit per warp
-  if (G > maxG) G = std::max(1LL, maxG);
   size_t off = 0;
   auto take = [&](size_t bytes) {
     size_t o = off;
@@ -396,11 +407,11 @@ topo_status solve_stencil_fp64(topo_ctx* c, const double* rho, const double* F, 
   const size_t oC = take((size_t)StencilGeom<DIM>::NC * g.nnodes * 8), oD = take(N * 8);
   size_t ov[5];
   for (int t = 0; t < 5; ++t) ov[t] = take(N * m * 8);
-  const size_t opart = take(sizeof(double) * 3 * m * G), oinfo = take(64);
+  const size_t opart = take(sizeof(double) * 4 * m * G), oinfo = take(64);
   topo_status st = ensure_scratch(c, off);
   if (st) return st;
   char* base = (char*)c->d_scratch;
-  Pcg2Args<DIM> a;
+  Pcg2Args<DIM>& a = *out;
   a.g = g;
   if (DIM == 2)
     memcpy(&a.ke, &c->q4_64, sizeof(a.ke));
@@ -412,7 +423,7 @@ topo_status solve_stencil_fp64(topo_ctx* c, const double* rho, const double* F, 
   a.ld = ld;
   a.m = m;
   a.N = N;
-  a.nunits = nunits;
+  a.nunits = (long long)((g.nnx + 31) / 32) * g.nny * g.nnz;
   a.C = (double*)(base + oC);
   a.dinv = (double*)(base + oD);
   double** vecs[5] = {&a.r, &a.z, &a.w, &a.p, &a.s};
@@ -420,11 +431,49 @@ topo_status solve_stencil_fp64(topo_ctx* c, const double* rho, const double* F, 
   a.partial = (double*)(base + opart);
   a.info = (int*)(base + oinfo);
   a.info_rr = (double*)(base + oinfo + 16);
-  a.gs = c->d_sync;
+  a.gs = status;
   a.gb = c->d_bar;
   a.rtol = rtol;
   a.maxit = maxit;
   a.wait_cycles = c->wait_cycles;
+  return TOPO_OK;
+}
+
+cudaError_t launch_pcg2_batch2(unsigned ctas, cudaStream_t stream, const Pcg2Args<2>* args, const int* cta_inst,
+                               const int* cta_rank, const int* grp_size) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(ctas);
+  cfg.blockDim = dim3(P2_THREADS);
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, pcg2_batch_kernel<2>, args, cta_inst, cta_rank, grp_size);
+}
+
+int pcg2_occupancy() {
+  int occ = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pcg2_batch_kernel<2>, P2_THREADS, 0);
+  return occ;
+}
+
+template <int DIM>
+topo_status solve_stencil_fp64(topo_ctx* c, const double* rho, const double* F, double* U, int m, int ld, double rtol,
+                               int maxit, topo_solve_info* info_host) {
+  const Grid& g = c->g;
+  const long long nunits = (long long)((g.nnx + 31) / 32) * g.nny * g.nnz;
+  int occ = 0;
+  TOPO_CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pcg2_kernel<DIM>, P2_THREADS, 0));
+  if (occ < 1) return fail(c, TOPO_ERR_CUDA, "pcg2 kernel cannot be resident");
+  const int per_sm = c->pcg_blocks_per_sm > 0 ? std::min(c->pcg_blocks_per_sm, occ) : std::min(occ, 2);
+  long long G = (long long)per_sm * c->num_sms;
+  const long long maxG = (nunits + 7) / 8;  // at least one unit per warp
+  if (G > maxG) G = std::max(1LL, maxG);
+  Pcg2Args<DIM> a;
+  topo_status st = build_pcg2_args<DIM>(c, rho, F, U, m, ld, rtol, maxit, (int)G, &a, c->d_sync);
+  if (st) return st;
   TOPO_CUDA_TRY(c, cudaMemsetAsync(c->d_bar, 0, sizeof(GridBar), c->stream));  // counter, generation, abort
   TOPO_CUDA_TRY(c, cudaMemsetAsync(a.info, 0, 32, c->stream));
   cudaLaunchConfig_t cfg = {};
@@ -449,6 +498,7 @@ topo_status solve_stencil_fp64(topo_ctx* c, const double* rho, const double* F, 
     info_host->iters = hinfo[0];
     info_host->outer = 0;
     info_host->relres = sqrt(hrr[0]);
+    info_host->floor = sqrt(hrr[1]);
     info_host->status = dev_status ? dev_status : hinfo[2];
     if (dev_status) {
       int zero = 0;
@@ -468,3 +518,6 @@ template topo_status solve_stencil_fp64<3>(topo_ctx*, const double*, const doubl
                                            topo_solve_info*);
 
 }  // namespace topo
+
+template topo_status topo::build_pcg2_args<2>(topo_ctx*, const double*, const double*, double*, int, int, double, int,
+                                              int, topo::Pcg2Args<2>*, topo::GridSync*);

@@ -1,0 +1,58 @@
+// Shared by pcg2.cu (the stencil PCG) and batch.cu (its batched launch).
+#pragma once
+
+#include "common.cuh"
+
+namespace topo {
+
+constexpr int P2_MAX_COLS = 32;
+constexpr int P2_THREADS = 256;
+
+template <int DIM>
+struct Pcg2Args {
+  Grid g;
+  typename KeOf<DIM, double>::type ke;
+  const double* rho;
+  const double* F;
+  double* U;
+  long long ld;
+  int m;
+  long long N;       // scratch leading dimension (= ndof)
+  long long nunits;  // ceil(nnx / 32) * nny * nnz
+  double* C;         // [NB*DIM*DIM][nnodes]
+  double* dinv;      // [N]
+  double* r;         // N x m each
+  double* z;
+  double* w;
+  double* p;
+  double* s;
+  double* partial;
+  GridSync* gs;      // sticky status
+  GridBar* gb;
+  double rtol;
+  int maxit;
+  long long wait_cycles;
+  int* info;
+  double* info_rr;
+};
+
+template <int DIM>
+struct StencilGeom {
+  static constexpr int NB = DIM == 2 ? 9 : 27;
+  static constexpr int NC = NB * DIM * DIM;  // coefficients per node
+};
+
+// Launch the batched 2D solve kernel: ctas CTAs (co-resident, cooperative) on stream.
+cudaError_t launch_pcg2_batch2(unsigned ctas, cudaStream_t stream, const Pcg2Args<2>* args, const int* cta_inst,
+                               const int* cta_rank, const int* grp_size);
+
+// Prepare one instance's solve for a group of G CTAs: scratch, stencil and vector pointers,
+// barrier state, info words. status is the sticky status word the solve reports into.
+template <int DIM>
+topo_status build_pcg2_args(topo_ctx* c, const double* rho, const double* F, double* U, int m, int ld, double rtol,
+                            int maxit, int G, Pcg2Args<DIM>* out, GridSync* status);
+
+// Resident CTAs per SM of the batched kernel.
+int pcg2_occupancy();
+
+}  // namespace topo

@@ -26,7 +26,9 @@ PREC = {"fp64": TOPO_FP64, "fp32": TOPO_FP32_REFINED, "fp32_bf16ke": TOPO_FP32_B
 EXPORTS = ["topo_create", "topo_destroy", "topo_last_error", "topo_set_param", "topo_check", "topo_sizes",
            "topo_filter", "topo_apply_K", "topo_solve_hdm", "topo_rom_build", "topo_rom_solve",
            "topo_rom_error", "topo_compliance_grad", "topo_launch_count", "topo_rom_elem",
-           "topo_rom_solve_elem", "topo_rom_solve_elem_noalloc"]
+           "topo_rom_solve_elem", "topo_rom_solve_elem_noalloc", "topo_batch_create", "topo_batch_destroy",
+           "topo_batch_last_error", "topo_batch_context", "topo_batch_solve_hdm", "topo_batch_filter",
+           "topo_batch_compliance_grad", "topo_batch_rom_solve_elem"]
 
 
 class TopoError(RuntimeError):
@@ -44,7 +46,7 @@ class topo_problem(ctypes.Structure):
 
 class topo_solve_info(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("outer", ctypes.c_int), ("relres", ctypes.c_double),
-                ("status", ctypes.c_int)]
+                ("status", ctypes.c_int), ("floor", ctypes.c_double)]
 
 
 _lib = None
@@ -77,6 +79,14 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "topo_rom_elem": ([P, P, I, I, P], I),
         "topo_rom_solve_elem": ([P, P, P, I, P, P, P, P], I),
         "topo_rom_solve_elem_noalloc": ([P, P, P, I, P, P, P, P], I),
+        "topo_batch_create": ([ctypes.POINTER(topo_problem), I, P, ctypes.POINTER(P)], I),
+        "topo_batch_destroy": ([P], I),
+        "topo_batch_last_error": ([P], ctypes.c_char_p),
+        "topo_batch_context": ([P, I, ctypes.POINTER(P)], I),
+        "topo_batch_solve_hdm": ([P, P, P, P, P, P, D, I, ctypes.POINTER(topo_solve_info)], I),
+        "topo_batch_filter": ([P, P, P, I], I),
+        "topo_batch_compliance_grad": ([P, P, P, P, P, P, P, P, P], I),
+        "topo_batch_rom_solve_elem": ([P, P, P, P, P, P, P, P], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -170,7 +180,8 @@ class Topo:
                                      PREC[prec], ctypes.byref(inf) if info else None)
         if st not in (TOPO_OK, TOPO_ERR_NOT_CONVERGED):
             self._chk(st, "topo_solve_hdm")
-        return dict(iters=inf.iters, outer=inf.outer, relres=inf.relres, status=inf.status) if info else None
+        return dict(iters=inf.iters, outer=inf.outer, relres=inf.relres, status=inf.status,
+                    floor=inf.floor) if info else None
 
     def topo_rom_build(self, rho, Usnap, Phi, H, b, f):
         m, ld = _cols(Usnap, self.N)
@@ -222,3 +233,75 @@ def _cols(t, N: int):
 
 def _ld(t, N: int) -> int:
     return _cols(t, N)[1]
+
+
+def _ptr_array(ts):
+    arr = (ctypes.c_void_p * len(ts))()
+    for i, t in enumerate(ts):
+        arr[i] = _ptr(t)
+    return arr
+
+
+def _int_array(vals):
+    return (ctypes.c_int * len(vals))(*[int(v) for v in vals])
+
+
+class TopoBatch:
+    """Batched form (topo_batch_*): many 2D problems on one stream. Lists of CUDA tensors are
+    marshalled into host pointer arrays."""
+
+    def __init__(self, problems, stream=None):
+        self.lib = load()
+        self.problems = list(problems)
+        self._masks = [np.ascontiguousarray(p.fixed, dtype=np.uint8) for p in self.problems]
+        arr = (topo_problem * len(self.problems))()
+        for i, (p, mk) in enumerate(zip(self.problems, self._masks)):
+            arr[i] = topo_problem(p.dim, p.nx, p.ny, 1, p.E0, p.Emin, p.nu, p.penal, p.rmin,
+                                  mk.ctypes.data_as(ctypes.POINTER(ctypes.c_ubyte)))
+        h = ctypes.c_void_p()
+        st = self.lib.topo_batch_create(arr, len(self.problems), _stream_handle(stream), ctypes.byref(h))
+        if st != TOPO_OK:
+            raise TopoError(st, "topo_batch_create failed")
+        self.h = h
+        self.count = len(self.problems)
+
+    def _chk(self, st, what):
+        if st != TOPO_OK:
+            raise TopoError(st, f"{what}: {self.lib.topo_batch_last_error(self.h).decode(errors='replace')}")
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.topo_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def topo_batch_filter(self, xs, outs, adjoint=False):
+        self._chk(self.lib.topo_batch_filter(self.h, _ptr_array(xs), _ptr_array(outs), int(adjoint)), "topo_batch_filter")
+
+    def topo_batch_solve_hdm(self, rhos, Fs, Us, rtol=1e-8, maxit=200000, info=True):
+        ms, lds = zip(*[_cols(F, 0) for F in Fs])
+        inf = (topo_solve_info * self.count)() if info else None
+        st = self.lib.topo_batch_solve_hdm(self.h, _ptr_array(rhos), _ptr_array(Fs), _ptr_array(Us), _int_array(ms),
+                                           _int_array(lds), float(rtol), int(maxit), inf)
+        if st not in (TOPO_OK, TOPO_ERR_NOT_CONVERGED):
+            self._chk(st, "topo_batch_solve_hdm")
+        if not info:
+            return None
+        return [dict(iters=x.iters, relres=x.relres, status=x.status, floor=x.floor) for x in inf]
+
+    def topo_batch_compliance_grad(self, rhos, Us, Fs, J, dcs, dpsis=None):
+        ms, lds = zip(*[_cols(U, 0) for U in Us])
+        self._chk(self.lib.topo_batch_compliance_grad(self.h, _ptr_array(rhos), _ptr_array(Us), _int_array(ms),
+                                                      _int_array(lds), _ptr_array(Fs), _ptr(J), _ptr_array(dcs),
+                                                      _ptr_array(dpsis) if dpsis is not None else None),
+                  "topo_batch_compliance_grad")
+
+    def topo_batch_rom_solve_elem(self, rhos, Hels, ks, bs, Hws, ys, Jk):
+        self._chk(self.lib.topo_batch_rom_solve_elem(self.h, _ptr_array(rhos), _ptr_array(Hels), _int_array(ks),
+                                                     _ptr_array(bs), _ptr_array(Hws), _ptr_array(ys), _ptr(Jk)),
+                  "topo_batch_rom_solve_elem")
