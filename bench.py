@@ -40,6 +40,7 @@ CONFIGS = {
     "mbb60x20": dict(kind="q4", shape=(60, 20), rmin=1.5),
     "cant96x48x48": dict(kind="h8", shape=(96, 48, 48), rmin=2.0),
     "batch256": dict(kind="batch", count=256),
+    "serving": dict(kind="serving"),
 }
 
 
@@ -462,6 +463,32 @@ def run_batch(args):
                          "frac": flops / (ms * 1e-3) / fp64_peak, "traffic": None}}
 
 
+def run_serving(args):
+    """Serving form: a seeded Poisson stream of trust-region design evaluations, 50/50 2D Q4
+    (100x50 .. 800x400) and 3D H8 (32^3 .. 96x48x48), admitted by free HBM into slots that
+    overlap on the GPU. Reports evals/s and p50/p99 latency (arrival to completion)."""
+    import torch
+    from paper_2004_05756_gb300 import serving
+
+    torch.cuda.set_device(0)
+    srv = serving.Server(slots=args.slots)
+    warm = serving.poisson_requests(2, rate_per_s=100.0, seed=99, q4=((100, 50), (120, 60)),
+                                    h8=((16, 16, 16), (20, 20, 20)))
+    srv.run(warm, realtime=False)
+    reqs = serving.poisson_requests(args.requests, rate_per_s=args.rate, seed=7)
+    t0 = time.perf_counter()
+    res = srv.run(reqs, realtime=True)
+    wall = time.perf_counter() - t0
+    s = serving.summarize(res, wall)
+    return {"metric": METRIC, "value": s["evals_per_s"], "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 1,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"serving: {len(reqs)} Poisson requests at {args.rate}/s, 50/50 Q4 100x50..800x400 "
+                                   f"and H8 32^3..96x48x48, {args.slots} slots", "slots": args.slots,
+                       "rate_per_s": args.rate},
+            "p50_ms": s["p50_ms"], "p99_ms": s["p99_ms"], "hdm_fallbacks": s["hdm_fallbacks"],
+            "max_concurrency": srv.max_concurrency, "wall_s": wall}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -477,6 +504,9 @@ def main():
     ap.add_argument("--rom-path", default="elem", choices=["elem", "phi"],
                     help="reduced matrix from cached element reduced matrices, or from K(rho) Phi")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--slots", type=int, default=4, help="serving: concurrent request slots")
+    ap.add_argument("--requests", type=int, default=32, help="serving: requests in the stream")
+    ap.add_argument("--rate", type=float, default=2.0, help="serving: Poisson arrival rate (requests/s)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -518,6 +548,9 @@ def main():
 
     if args.config == "batch256":
         print(json.dumps(run_batch(args)), flush=True)
+        return
+    if args.config == "serving":
+        print(json.dumps(run_serving(args)), flush=True)
         return
     out, p, psi0 = run_ours(args, rank, world)
     if rank == 0:

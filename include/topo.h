@@ -84,8 +84,11 @@ typedef enum {
   TOPO_PARAM_TILE_X = 4,       /* apply tile width in nodes (autotuner hint; 0 = default) */
   TOPO_PARAM_PCG_BLOCKS_PER_SM = 5, /* CTAs per SM of the persistent PCG (0 = occupancy) */
   TOPO_PARAM_INNER_CAP = 6,        /* max FP32 inner iterations per refinement step (default 2000) */
-  TOPO_PARAM_HDM_KERNEL = 7        /* FP64 solve: 0 = K(rho) assembled once per solve as a per-node
+  TOPO_PARAM_HDM_KERNEL = 7,       /* FP64 solve: 0 = K(rho) assembled once per solve as a per-node
                                       stencil, Chronopoulos-Gear PCG (default); 1 = element-form PCG */
+  TOPO_PARAM_PCG_MAX_CTAS = 8      /* cap on the CTAs of one persistent FP64 solve (0 = whole GPU);
+                                      lets solves of several contexts share the GPU concurrently and
+                                      fixes their reduction order independently of load */
 } topo_param;
 
 /* Create a context for one problem; computes K_e (2x2(x2) Gauss quadrature), the filter

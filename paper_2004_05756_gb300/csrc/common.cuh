@@ -515,6 +515,7 @@ struct topo_ctx {
   int pcg_blocks_per_sm;
   int inner_cap;
   int hdm_kernel;  // 0: assembled-stencil Chronopoulos-Gear PCG (FP64); 1: element-form PCG
+  int pcg_max_ctas;  // cap on the CTAs of one persistent solve (0 = none)
   char err[512];
 };
 

@@ -500,6 +500,10 @@ extern "C" topo_status topo_set_param(topo_ctx* c, topo_param which, double v) {
       if (!(v >= 1 && v <= 1e7)) return fail(c, TOPO_ERR_INVALID, "inner cap must be in [1,1e7]");
       c->inner_cap = (int)v;
       return TOPO_OK;
+    case TOPO_PARAM_PCG_MAX_CTAS:
+      if (!(v >= 0 && v <= 1e6)) return fail(c, TOPO_ERR_INVALID, "max CTAs must be in [0,1e6]");
+      c->pcg_max_ctas = (int)v;
+      return TOPO_OK;
     case TOPO_PARAM_HDM_KERNEL:
       if (!(v == 0 || v == 1)) return fail(c, TOPO_ERR_INVALID, "hdm kernel must be 0 or 1");
       c->hdm_kernel = (int)v;

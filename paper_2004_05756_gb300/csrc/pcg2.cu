@@ -469,6 +469,7 @@ topo_status solve_stencil_fp64(topo_ctx* c, const double* rho, const double* F, 
   if (occ < 1) return fail(c, TOPO_ERR_CUDA, "pcg2 kernel cannot be resident");
   const int per_sm = c->pcg_blocks_per_sm > 0 ? std::min(c->pcg_blocks_per_sm, occ) : std::min(occ, 2);
   long long G = (long long)per_sm * c->num_sms;
+  if (c->pcg_max_ctas > 0 && G > c->pcg_max_ctas) G = c->pcg_max_ctas;  // a share of the GPU
   const long long maxG = (nunits + 7) / 8;  // at least one unit per warp
   if (G > maxG) G = std::max(1LL, maxG);
   Pcg2Args<DIM> a;
