@@ -354,6 +354,7 @@ def run_ours(args, rank, world):
     # apply 2 * 3^d * d (36 in 2D, 162 in 3D), delta 2, the five updates, z and the two dots 13.
     hdm_ms = statistics.fmean(stats["hdm"])
     iters = statistics.fmean(stats["iters"])
+    outer = statistics.fmean(stats["outer"])
     flop_dof = 51.0 if p.dim == 2 else 177.0
     flops_launch = N * flop_dof * iters
     # FP64 peak derived from unit counts and clocks: 152 SMs x 2 FP64 FMA/clk (4 flop) x 2.07 GHz

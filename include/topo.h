@@ -86,9 +86,13 @@ typedef enum {
   TOPO_PARAM_INNER_CAP = 6,        /* max FP32 inner iterations per refinement step (default 2000) */
   TOPO_PARAM_HDM_KERNEL = 7,       /* FP64 solve: 0 = K(rho) assembled once per solve as a per-node
                                       stencil, Chronopoulos-Gear PCG (default); 1 = element-form PCG */
-  TOPO_PARAM_PCG_MAX_CTAS = 8      /* cap on the CTAs of one persistent FP64 solve (0 = whole GPU);
+  TOPO_PARAM_PCG_MAX_CTAS = 8,     /* cap on the CTAs of one persistent FP64 solve (0 = whole GPU);
                                       lets solves of several contexts share the GPU concurrently and
                                       fixes their reduction order independently of load */
+  TOPO_PARAM_ROM_TENSOR = 9        /* contraction Phi^T W of the FP32 projection forms of
+                                      topo_rom_solve: 1 = tensor cores (tcgen05 kind::tf32 on an exact
+                                      hi/lo split of each FP32 operand, FP32 accumulate per 256 rows,
+                                      FP64 beyond; default), 0 = SIMT FP32 */
 } topo_param;
 
 /* Create a context for one problem; computes K_e (2x2(x2) Gauss quadrature), the filter

@@ -93,6 +93,28 @@ def apply_K(p, rho: np.ndarray, V: np.ndarray) -> np.ndarray:
     return Y[:, 0] if one else Y
 
 
+def apply_K_ebe(p, rho: np.ndarray, V: np.ndarray) -> np.ndarray:
+    """The same operator as apply_K, element by element without assembly (Section 2.1):
+    Y = sum_e E(rho_e) P_e K_e P_e^T V0 with V0 = V zeroed on the Dirichlet DOFs, then Y_d = V_d.
+    For meshes whose assembled matrix is too large to build in seconds (N x m)."""
+    V = np.asarray(V, dtype=float)
+    one = V.ndim == 1
+    V2 = (V[:, None] if one else V).copy()
+    d = fixed_dofs(p)
+    V0 = V2.copy()
+    V0[d] = 0.0
+    Ke = element.ke(p.dim, p.nu)
+    ed = edof(p)
+    E = young(rho, p.E0, p.Emin, p.penal)
+    Y = np.zeros_like(V2)
+    for j in range(V2.shape[1]):
+        Ve = V0[ed, j]                         # N_e x ndof_e
+        Ye = E[:, None] * (Ve @ Ke.T)          # E_e K_e v_e per element
+        Y[:, j] = np.bincount(ed.ravel(), weights=Ye.ravel(), minlength=p.ndof)
+    Y[d] = V2[d]
+    return Y[:, 0] if one else Y
+
+
 def jacobi_diag(p, rho: np.ndarray) -> np.ndarray:
     """diag(K) on free DOFs, 1 on Dirichlet DOFs (the Jacobi preconditioner)."""
     K = assemble_K(p, rho)

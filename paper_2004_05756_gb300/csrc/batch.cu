@@ -154,6 +154,8 @@ static topo_status batch_solve_dim(topo_batch* b, const double* const* rho, cons
                                            cudaMemcpyHostToDevice, b->stream));
   for (int i = 0; i < n; ++i) {
     TOPO_CUDA_TRY(b->ctx[0], cudaMemsetAsync(b->ctx[i]->d_bar, 0, sizeof(GridBar), b->stream));
+    TOPO_CUDA_TRY(b->ctx[0],
+                  cudaMemsetAsync(args[i].zflag, 0, sizeof(unsigned long long) * plan.grp[i], b->stream));
     TOPO_CUDA_TRY(b->ctx[0], cudaMemsetAsync(args[i].info, 0, 32, b->stream));
   }
   for (int wv = 0; wv < plan.waves; ++wv) {

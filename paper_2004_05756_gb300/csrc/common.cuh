@@ -332,6 +332,28 @@ __device__ inline double block_sum(double v, double* red) {
   return t;
 }
 
+// Three block sums at once, each in the order of block_sum (so bitwise the same results);
+// valid in thread 0. red must hold 3 * 32 doubles.
+__device__ inline void block_sum3(double& a, double& b, double& c, double* red) {
+  a = warp_sum(a);
+  b = warp_sum(b);
+  c = warp_sum(c);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) {
+    red[w] = a;
+    red[32 + w] = b;
+    red[64 + w] = c;
+  }
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const int nw = blockDim.x >> 5;
+    a = warp_sum((l < nw) ? red[l] : 0.0);
+    b = warp_sum((l < nw) ? red[32 + l] : 0.0);
+    c = warp_sum((l < nw) ? red[64 + l] : 0.0);
+  }
+  __syncthreads();
+}
+
 // ---------------------------------------------------------------------------------------
 // Grid-wide barrier for cooperative (co-resident) launches, with a deterministic reduction
 // folded in: each CTA has written partial[j * G + cta] for j < nred; the last CTA to arrive
@@ -516,6 +538,7 @@ struct topo_ctx {
   int inner_cap;
   int hdm_kernel;  // 0: assembled-stencil Chronopoulos-Gear PCG (FP64); 1: element-form PCG
   int pcg_max_ctas;  // cap on the CTAs of one persistent solve (0 = none)
+  int rom_tensor;    // FP32 projection contraction: 1 tensor cores (tcgen05), 0 SIMT FP32
   char err[512];
 };
 
@@ -537,6 +560,11 @@ topo_status launch_residual64(topo_ctx* c, const double* rho, const double* u, c
                               double* out2);
 // Deterministic sum of n doubles -> *out (device), two passes.
 topo_status launch_sum(topo_ctx* c, const double* x, long long n, double* out);
+// Tensor-core contraction (tcgen05, kind::tf32 with an exact hi/lo split of each FP32 operand):
+// per-CTA FP64 partials of A^T B into partial[g * k1 * k2 + i * k2 + j], g < *G_out. A, B are
+// FP32 column-major N x k1 / N x k2, 16-byte aligned, lda and ldb multiples of 4; k1, k2 <= 128.
+topo_status launch_atb_tc_partial(topo_ctx* c, const float* A, long long lda, int k1, const float* B, long long ldb,
+                                  int k2, long long N, double* partial, size_t partial_cap, int* G_out);
 
 #define TOPO_CUDA_TRY(ctx, expr)                         \
   do {                                                   \

@@ -334,6 +334,7 @@ extern "C" topo_status topo_create(const topo_problem* prob, void* cuda_stream, 
   c->inner_rtol = 1e-5;
   c->max_outer = 30;
   c->wait_cycles = 2000000000LL;
+  c->rom_tensor = 1;
   c->rom_refine = 8;
   c->pcg_blocks_per_sm = 0;
   c->inner_cap = 2000;
@@ -507,6 +508,10 @@ extern "C" topo_status topo_set_param(topo_ctx* c, topo_param which, double v) {
     case TOPO_PARAM_HDM_KERNEL:
       if (!(v == 0 || v == 1)) return fail(c, TOPO_ERR_INVALID, "hdm kernel must be 0 or 1");
       c->hdm_kernel = (int)v;
+      return TOPO_OK;
+    case TOPO_PARAM_ROM_TENSOR:
+      if (!(v == 0 || v == 1)) return fail(c, TOPO_ERR_INVALID, "rom tensor must be 0 or 1");
+      c->rom_tensor = (int)v;
       return TOPO_OK;
     case TOPO_PARAM_PCG_BLOCKS_PER_SM:
       if (!(v >= 0 && v <= 8)) return fail(c, TOPO_ERR_INVALID, "blocks per SM must be in [0,8]");

@@ -118,6 +118,32 @@ template <int DIM>
 __device__ __forceinline__ void stencil_apply(const Grid& g, const double* __restrict__ C, const double* v, int i,
                                               int j, int k, long long n, double* y) {
   constexpr int NB = StencilGeom<DIM>::NB;
+  if constexpr (DIM == 2) {
+    // Branch-free: a neighbour outside the grid has all-zero coefficients (assembly), so its
+    // value is read at the node itself and contributes fma(0, v, y) = y exactly. All 18 values
+    // and 36 coefficients are loaded before the first FMA (one L2 round trip per node).
+    double vv[NB][2], cc[NB][4];
+#pragma unroll
+    for (int nb = 0; nb < NB; ++nb) {
+      const int ii = i + nb % 3 - 1, jj = j + nb / 3 - 1;
+      const bool nin = ii >= 0 && ii < g.nnx && jj >= 0 && jj < g.nny;
+      const long long m = nin ? ii + (long long)g.nnx * jj : n;
+      vv[nb][0] = __ldcg(v + 2 * m);
+      vv[nb][1] = __ldcg(v + 2 * m + 1);
+    }
+#pragma unroll
+    for (int nb = 0; nb < NB; ++nb)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) cc[nb][q] = __ldg(C + (long long)(nb * 4 + q) * g.nnodes + n);
+    y[0] = y[1] = 0.0;
+#pragma unroll
+    for (int nb = 0; nb < NB; ++nb)
+#pragma unroll
+      for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int d = 0; d < 2; ++d) y[r] = fma(cc[nb][r * 2 + d], vv[nb][d], y[r]);
+    return;
+  }
 #pragma unroll
   for (int r = 0; r < DIM; ++r) y[r] = 0.0;
 #pragma unroll
@@ -142,24 +168,30 @@ __device__ __forceinline__ void stencil_apply(const Grid& g, const double* __res
 template <int DIM>
 __device__ __forceinline__ void pcg2_body(const Pcg2Args<DIM>& a, const unsigned G, const unsigned rank,
                                           GridBar* gb) {
-  __shared__ double red[32];
+  __shared__ double red[96];
   __shared__ double sh_gamma[P2_MAX_COLS], sh_alpha[P2_MAX_COLS], sh_beta[P2_MAX_COLS], sh_tol2[P2_MAX_COLS],
       sh_ff[P2_MAX_COLS], sh_rr[P2_MAX_COLS];
   __shared__ int sh_done[P2_MAX_COLS];
   __shared__ double sh_sum[4 * P2_MAX_COLS];
   __shared__ double sh_floor2[P2_MAX_COLS];
+  __shared__ int s_okw;
   const Grid& g = a.g;
   const int m = a.m;
   const long long N = a.N;
   GridSync* gs = a.gs;
-  unsigned long long bar = 0;
+  unsigned long long bar = 0;  // grid barriers passed
   double* part = a.partial;
-  auto P = [&](int slot, int c) -> double* { return part + ((size_t)(slot * m + c)) * G + rank; };
+  // Partials written before barrier number bar + 1 go to buffer (bar + 1) & 1 and are read
+  // after it; a CTA can only reuse a buffer after the next barrier, i.e. after every CTA has
+  // finished reading it.
+  auto P = [&](int slot, int c) -> double* {
+    return part + ((size_t)((((bar + 1) & 1) * 4 + slot) * m + c)) * G + rank;
+  };
   auto R = [&](int slot, int c) -> double { return sh_sum[slot * m + c]; };
   // grid barrier, then every CTA reduces the per-CTA partials of nred slots itself
   auto sync_reduce = [&](int nred) -> bool {
     if (!grid_barrier(gb, &gs->status, bar, a.wait_cycles, G)) return false;
-    if (nred > 0) reduce_slots(part, G, nred, sh_sum);
+    if (nred > 0) reduce_slots(part + (size_t)((bar & 1) * 4 * m) * G, G, nred, sh_sum);
     return true;
   };
   // this CTA's units: a contiguous, balanced range
@@ -176,6 +208,53 @@ __device__ __forceinline__ void pcg2_body(const Pcg2Args<DIM>& a, const unsigned
       fn(i, j, kz, n);
     }
   };
+  // CTAs owning the nodes whose z the apply of this CTA's nodes reads: units within `span` of
+  // the own range (one x-row (and one z-plane) plus one unit on either side).
+  const long long ux = (g.nnx + 31) / 32;
+  const long long span = DIM == 2 ? ux + 1 : ux * g.nny + ux + 1;
+  auto owner = [&](long long u) -> long long {
+    long long b = u * (long long)G / a.nunits;
+    while (b + 1 < (long long)G && a.nunits * (b + 1) / G <= u) ++b;
+    while (b > 0 && a.nunits * b / G > u) --b;
+    return b;
+  };
+  const long long nb_lo = u1 > u0 ? owner(max(0LL, u0 - span)) : (long long)rank;
+  const long long nb_hi = u1 > u0 ? owner(min(a.nunits - 1, u1 - 1 + span)) : (long long)rank;
+  unsigned long long zseq = 0;  // phase-U completions so far (the same on every CTA)
+  // after phase U: z of the owned nodes is complete
+  auto publish_z = [&]() {
+    __syncthreads();
+    ++zseq;
+    if (threadIdx.x == 0) {
+      __threadfence();
+      cuda::atomic_ref<unsigned long long, cuda::thread_scope_device> f(a.zflag[rank]);
+      f.store(zseq, cuda::memory_order_release);
+    }
+  };
+  // before phase W: every neighbour has published the same z (bounded wait)
+  auto wait_z = [&]() -> bool {
+    if (threadIdx.x == 0) s_okw = 1;
+    __syncthreads();
+    for (long long q = nb_lo + threadIdx.x; q <= nb_hi; q += blockDim.x) {
+      if (q == (long long)rank) continue;
+      cuda::atomic_ref<unsigned long long, cuda::thread_scope_device> f(a.zflag[q]);
+      const long long t0 = clock64();
+      while (f.load(cuda::memory_order_acquire) < zseq) {
+        if (*(volatile int*)&gb->abort) {
+          s_okw = 0;
+          break;
+        }
+        if (clock64() - t0 > a.wait_cycles) {
+          atomicCAS(&gs->status, 0, (int)TOPO_ERR_TIMEOUT);
+          atomicExch(&gb->abort, 1);
+          s_okw = 0;
+          break;
+        }
+      }
+    }
+    __syncthreads();
+    return s_okw != 0;
+  };
 
   // --- stencil assembly and Jacobi diagonal ----------------------------------------------
   for_owned([&](int i, int j, int k, long long n) {
@@ -189,9 +268,9 @@ __device__ __forceinline__ void pcg2_body(const Pcg2Args<DIM>& a, const unsigned
   });
   if (!sync_reduce(0)) return;
 
-  // --- true residual r = f - K x, z = D^-1 r, w = K z (two phases) ------------------------
-  // Phase T1: r, z for owned nodes (x = caller's U, Dirichlet entries zeroed), partial gamma,
-  // r.r, f.f.
+  // --- true residual r = f - K x, z = D^-1 r -----------------------------------------------
+  // r, z for owned nodes (x = caller's U, Dirichlet entries zeroed), partial gamma, r.r, f.f,
+  // (|K||x|)^2; one barrier (it also publishes z to every CTA).
   auto true_residual = [&](bool first) -> bool {
     double acc[4][P2_MAX_COLS];
     for (int c = 0; c < m; ++c) acc[0][c] = acc[1][c] = acc[2][c] = acc[3][c] = 0.0;
@@ -244,8 +323,16 @@ __device__ __forceinline__ void pcg2_body(const Pcg2Args<DIM>& a, const unsigned
     return true;
   };
 
-  // Phase W: w = K z for owned nodes, partial delta = w.z; then alpha (first step: beta = 0).
+  // gamma = r.z and r.r of the last phase U, per thread, until phase W reduces them
+  double accg[P2_MAX_COLS], accr[P2_MAX_COLS];
+
+  // Phase W: w = K z for owned nodes and partial delta = w.z; one grid barrier reduces delta
+  // together with gamma and r.r of the preceding phase U (Chronopoulos-Gear: one reduction
+  // per iteration). Then beta = gamma_new / gamma, the convergence test on r.r, and
+  // alpha = gamma / (delta - beta gamma / alpha_old) (restart: beta = 0, alpha = gamma / delta,
+  // gamma and r.r come from the true residual).
   auto phase_w = [&](bool restart) -> bool {
+    if (!restart && !wait_z()) return false;
     double acc[P2_MAX_COLS];
     for (int c = 0; c < m; ++c) acc[c] = 0.0;
     for (int c = 0; c < m; ++c) {
@@ -263,13 +350,28 @@ __device__ __forceinline__ void pcg2_body(const Pcg2Args<DIM>& a, const unsigned
       });
     }
     for (int c = 0; c < m; ++c) {
-      const double t = block_sum(acc[c], red);
-      if (threadIdx.x == 0) *P(0, c) = t;
+      double t0 = acc[c], t1 = restart ? 0.0 : accg[c], t2 = restart ? 0.0 : accr[c];
+      block_sum3(t0, t1, t2, red);
+      if (threadIdx.x == 0) {
+        *P(0, c) = t0;
+        *P(1, c) = t1;
+        *P(2, c) = t2;
+      }
     }
-    if (!sync_reduce(m)) return false;
+    if (!sync_reduce(3 * m)) return false;
     if (threadIdx.x == 0) {
       for (int c = 0; c < m; ++c) {
         if (sh_done[c]) continue;
+        if (!restart) {
+          const double gnew = R(1, c);
+          sh_beta[c] = gnew / sh_gamma[c];
+          sh_gamma[c] = gnew;
+          sh_rr[c] = R(2, c);
+          if (sh_rr[c] <= sh_tol2[c]) {
+            sh_done[c] = 1;
+            continue;
+          }
+        }
         const double delta = R(0, c);
         if (restart) {
           sh_beta[c] = 0.0;
@@ -288,10 +390,9 @@ __device__ __forceinline__ void pcg2_body(const Pcg2Args<DIM>& a, const unsigned
     return true;
   };
 
-  // Phase U: p = z + beta p, s = w + beta s, x += alpha p, r -= alpha s, z = D^-1 r; partial
-  // gamma = r.z and r.r; then beta for the next step.
-  auto phase_u = [&](bool restart) -> bool {
-    double accg[P2_MAX_COLS], accr[P2_MAX_COLS];
+  // Phase U: p = z + beta p, s = w + beta s, x += alpha p, r -= alpha s, z = D^-1 r; per-thread
+  // gamma = r.z and r.r (reduced by the next phase W); then z is published to the neighbours.
+  auto phase_u = [&](bool restart) {
     for (int c = 0; c < m; ++c) accg[c] = accr[c] = 0.0;
     for (int c = 0; c < m; ++c) {
       if (sh_done[c]) continue;
@@ -316,27 +417,7 @@ __device__ __forceinline__ void pcg2_body(const Pcg2Args<DIM>& a, const unsigned
         }
       });
     }
-    for (int c = 0; c < m; ++c) {
-      const double t1 = block_sum(accg[c], red);
-      const double t2 = block_sum(accr[c], red);
-      if (threadIdx.x == 0) {
-        *P(0, c) = t1;
-        *P(1, c) = t2;
-      }
-    }
-    if (!sync_reduce(2 * m)) return false;
-    if (threadIdx.x == 0) {
-      for (int c = 0; c < m; ++c) {
-        if (sh_done[c]) continue;
-        const double gnew = R(0, c);
-        sh_beta[c] = gnew / sh_gamma[c];
-        sh_gamma[c] = gnew;
-        sh_rr[c] = R(1, c);
-        if (sh_rr[c] <= sh_tol2[c]) sh_done[c] = 1;
-      }
-    }
-    __syncthreads();
-    return true;
+    publish_z();
   };
 
   int iters = 0;
@@ -346,16 +427,18 @@ __device__ __forceinline__ void pcg2_body(const Pcg2Args<DIM>& a, const unsigned
     for (int c = 0; c < m; ++c) all = all && sh_done[c];
     if (all || iters >= a.maxit) break;
     bool restart = true;
-    while (iters < a.maxit) {
+    while (true) {
+      if (!phase_w(restart)) return;
       bool any = false;
       for (int c = 0; c < m; ++c) any = any || !sh_done[c];
-      if (!any) break;
-      if (!phase_w(restart)) return;
-      if (!phase_u(restart)) return;
+      if (!any || iters >= a.maxit) break;
+      phase_u(restart);
       restart = false;
       ++iters;
     }
-    if (!true_residual(false)) return;  // residual replacement: restart from the true residual
+    // residual replacement: restart from the true residual (the last phase W's barrier has
+    // made every CTA's x visible)
+    if (!true_residual(false)) return;
   }
   if (rank == 0 && threadIdx.x == 0) {
     double worst = 0.0, wfloor = 0.0;
@@ -375,7 +458,7 @@ __device__ __forceinline__ void pcg2_body(const Pcg2Args<DIM>& a, const unsigned
 }
 
 template <int DIM>
-__global__ void __launch_bounds__(P2_THREADS) pcg2_kernel(const __grid_constant__ Pcg2Args<DIM> a) {
+__global__ void __launch_bounds__(P2_THREADS, 2) pcg2_kernel(const __grid_constant__ Pcg2Args<DIM> a) {
   pcg2_body<DIM>(a, gridDim.x, blockIdx.x, a.gb);
 }
 
@@ -383,7 +466,7 @@ __global__ void __launch_bounds__(P2_THREADS) pcg2_kernel(const __grid_constant_
 // group of grp_size[instance] CTAs; every instance has its own barrier state and progresses on
 // its own (no barrier spans instances).
 template <int DIM>
-__global__ void __launch_bounds__(256) pcg2_batch_kernel(const Pcg2Args<DIM>* __restrict__ args,
+__global__ void __launch_bounds__(P2_THREADS, 2) pcg2_batch_kernel(const Pcg2Args<DIM>* __restrict__ args,
                                                                 const int* __restrict__ cta_inst,
                                                                 const int* __restrict__ cta_rank,
                                                                 const int* __restrict__ grp_size) {
@@ -407,7 +490,8 @@ topo_status build_pcg2_args(topo_ctx* c, const double* rho, const double* F, dou
   const size_t oC = take((size_t)StencilGeom<DIM>::NC * g.nnodes * 8), oD = take(N * 8);
   size_t ov[5];
   for (int t = 0; t < 5; ++t) ov[t] = take(N * m * 8);
-  const size_t opart = take(sizeof(double) * 4 * m * G), oinfo = take(64);
+  const size_t opart = take(sizeof(double) * 8 * m * G), oflag = take(sizeof(unsigned long long) * G),
+               oinfo = take(64);
   topo_status st = ensure_scratch(c, off);
   if (st) return st;
   char* base = (char*)c->d_scratch;
@@ -429,6 +513,7 @@ topo_status build_pcg2_args(topo_ctx* c, const double* rho, const double* F, dou
   double** vecs[5] = {&a.r, &a.z, &a.w, &a.p, &a.s};
   for (int t = 0; t < 5; ++t) *vecs[t] = (double*)(base + ov[t]);
   a.partial = (double*)(base + opart);
+  a.zflag = (unsigned long long*)(base + oflag);
   a.info = (int*)(base + oinfo);
   a.info_rr = (double*)(base + oinfo + 16);
   a.gs = status;
@@ -476,6 +561,7 @@ topo_status solve_stencil_fp64(topo_ctx* c, const double* rho, const double* F, 
   topo_status st = build_pcg2_args<DIM>(c, rho, F, U, m, ld, rtol, maxit, (int)G, &a, c->d_sync);
   if (st) return st;
   TOPO_CUDA_TRY(c, cudaMemsetAsync(c->d_bar, 0, sizeof(GridBar), c->stream));  // counter, generation, abort
+  TOPO_CUDA_TRY(c, cudaMemsetAsync(a.zflag, 0, sizeof(unsigned long long) * G, c->stream));
   TOPO_CUDA_TRY(c, cudaMemsetAsync(a.info, 0, 32, c->stream));
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)G);

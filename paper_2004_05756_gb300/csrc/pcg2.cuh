@@ -26,7 +26,8 @@ struct Pcg2Args {
   double* w;
   double* p;
   double* s;
-  double* partial;
+  double* partial;   // [2 barrier parities][4 slots][m][G]
+  unsigned long long* zflag;  // [G]: phase-U completions of each CTA (z published), reset per launch
   GridSync* gs;      // sticky status
   GridBar* gb;
   double rtol;

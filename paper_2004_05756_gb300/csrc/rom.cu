@@ -162,11 +162,12 @@ __global__ void scale_kernel(double* x, long long N, const double* nrm) {
     x[r] *= s;
 }
 
-__global__ void to_float_kernel(const double* __restrict__ A, long long lda, int k, float* B, long long N) {
+__global__ void to_float_kernel(const double* __restrict__ A, long long lda, int k, float* B, long long ldb,
+                                long long N) {
   const long long total = N * k;
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total; t += (long long)gridDim.x * blockDim.x) {
     const long long j = t / N, r = t % N;
-    B[j * N + r] = (float)A[j * lda + r];
+    B[j * ldb + r] = (float)A[j * lda + r];
   }
 }
 
@@ -361,14 +362,25 @@ static topo_status project(topo_ctx* c, const double* rho, const double* Phi, in
     s = launch_atb<double>(c, Phi, ld, k, W, ld, k, N, partial, pcap, H, 1, gate);
     if (s) return s;
   } else {
+    // FP32 copies with a leading dimension padded to 32 rows (16-byte aligned TMA strides)
+    const long long ld32 = (N + 31) & ~31LL;
     float* P32 = (float*)p;
-    float* W32 = P32 + (size_t)N * k;
-    to_float_kernel<<<stream_blocks(c, N * k), 256, 0, c->stream>>>(Phi, ld, k, P32, N);
+    float* W32 = P32 + (size_t)ld32 * k;
+    to_float_kernel<<<stream_blocks(c, N * k), 256, 0, c->stream>>>(Phi, ld, k, P32, ld32, N);
     note_launch();
-    topo_status s = launch_apply(c, rho, P32, W32, k, (int)N, prec);
+    topo_status s = launch_apply(c, rho, P32, W32, k, (int)ld32, prec);
     if (s) return s;
-    s = launch_atb<float>(c, P32, N, k, W32, N, k, N, partial, pcap, H, 1);
-    if (s) return s;
+    if (c->rom_tensor) {
+      int G = 0;
+      s = launch_atb_tc_partial(c, P32, ld32, k, W32, ld32, k, N, partial, pcap, &G);
+      if (s) return s;
+      atb_final_kernel<<<(k * k + 255) / 256, 256, 0, c->stream>>>(partial, G, k, k, H, 1, nullptr);
+      note_launch();
+      TOPO_CUDA_TRY(c, cudaGetLastError());
+    } else {
+      s = launch_atb<float>(c, P32, ld32, k, W32, ld32, k, N, partial, pcap, H, 1);
+      if (s) return s;
+    }
   }
   if (b) return launch_atv(c, Phi, ld, k, f, N, partial, pcap, b, nullptr);
   return TOPO_OK;
@@ -381,7 +393,7 @@ static size_t project_scratch(topo_ctx* c, int k, long long ld, topo_prec prec) 
   if (prec == TOPO_FP64)
     s += (size_t)ld * k * sizeof(double);
   else
-    s += 2 * (size_t)N * k * sizeof(float);
+    s += 2 * (size_t)((N + 31) & ~31LL) * k * sizeof(float);
   return s + 256;
 }
 

@@ -3,6 +3,7 @@
     python -m paper_2004_05756_gb300.profcase --call pcg --prec fp64 --maxit 200
     python -m paper_2004_05756_gb300.profcase --call apply --prec fp32 --m 64
     python -m paper_2004_05756_gb300.profcase --call rom_solve_elem --k 16
+    python -m paper_2004_05756_gb300.profcase --call rom_solve --prec fp32 --k 64 --shape 96x48x48
 
 Workloads are the seeded benchmark problems (MBB 600x200 Q4 by default). Prints the mean
 CUDA-event time of the call, measured after one warm-up call.
@@ -32,6 +33,7 @@ def main(argv=None):
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--hdm-kernel", type=int, default=0, help="FP64 solve: 0 stencil C-G PCG, 1 element-form PCG")
     ap.add_argument("--blocks-per-sm", type=int, default=0, help="CTAs per SM of the persistent solve (0 = default)")
+    ap.add_argument("--rom-tensor", type=int, default=1, help="FP32 projection contraction: 1 tcgen05, 0 SIMT")
     a = ap.parse_args(argv)
     import torch
 
@@ -44,6 +46,7 @@ def main(argv=None):
     T = native.Topo(p)
     T.topo_set_param(native.TOPO_PARAM_HDM_KERNEL, a.hdm_kernel)
     T.topo_set_param(native.TOPO_PARAM_PCG_BLOCKS_PER_SM, a.blocks_per_sm)
+    T.topo_set_param(native.TOPO_PARAM_ROM_TENSOR, a.rom_tensor)
     f64 = dict(dtype=torch.float64, device="cuda")
     psi = torch.as_tensor(w.design_field(p, 0)).to(**f64)
     rho = torch.empty(p.nel, **f64)
@@ -99,7 +102,8 @@ def main(argv=None):
         call()
     e1.record()
     e1.synchronize()
-    print(f"{a.call} {a.prec} shape={a.shape} m={a.m} k={k} hdm_kernel={a.hdm_kernel} bps={a.blocks_per_sm}: "
+    print(f"{a.call} {a.prec} shape={a.shape} m={a.m} k={k} hdm_kernel={a.hdm_kernel} bps={a.blocks_per_sm} "
+          f"rom_tensor={a.rom_tensor}: "
           f"{e0.elapsed_time(e1) / a.reps * 1e3:.1f} us/call")
     T.topo_check()
 

@@ -128,6 +128,25 @@ def test_apply_convention():
     assert np.abs(Y - K @ V).max() < 1e-14 * np.abs(Y).max()
 
 
+@pytest.mark.parametrize("mk", [lambda: w.mbb_2d(7, 5), lambda: w.cantilever_3d(4, 3, 5), lambda: w.mbb_2d(1, 1)])
+def test_apply_element_by_element(mk):
+    """The unassembled product equals the assembled one (same convention), and on a mesh
+    without supports it annihilates the rigid-body modes."""
+    import dataclasses
+    p = mk()
+    rng = np.random.default_rng(3)
+    rho = rng.uniform(1e-3, 1, p.nel)
+    V = rng.standard_normal((p.ndof, 3))
+    Y = fem.apply_K_ebe(p, rho, V)
+    assert np.abs(Y - fem.apply_K(p, rho, V)).max() < 1e-13 * np.abs(Y).max()
+    assert np.abs(fem.apply_K_ebe(p, rho, V[:, 1]) - Y[:, 1]).max() < 1e-13 * np.abs(Y).max()
+    pf = dataclasses.replace(p, fixed=np.zeros_like(p.fixed))
+    R = _rbm(pf)
+    KR = fem.apply_K_ebe(pf, rho, R)
+    assert np.abs(KR).max() < 1e-12 * np.abs(R).max()
+    assert np.abs(fem.apply_K_ebe(pf, rho, V)).max() > 1e-3
+
+
 @pytest.mark.parametrize("prob", ["q4", "h8"])
 @pytest.mark.parametrize("filtered", [False, True])
 def test_gradient_finite_differences(prob, filtered):
