@@ -8,7 +8,8 @@
 // (128 rows) against [B_hi; B_lo] (128 columns) makes one 128 x 128 x 8 kind::tf32 MMA form all
 // four products hi*hi, hi*lo, lo*hi, lo*lo, whose sum carries about 20 significant bits per
 // product. Products accumulate in FP32 in TMEM over one segment (SEG chunks of 32 rows), then
-// in FP64 registers, then in the fixed-order FP64 sum over CTAs of the caller.
+// in compensated FP32 pairs in registers (about 2^-48 relative), then in FP64: once per CTA and
+// in the fixed-order sum over CTAs of the caller.
 //
 // Pipeline (one CTA per SM; each CTA owns a contiguous row range and one 64 x 64 output tile):
 //   warp 0     TMA producer: 32-row chunks of A and B (64 columns each) in a STAGES-deep ring,
@@ -17,9 +18,10 @@
 //              the writes to the async proxy, arrive on conv[s];
 //   warp 1     owns TMEM (two 128 x 128 FP32 accumulators); one lane issues 4 MMAs per chunk
 //              and commits empty[s] per chunk and tfull[b] per segment;
-//   warps 6-9  drain a finished accumulator with tcgen05.ld into FP64 registers (one
-//              accumulator row per thread), release it on tempty[b]; at the end rows i and
-//              64 + i are combined into the CTA's FP64 partial tile.
+//   warps 6-13 drain a finished accumulator with tcgen05.ld into compensated FP32 sums (two
+//              warps per 32-lane quarter, each thread one accumulator row and 32 of the 64
+//              output columns), release it on tempty[b]; at the end rows i and 64 + i are
+//              combined into the CTA's FP64 partial tile.
 // Every wait is bounded by wait_cycles. On expiry the CTA records TOPO_ERR_TIMEOUT, lets its
 // copies and MMAs in flight finish (bounded again), frees its TMEM and returns.
 // One CTA holds > 190 KB of shared memory, so no second CTA of this kernel (the only TMEM user
@@ -40,7 +42,7 @@ constexpr int STAGES = 6;             // chunks in flight
 constexpr int HALF = 8192;            // one 64-row x 128-B operand tile
 constexpr int STAGE_BYTES = 4 * HALF; // A_hi | A_lo | B_hi | B_lo
 constexpr int SEG = 8;                // chunks accumulated in FP32 before an FP64 drain
-constexpr int NTHREADS = 320;
+constexpr int NTHREADS = 448;       // warps 0-1 issue, 2-5 split, 6-13 drain
 constexpr int SMEM_BYTES = 1024 + STAGES * STAGE_BYTES + 512;
 
 // Instruction descriptor of tcgen05.mma kind::tf32: D FP32 (bits 4-5 = 1), A and B TF32
@@ -121,19 +123,27 @@ __device__ __forceinline__ void tc_mma(uint32_t dtmem, uint64_t adesc, uint64_t 
 __device__ __forceinline__ void tc_commit(uint32_t bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
 }
-// 16 consecutive FP32 columns of this thread's TMEM lane.
-__device__ __forceinline__ void tc_ld16(uint32_t taddr, uint32_t (&r)[16]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, "
-      "[%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr)
-      : "memory");
+// 8 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void tc_ld8(uint32_t taddr, uint32_t (&r)[8]) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr)
+               : "memory");
 }
 __device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
+
+// s + c += v, compensated (Knuth's TwoSum): s carries the rounded sum, c the accumulated
+// rounding errors, so the pair holds the running sum to about 2^-48 relative. FP32 only:
+// FP64 runs at 1/64 of the FP32 rate on this part.
+__device__ __forceinline__ void two_sum_add(float& s, float& c, float v) {
+  const float t = __fadd_rn(s, v);
+  const float bp = __fsub_rn(t, s);
+  const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(v, bp));
+  s = t;
+  c = __fadd_rn(c, err);
+}
 
 __global__ void __launch_bounds__(NTHREADS, 1)
     atb_tc_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int k1, int k2,
@@ -169,7 +179,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(su32(&tfull[b]), 1);
-      mbar_init(su32(&tempty[b]), 4);
+      mbar_init(su32(&tempty[b]), 8);
     }
     mbar_init(su32(done), 1);
     *abort_flag = 0;
@@ -271,12 +281,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       if (lane == 0) mbar_arrive(su32(&conv[s]));
     }
   } else {
-    // ---- drain: TMEM (FP32) -> FP64 registers; thread = accumulator row ----
+    // ---- drain: TMEM (FP32) -> compensated FP32 pairs in registers; thread = accumulator row ----
     const int quarter = warp & 3;  // this warp may read TMEM lanes 32 * quarter ... + 31
     const int row = 32 * quarter + lane;
-    double acc[64];
+    const int c0 = 32 * ((warp - 6) >> 2);  // output columns c0 ... c0 + 31 of the tile
+    float accs[32], accc[32];
 #pragma unroll
-    for (int j = 0; j < 64; ++j) acc[j] = 0.0;
+    for (int j = 0; j < 32; ++j) accs[j] = accc[j] = 0.0f;
     int drained = 0;
     for (int q = 0; q < nseg; ++q) {
       const int b = q & 1;
@@ -285,14 +296,16 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       tc_fence_after();
       const uint32_t ta = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)(b * 128);
 #pragma unroll
-      for (int cb = 0; cb < 64; cb += 16) {
-        uint32_t r0[16], r1[16];
-        tc_ld16(ta + cb, r0);       // [A_hi or A_lo row] x B_hi columns
-        tc_ld16(ta + 64 + cb, r1);  // [A_hi or A_lo row] x B_lo columns
+      for (int cb = 0; cb < 32; cb += 8) {
+        uint32_t r0[8], r1[8];
+        tc_ld8(ta + c0 + cb, r0);       // [A_hi or A_lo row] x B_hi columns
+        tc_ld8(ta + 64 + c0 + cb, r1);  // [A_hi or A_lo row] x B_lo columns
         tc_wait_ld();
 #pragma unroll
-        for (int i = 0; i < 16; ++i)
-          acc[cb + i] += (double)__uint_as_float(r0[i]) + (double)__uint_as_float(r1[i]);
+        for (int i = 0; i < 8; ++i) {
+          two_sum_add(accs[cb + i], accc[cb + i], __uint_as_float(r0[i]));
+          two_sum_add(accs[cb + i], accc[cb + i], __uint_as_float(r1[i]));
+        }
       }
       tc_fence_before();
       __syncwarp();
@@ -301,21 +314,21 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     }
     // combine row i (A_hi) with row 64 + i (A_lo) through shared memory; every stage is idle
     // once the last accumulator has been drained
-    asm volatile("bar.sync 1, 128;" ::: "memory");
+    asm volatile("bar.sync 1, 256;" ::: "memory");
     const bool complete = (drained == nseg) && !*abort_flag;
-    asm volatile("bar.sync 1, 128;" ::: "memory");
+    asm volatile("bar.sync 1, 256;" ::: "memory");
     if (complete) {
       double* X = (double*)base;  // 64 x 65
       if (row >= 64) {
 #pragma unroll
-        for (int j = 0; j < 64; ++j) X[(row - 64) * 65 + j] = acc[j];
+        for (int j = 0; j < 32; ++j) X[(row - 64) * 65 + c0 + j] = (double)accs[j] + (double)accc[j];
       }
-      asm volatile("bar.sync 1, 128;" ::: "memory");
+      asm volatile("bar.sync 1, 256;" ::: "memory");
       if (row < 64 && i0 + row < k1) {
         double* out = partial + (size_t)blockIdx.x * k1 * k2 + (size_t)(i0 + row) * k2;
 #pragma unroll
-        for (int j = 0; j < 64; ++j)
-          if (j0 + j < k2) out[j0 + j] = acc[j] + X[row * 65 + j];
+        for (int j = 0; j < 32; ++j)
+          if (j0 + c0 + j < k2) out[j0 + c0 + j] = ((double)accs[j] + (double)accc[j]) + X[row * 65 + c0 + j];
       }
     }
   }

@@ -332,24 +332,39 @@ __device__ inline double block_sum(double v, double* red) {
   return t;
 }
 
-// Three block sums at once, each in the order of block_sum (so bitwise the same results);
-// valid in thread 0. red must hold 3 * 32 doubles.
+// Three block sums at once (result in thread 0; blockDim.x <= 256, a multiple of 32; red holds
+// 3 * 32 doubles). Within a warp the values are reduced by a butterfly that halves the number
+// of values each lane carries at the first two levels, so the warp spends 6 FP64 additions on
+// all three sums instead of 15 (FP64 issue is scarce on this part); the order is fixed, so
+// the result is deterministic.
 __device__ inline void block_sum3(double& a, double& b, double& c, double* red) {
-  a = warp_sum(a);
-  b = warp_sum(b);
-  c = warp_sum(c);
-  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-  if (l == 0) {
-    red[w] = a;
-    red[32 + w] = b;
-    red[64 + w] = c;
-  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+  // level 16: lanes 0-15 carry values (0, 1), lanes 16-31 carry (2, 3 = 0)
+  const bool lo = l < 16;
+  const double ka = lo ? a : c, kb = lo ? b : 0.0;
+  const double sa = lo ? c : a, sb = lo ? 0.0 : b;
+  double x = ka + __shfl_xor_sync(0xffffffffu, sa, 16);
+  double y = kb + __shfl_xor_sync(0xffffffffu, sb, 16);
+  // level 8: lanes with bit 3 clear keep x, the others y
+  const bool lo8 = (l & 8) == 0;
+  double v = (lo8 ? x : y) + __shfl_xor_sync(0xffffffffu, lo8 ? y : x, 8);
+  v += __shfl_xor_sync(0xffffffffu, v, 4);
+  v += __shfl_xor_sync(0xffffffffu, v, 2);
+  v += __shfl_xor_sync(0xffffffffu, v, 1);
+  // lane 0: value 0, lane 8: value 1, lane 16: value 2 (lane 24: the zero pad)
+  if (l == 0) red[w] = v;
+  if (l == 8) red[32 + w] = v;
+  if (l == 16) red[64 + w] = v;
   __syncthreads();
-  if (threadIdx.x < 32) {
-    const int nw = blockDim.x >> 5;
-    a = warp_sum((l < nw) ? red[l] : 0.0);
-    b = warp_sum((l < nw) ? red[32 + l] : 0.0);
-    c = warp_sum((l < nw) ? red[64 + l] : 0.0);
+  if (w == 0) {
+    const int q = l >> 3, ww = l & 7;  // lane (q, ww): value q of warp ww
+    double t = (q < 3 && ww < nw) ? red[q * 32 + ww] : 0.0;
+    t += __shfl_xor_sync(0xffffffffu, t, 1);
+    t += __shfl_xor_sync(0xffffffffu, t, 2);
+    t += __shfl_xor_sync(0xffffffffu, t, 4);
+    a = __shfl_sync(0xffffffffu, t, 0);
+    b = __shfl_sync(0xffffffffu, t, 8);
+    c = __shfl_sync(0xffffffffu, t, 16);
   }
   __syncthreads();
 }

@@ -18,7 +18,7 @@ __global__ void __launch_bounds__(256) rom_assemble_partial_kernel(const double*
                                                                    const double* __restrict__ E, long long rows,
                                                                    int npair, long long rows_per_cta,
                                                                    double* partial);
-__global__ void rom_assemble_final_kernel(const double* partial, int G, int k, double* H);
+void launch_rom_assemble_final(cudaStream_t stream, const double* partial, int G, int k, double* H);
 __global__ void cholesky_kernel(double* H, int k, int* status, int* ok_flag, const int* gate);
 __global__ void chol_solve_kernel(const double* L, int k, const double* rhs, double* y, int mode, const int* ok_flag,
                                   const int* gate);
@@ -91,8 +91,7 @@ extern "C" topo_status topo_rom_solve_elem_noalloc(topo_ctx* c, const double* rh
   rom_assemble_partial_kernel<<<dim3((unsigned)G, (npair + 255) / 256), std::min(256, ((npair + 31) / 32) * 32), 0,
                                 c->stream>>>(Hel, E, rows, npair, per, partial);
   note_launch();
-  rom_assemble_final_kernel<<<(npair + 127) / 128, 128, 0, c->stream>>>(partial, (int)G, k, H_work);
-  note_launch();
+  launch_rom_assemble_final(c->stream, partial, (int)G, k, H_work);
   // k <= 64: the factor (32 KB) fits the default shared-memory window, no attribute change
   const size_t sm_chol = (size_t)k * k * sizeof(double);
   cholesky_kernel<<<1, 256, sm_chol, c->stream>>>(H_work, k, &c->d_sync->status, ok, nullptr);

@@ -170,7 +170,7 @@ __device__ __forceinline__ void pcg2_body(const Pcg2Args<DIM>& a, const unsigned
                                           GridBar* gb) {
   __shared__ double red[96];
   __shared__ double sh_gamma[P2_MAX_COLS], sh_alpha[P2_MAX_COLS], sh_beta[P2_MAX_COLS], sh_tol2[P2_MAX_COLS],
-      sh_ff[P2_MAX_COLS], sh_rr[P2_MAX_COLS];
+      sh_ff[P2_MAX_COLS], sh_rr[P2_MAX_COLS], sh_den[P2_MAX_COLS];
   __shared__ int sh_done[P2_MAX_COLS];
   __shared__ double sh_sum[4 * P2_MAX_COLS];
   __shared__ double sh_floor2[P2_MAX_COLS];
@@ -329,8 +329,9 @@ __device__ __forceinline__ void pcg2_body(const Pcg2Args<DIM>& a, const unsigned
   // Phase W: w = K z for owned nodes and partial delta = w.z; one grid barrier reduces delta
   // together with gamma and r.r of the preceding phase U (Chronopoulos-Gear: one reduction
   // per iteration). Then beta = gamma_new / gamma, the convergence test on r.r, and
-  // alpha = gamma / (delta - beta gamma / alpha_old) (restart: beta = 0, alpha = gamma / delta,
-  // gamma and r.r come from the true residual).
+  // alpha = gamma / den with den = delta - beta gamma / alpha_old = delta - beta^2 den_old
+  // (alpha_old = gamma_old / den_old; two FP64 divisions per step). Restart: beta = 0,
+  // den = delta; gamma and r.r come from the true residual.
   auto phase_w = [&](bool restart) -> bool {
     if (!restart && !wait_z()) return false;
     double acc[P2_MAX_COLS];
@@ -375,11 +376,11 @@ __device__ __forceinline__ void pcg2_body(const Pcg2Args<DIM>& a, const unsigned
         const double delta = R(0, c);
         if (restart) {
           sh_beta[c] = 0.0;
-          sh_alpha[c] = sh_gamma[c] / delta;
+          sh_den[c] = delta;
         } else {
-          const double den = delta - sh_beta[c] * sh_gamma[c] / sh_alpha[c];
-          sh_alpha[c] = sh_gamma[c] / den;
+          sh_den[c] = delta - sh_beta[c] * sh_beta[c] * sh_den[c];
         }
+        sh_alpha[c] = sh_gamma[c] / sh_den[c];
         if (!(sh_alpha[c] > 0.0) || !isfinite(sh_alpha[c])) {
           set_status(&gs->status, TOPO_ERR_NOT_SPD);
           sh_done[c] = 1;

@@ -79,21 +79,46 @@ __global__ void __launch_bounds__(256) atb_partial_kernel(const T* __restrict__ 
     }
 }
 
-// Sum the G partial k1 x k2 matrices in CTA order. sym: C = (C + C^T)/2 (k1 == k2).
-__global__ void atb_final_kernel(const double* partial, int G, int k1, int k2, double* C, int sym, const int* gate) {
+// C[e] = sum over g < G of partial[g * KK + e] (KK = k1 k2) in a fixed order: a CTA takes 32
+// consecutive entries (lane = entry); warp w sums the partials g in [G w / 8, G (w + 1) / 8) in
+// order, then the 8 warp sums are added in warp order. Spreading the G-long sums over many SMs
+// keeps this FP64 reduction short.
+__global__ void __launch_bounds__(256) atb_final_kernel(const double* __restrict__ partial, int G, int KK, double* C,
+                                                        const int* gate) {
+  __shared__ double red[8][33];
   if (gate && *gate == 0) return;
-  const int KK = k1 * k2;
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < KK; e += gridDim.x * blockDim.x) {
-    double s = 0.0;
-    for (int g = 0; g < G; ++g) s += partial[(size_t)g * KK + e];
-    if (sym) {
-      const int i = e / k2, j = e % k2;
-      double t = 0.0;
-      const int et = j * k2 + i;
-      for (int g = 0; g < G; ++g) t += partial[(size_t)g * KK + et];
-      s = 0.5 * (s + t);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  const int e = blockIdx.x * 32 + l;
+  const int g0 = (int)((long long)G * w / 8), g1 = (int)((long long)G * (w + 1) / 8);
+  double s = 0.0;
+  if (e < KK)
+    for (int g = g0; g < g1; ++g) s += __ldcg(partial + (size_t)g * KK + e);
+  red[w][l] = s;
+  __syncthreads();
+  if (w == 0 && e < KK) {
+    double t = red[0][l];
+#pragma unroll
+    for (int q = 1; q < 8; ++q) t += red[q][l];
+    C[e] = t;
+  }
+}
+
+// C = (C + C^T) / 2 for a k x k row-major matrix (one thread per pair i < j).
+__global__ void symmetrize_kernel(double* C, int k, const int* gate) {
+  if (gate && *gate == 0) return;
+  const long long npair = (long long)k * (k - 1) / 2;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < npair; t += (long long)gridDim.x * blockDim.x) {
+    // pair t -> (i, j), i < j, row-major over the strict upper triangle
+    int i = 0;
+    long long rem = t;
+    while (rem >= k - 1 - i) {
+      rem -= k - 1 - i;
+      ++i;
     }
-    C[e] = s;
+    const int j = i + 1 + (int)rem;
+    const double v = 0.5 * (C[i * k + j] + C[j * k + i]);
+    C[i * k + j] = v;
+    C[j * k + i] = v;
   }
 }
 
@@ -299,6 +324,21 @@ static RowSplit row_split(topo_ctx* c, long long N, int per_sm) {
   return {(int)G, rows};
 }
 
+// Fixed-order sum of the G partial k1 x k2 tiles into C; sym (k1 == k2): C = (C + C^T) / 2.
+static topo_status launch_atb_final(topo_ctx* c, const double* partial, int G, int k1, int k2, double* C, int sym,
+                                    const int* gate) {
+  const int KK = k1 * k2;
+  atb_final_kernel<<<(KK + 31) / 32, 256, 0, c->stream>>>(partial, G, KK, C, gate);
+  note_launch();
+  if (sym && k1 == k2 && k1 > 1) {
+    const long long npair = (long long)k1 * (k1 - 1) / 2;
+    symmetrize_kernel<<<(int)std::min<long long>((npair + 255) / 256, 64), 256, 0, c->stream>>>(C, k1, gate);
+    note_launch();
+  }
+  TOPO_CUDA_TRY(c, cudaGetLastError());
+  return TOPO_OK;
+}
+
 template <typename T>
 static topo_status launch_atb(topo_ctx* c, const T* A, long long lda, int k1, const T* B, long long ldb, int k2,
                               long long N, double* partial_buf, size_t partial_cap, double* C, int sym,
@@ -317,10 +357,7 @@ static topo_status launch_atb(topo_ctx* c, const T* A, long long lda, int k1, co
                                                                         gate);
   }
   note_launch();
-  atb_final_kernel<<<(k1 * k2 + 255) / 256, 256, 0, c->stream>>>(partial_buf, rs.G, k1, k2, C, sym, gate);
-  note_launch();
-  TOPO_CUDA_TRY(c, cudaGetLastError());
-  return TOPO_OK;
+  return launch_atb_final(c, partial_buf, rs.G, k1, k2, C, sym, gate);
 }
 
 static topo_status launch_atv(topo_ctx* c, const double* A, long long lda, int k, const double* v, long long N,
@@ -374,9 +411,8 @@ static topo_status project(topo_ctx* c, const double* rho, const double* Phi, in
       int G = 0;
       s = launch_atb_tc_partial(c, P32, ld32, k, W32, ld32, k, N, partial, pcap, &G);
       if (s) return s;
-      atb_final_kernel<<<(k * k + 255) / 256, 256, 0, c->stream>>>(partial, G, k, k, H, 1, nullptr);
-      note_launch();
-      TOPO_CUDA_TRY(c, cudaGetLastError());
+      s = launch_atb_final(c, partial, G, k, k, H, 1, nullptr);
+      if (s) return s;
     } else {
       s = launch_atb<float>(c, P32, ld32, k, W32, ld32, k, N, partial, pcap, H, 1);
       if (s) return s;

@@ -132,21 +132,40 @@ __global__ void __launch_bounds__(256) rom_assemble_partial_kernel(const double*
   partial[(size_t)blockIdx.x * npair + p] = (a0 + a1) + (a2 + a3);
 }
 
-// H (k x k row-major, symmetric) from the G partial packed sums, in CTA order.
-__global__ void rom_assemble_final_kernel(const double* partial, int G, int k, double* H) {
+// H (k x k row-major, symmetric) from the G partial packed sums in a fixed order: a CTA takes
+// 32 consecutive packed entries (lane = entry); warp w sums partials g in [G w / 8, G (w + 1) / 8)
+// in order and the 8 warp sums are added in warp order (the G-long FP64 sums spread over SMs).
+__global__ void __launch_bounds__(256) rom_assemble_final_kernel(const double* __restrict__ partial, int G, int k,
+                                                                 double* H) {
+  __shared__ double red[8][33];
   const int npair = k * (k + 1) / 2;
-  for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < npair; p += gridDim.x * blockDim.x) {
-    double s = 0.0;
-    for (int gg = 0; gg < G; ++gg) s += partial[(size_t)gg * npair + p];
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  const int p = blockIdx.x * 32 + l;
+  const int g0 = (int)((long long)G * w / 8), g1 = (int)((long long)G * (w + 1) / 8);
+  double s = 0.0;
+  if (p < npair)
+    for (int g = g0; g < g1; ++g) s += __ldcg(partial + (size_t)g * npair + p);
+  red[w][l] = s;
+  __syncthreads();
+  if (w == 0 && p < npair) {
+    double t = red[0][l];
+#pragma unroll
+    for (int q = 1; q < 8; ++q) t += red[q][l];
     int i = 0, rem = p;
     while (rem >= k - i) {
       rem -= k - i;
       ++i;
     }
     const int j = i + rem;
-    H[i * k + j] = s;
-    H[j * k + i] = s;
+    H[i * k + j] = t;
+    H[j * k + i] = t;
   }
+}
+
+void launch_rom_assemble_final(cudaStream_t stream, const double* partial, int G, int k, double* H) {
+  const int npair = k * (k + 1) / 2;
+  rom_assemble_final_kernel<<<(npair + 31) / 32, 256, 0, stream>>>(partial, G, k, H);
+  note_launch();
 }
 
 // Kernels of the k x k reduced solve live in rom.cu.
@@ -216,8 +235,7 @@ extern "C" topo_status topo_rom_solve_elem(topo_ctx* c, const double* rho, const
   rom_assemble_partial_kernel<<<dim3((unsigned)G, by), std::min(256, ((npair + 31) / 32) * 32), 0, c->stream>>>(
       Hel, E, rows, npair, per, partial);
   note_launch();
-  rom_assemble_final_kernel<<<(npair + 127) / 128, 128, 0, c->stream>>>(partial, (int)G, k, H_work);
-  note_launch();
+  launch_rom_assemble_final(c->stream, partial, (int)G, k, H_work);
   TOPO_CUDA_TRY(c, cudaGetLastError());
   return reduced_solve(c, k, b, H_work, yhat, Jk);
 }
