@@ -114,34 +114,41 @@ __device__ __forceinline__ void stencil_apply_abs(const Grid& g, const double* _
   }
 }
 
+// y = C v for node (i, j, k); vown = v at the node itself.
 template <int DIM>
 __device__ __forceinline__ void stencil_apply(const Grid& g, const double* __restrict__ C, const double* v, int i,
-                                              int j, int k, long long n, double* y) {
+                                              int j, int k, long long n, double* y, double* vown) {
   constexpr int NB = StencilGeom<DIM>::NB;
   if constexpr (DIM == 2) {
     // Branch-free: a neighbour outside the grid has all-zero coefficients (assembly), so its
-    // value is read at the node itself and contributes fma(0, v, y) = y exactly. All 18 values
-    // and 36 coefficients are loaded before the first FMA (one L2 round trip per node).
-    double vv[NB][2], cc[NB][4];
+    // value is read at the node itself and contributes fma(0, v, y) = y exactly. A node's two
+    // components are one 16-byte load (half the L2 sectors of two 8-byte loads at stride 16 B).
+    // All 18 values and 36 coefficients are loaded before the first FMA.
+    double vv[NB][2];
 #pragma unroll
     for (int nb = 0; nb < NB; ++nb) {
       const int ii = i + nb % 3 - 1, jj = j + nb / 3 - 1;
       const bool nin = ii >= 0 && ii < g.nnx && jj >= 0 && jj < g.nny;
       const long long m = nin ? ii + (long long)g.nnx * jj : n;
-      vv[nb][0] = __ldcg(v + 2 * m);
-      vv[nb][1] = __ldcg(v + 2 * m + 1);
+      const double2 t = __ldcg(reinterpret_cast<const double2*>(v) + m);  // (x, y) of node m: 16 B
+      vv[nb][0] = t.x;
+      vv[nb][1] = t.y;
     }
-#pragma unroll
-    for (int nb = 0; nb < NB; ++nb)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) cc[nb][q] = __ldg(C + (long long)(nb * 4 + q) * g.nnodes + n);
+    // each block's 4 coefficients are used as they arrive
+    const double* gp = C + n;
     y[0] = y[1] = 0.0;
 #pragma unroll
-    for (int nb = 0; nb < NB; ++nb)
+    for (int nb = 0; nb < NB; ++nb) {
+      double cc[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) cc[q] = __ldg(gp + (long long)(nb * 4 + q) * g.nnodes);
 #pragma unroll
       for (int r = 0; r < 2; ++r)
 #pragma unroll
-        for (int d = 0; d < 2; ++d) y[r] = fma(cc[nb][r * 2 + d], vv[nb][d], y[r]);
+        for (int d = 0; d < 2; ++d) y[r] = fma(cc[r * 2 + d], vv[nb][d], y[r]);
+    }
+    vown[0] = vv[4][0];  // the centre block (nb = 4) is the node itself
+    vown[1] = vv[4][1];
     return;
   }
 #pragma unroll
@@ -161,6 +168,8 @@ __device__ __forceinline__ void stencil_apply(const Grid& g, const double* __res
 #pragma unroll
       for (int d = 0; d < DIM; ++d) y[r] = fma(__ldg(C + (long long)((nb * DIM + r) * DIM + d) * g.nnodes + n), vv[d], y[r]);
   }
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) vown[d] = __ldcg(v + DIM * n + d);
 }
 
 // The solver, run by a group of G co-resident CTAs (this CTA is number `rank` of the group)
@@ -197,6 +206,7 @@ __device__ __forceinline__ void pcg2_body(const Pcg2Args<DIM>& a, const unsigned
   // this CTA's units: a contiguous, balanced range
   const long long u0 = a.nunits * rank / G, u1 = a.nunits * (rank + 1) / G;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
+  // iterate over the owned nodes of this CTA: fn(i, j, k, n)
   // iterate over the owned nodes of this CTA: fn(i, j, k, n)
   auto for_owned = [&](auto fn) {
     for (long long u = u0 + warp; u < u1; u += nwarps) {
@@ -277,6 +287,7 @@ __device__ __forceinline__ void pcg2_body(const Pcg2Args<DIM>& a, const unsigned
     for (int c = 0; c < m; ++c) {
       double* x = a.U + c * a.ld;
       const double* f = a.F + c * a.ld;
+      double t0 = 0.0, t1 = 0.0, t2 = 0.0, t3 = 0.0;  // register accumulators
       for_owned([&](int i, int j, int k, long long n) {
         double y[DIM], yabs[DIM];
         stencil_apply_abs<DIM>(g, a.C, x, i, j, k, n, y, yabs);
@@ -287,18 +298,22 @@ __device__ __forceinline__ void pcg2_body(const Pcg2Args<DIM>& a, const unsigned
           if (!is_fixed(g, dof)) {
             const double fv = f[dof];
             rv = fv - y[d];
-            acc[1][c] = fma(rv, rv, acc[1][c]);
-            acc[2][c] = fma(fv, fv, acc[2][c]);
-            acc[3][c] = fma(yabs[d], yabs[d], acc[3][c]);
+            t1 = fma(rv, rv, t1);
+            t2 = fma(fv, fv, t2);
+            t3 = fma(yabs[d], yabs[d], t3);
           } else if (first) {
             x[dof] = 0.0;  // Dirichlet entries of the solution are zero (their columns are zero)
           }
           const double zv = __ldg(a.dinv + dof) * rv;
           a.r[c * N + dof] = rv;
           a.z[c * N + dof] = zv;
-          acc[0][c] = fma(rv, zv, acc[0][c]);
+          t0 = fma(rv, zv, t0);
         }
       });
+      acc[0][c] = t0;
+      acc[1][c] = t1;
+      acc[2][c] = t2;
+      acc[3][c] = t3;
     }
     for (int c = 0; c < m; ++c)
       for (int q = 0; q < 4; ++q) {
@@ -334,21 +349,23 @@ __device__ __forceinline__ void pcg2_body(const Pcg2Args<DIM>& a, const unsigned
   // den = delta; gamma and r.r come from the true residual.
   auto phase_w = [&](bool restart) -> bool {
     if (!restart && !wait_z()) return false;
-    double acc[P2_MAX_COLS];
+    double acc[P2_MAX_COLS];  // per column; the node loop accumulates in a register
     for (int c = 0; c < m; ++c) acc[c] = 0.0;
     for (int c = 0; c < m; ++c) {
       if (sh_done[c]) continue;
       const double* zc = a.z + c * N;
+      double ad = 0.0;
       for_owned([&](int i, int j, int k, long long n) {
-        double y[DIM];
-        stencil_apply<DIM>(g, a.C, zc, i, j, k, n, y);
+        double y[DIM], zn[DIM];
+        stencil_apply<DIM>(g, a.C, zc, i, j, k, n, y, zn);
 #pragma unroll
         for (int d = 0; d < DIM; ++d) {
           const long long dof = DIM * n + d;
           a.w[c * N + dof] = y[d];
-          acc[c] = fma(y[d], __ldcg(zc + dof), acc[c]);
+          ad = fma(y[d], zn[d], ad);
         }
       });
+      acc[c] = ad;
     }
     for (int c = 0; c < m; ++c) {
       double t0 = acc[c], t1 = restart ? 0.0 : accg[c], t2 = restart ? 0.0 : accr[c];
@@ -399,24 +416,59 @@ __device__ __forceinline__ void pcg2_body(const Pcg2Args<DIM>& a, const unsigned
       if (sh_done[c]) continue;
       const double al = sh_alpha[c], be = restart ? 0.0 : sh_beta[c];
       double* x = a.U + c * a.ld;
+      double ag = 0.0, ar = 0.0;  // register accumulators of r.z and r.r
       for_owned([&](int i, int j, int k, long long n) {
+        if constexpr (DIM == 2) {
+          // the node's two DOFs as 16-byte accesses (scratch vectors are 16-byte aligned; x, the
+          // caller's array, may have an odd leading dimension and stays scalar)
+          const long long o2 = (c * N) / 2 + n;
+          const double2 zz = reinterpret_cast<const double2*>(a.z)[o2];
+          const double2 ww = reinterpret_cast<const double2*>(a.w)[o2];
+          const double2 rr = reinterpret_cast<const double2*>(a.r)[o2];
+          const double2 di = __ldg(reinterpret_cast<const double2*>(a.dinv) + n);
+          double2 pv, sv;
+          if (restart) {  // p and s hold stale (possibly non-finite) data: take z and w exactly
+            pv = zz;
+            sv = ww;
+          } else {
+            const double2 pp = reinterpret_cast<const double2*>(a.p)[o2];
+            const double2 ss = reinterpret_cast<const double2*>(a.s)[o2];
+            pv = make_double2(fma(be, pp.x, zz.x), fma(be, pp.y, zz.y));
+            sv = make_double2(fma(be, ss.x, ww.x), fma(be, ss.y, ww.y));
+          }
+          reinterpret_cast<double2*>(a.p)[o2] = pv;
+          reinterpret_cast<double2*>(a.s)[o2] = sv;
+          x[2 * n] = fma(al, pv.x, x[2 * n]);
+          x[2 * n + 1] = fma(al, pv.y, x[2 * n + 1]);
+          const double2 rv = make_double2(fma(-al, sv.x, rr.x), fma(-al, sv.y, rr.y));
+          const double2 zv = make_double2(di.x * rv.x, di.y * rv.y);
+          reinterpret_cast<double2*>(a.r)[o2] = rv;
+          reinterpret_cast<double2*>(a.z)[o2] = zv;
+          ag = fma(rv.x, zv.x, ag);
+          ag = fma(rv.y, zv.y, ag);
+          ar = fma(rv.x, rv.x, ar);
+          ar = fma(rv.y, rv.y, ar);
+        } else {
 #pragma unroll
-        for (int d = 0; d < DIM; ++d) {
-          const long long dof = DIM * n + d, o = c * N + dof;
-          // on a restart p and s hold stale (possibly non-finite) data: take z and w exactly
-          const double pv = restart ? a.z[o] : fma(be, a.p[o], a.z[o]);
-          const double sv = restart ? a.w[o] : fma(be, a.s[o], a.w[o]);
-          a.p[o] = pv;
-          a.s[o] = sv;
-          x[dof] = fma(al, pv, x[dof]);
-          const double rv = fma(-al, sv, a.r[o]);
-          const double zv = __ldg(a.dinv + dof) * rv;
-          a.r[o] = rv;
-          a.z[o] = zv;
-          accg[c] = fma(rv, zv, accg[c]);
-          accr[c] = fma(rv, rv, accr[c]);
+          for (int d = 0; d < DIM; ++d) {
+            const long long dof = DIM * n + d, o = c * N + dof;
+            // on a restart p and s hold stale (possibly non-finite) data: take z and w exactly
+            const double pv = restart ? a.z[o] : fma(be, a.p[o], a.z[o]);
+            const double sv = restart ? a.w[o] : fma(be, a.s[o], a.w[o]);
+            a.p[o] = pv;
+            a.s[o] = sv;
+            x[dof] = fma(al, pv, x[dof]);
+            const double rv = fma(-al, sv, a.r[o]);
+            const double zv = __ldg(a.dinv + dof) * rv;
+            a.r[o] = rv;
+            a.z[o] = zv;
+            ag = fma(rv, zv, ag);
+            ar = fma(rv, rv, ar);
+          }
         }
       });
+      accg[c] = ag;
+      accr[c] = ar;
     }
     publish_z();
   };
