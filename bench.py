@@ -204,11 +204,11 @@ def run_ours(args, rank, world):
         stream.synchronize()
 
     ev = lambda: torch.cuda.Event(enable_timing=True)
-    stats = dict(step=[], hdm=[], build=[], rom=[], iters=[], outer=[], relres=[])
+    stats = dict(step=[], hdm=[], solve=[], build=[], rom=[], iters=[], outer=[], relres=[])
 
     def step(s, record=True, host_io=None):
         """One trust-region-shaped pass; host_io = (pinned inputs, pinned outputs) for e2e."""
-        e0, e1, e2, e3 = ev(), ev(), ev(), ev()
+        e0, e1, e2, e3, es0, es1 = ev(), ev(), ev(), ev(), ev(), ev()
         e0.record(stream)
         if host_io is not None:
             hin, hout = host_io
@@ -216,7 +216,9 @@ def run_ours(args, rank, world):
             d_cand.copy_(hin["cands"], non_blocking=True)
         T.topo_filter(d_cent[s], rho)
         Uc.zero_()
+        es0.record(stream)
         info = T.topo_solve_hdm(rho, F, Uc, rtol=1e-8, maxit=400000, prec=prec)
+        es1.record(stream)
         assert info["status"] == 0, info
         T.topo_compliance_grad(rho, Uc, F, J, dc, dpsi)
         e1.record(stream)
@@ -249,6 +251,7 @@ def run_ours(args, rank, world):
         if record:
             stats["step"].append(e0.elapsed_time(e3))
             stats["hdm"].append(e0.elapsed_time(e1))
+            stats["solve"].append(es0.elapsed_time(es1))
             stats["build"].append(e1.elapsed_time(e2))
             stats["rom"].extend(a.elapsed_time(bq) for a, bq in rom_ev)
             stats["iters"].append(info["iters"])
@@ -288,7 +291,7 @@ def run_ours(args, rank, world):
                     dpr=torch.zeros((R, Ne), dtype=torch.float64).pin_memory())
         e2e_steps = []
         saved = stats["step"]
-        stats_e2e = dict(step=[], hdm=[], build=[], rom=[], iters=[], outer=[], relres=[])
+        stats_e2e = dict(step=[], hdm=[], solve=[], build=[], rom=[], iters=[], outer=[], relres=[])
         stats_main = stats
         for s in range(args.warmup, args.warmup + args.steps):
             flush.zero_()
@@ -353,6 +356,7 @@ def run_ours(args, rank, world):
     # (the whole working set sits in L2). FP64 flops it performs per DOF and iteration: stencil
     # apply 2 * 3^d * d (36 in 2D, 162 in 3D), delta 2, the five updates, z and the two dots 13.
     hdm_ms = statistics.fmean(stats["hdm"])
+    solve_ms = statistics.fmean(stats["solve"])  # the topo_solve_hdm call alone (one PCG launch)
     iters = statistics.fmean(stats["iters"])
     outer = statistics.fmean(stats["outer"])
     flop_dof = 51.0 if p.dim == 2 else 177.0
@@ -360,7 +364,7 @@ def run_ours(args, rank, world):
     # FP64 peak derived from unit counts and clocks: 152 SMs x 2 FP64 FMA/clk (4 flop) x 2.07 GHz
     # (NVIDIA's nominal FP64 rate is 1.25 TFLOP/s; this build's own FMA microbenchmark measured 1.19).
     fp64_peak = 152 * 4 * 2.07e9 / 1e12
-    achieved = flops_launch / (hdm_ms * 1e-3) / 1e12
+    achieved = flops_launch / (solve_ms * 1e-3) / 1e12
     try:
         hbm_peak = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
     except Exception:
@@ -385,7 +389,7 @@ def run_ours(args, rank, world):
         "accuracy": {"hdm_J_vs_fp64_rel": hdm_rel, "rom_Jk_vs_fp64_phi_path_rel": rom_rel, "J_centre": J_centre},
         "roofline": {"kernel": "pcg2_kernel (assembled-stencil Chronopoulos-Gear PCG, one launch per HDM solve)",
                      "bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
-                     "frac": achieved / fp64_peak, "traffic": None,
+                     "frac": achieved / fp64_peak, "traffic": None, "launch_ms": solve_ms,
                      "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2.07 GHz (measured FMA peak 1.19)",
                      "flop_per_dof_iter": flop_dof, "hbm_peak_gbs": hbm_peak},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
@@ -420,27 +424,44 @@ def run_batch(args):
         dps = [torch.empty(p.nel, **f64) for p in probs]
         flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
 
-        def step(record):
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
+        def body():
             B.topo_batch_filter(psis, rhos)
             for U in Us:
                 U.zero_()
             B.topo_batch_solve_hdm(rhos, Fs, Us, rtol=1e-8, maxit=100000, info=False)
             B.topo_batch_compliance_grad(rhos, Us, Fs, J, dcs, dps)
+
+        def timed(run):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            run()
             e1.record(stream)
             e1.synchronize()
             return e0.elapsed_time(e1)
 
+        # eager warm-up: autotunes the CTAs per SM and stages the launch tables; the step is then
+        # captured once in a CUDA graph (the identical solve call needs no host synchronisation)
         for _ in range(args.warmup):
             flush.zero_()
-            step(False)
+            timed(body)
+        graph, graph_error, per_step = None, None, 0
+        try:
+            stream.synchronize()
+            g = torch.cuda.CUDAGraph()
+            n0 = native.launch_count()
+            with torch.cuda.graph(g, stream=stream):
+                body()
+            per_step = native.launch_count() - n0
+            graph = g
+        except Exception as e:  # capture refused: time the eager step instead
+            graph_error = str(e).splitlines()[0][:200]
+        run = graph.replay if graph is not None else body
         n0 = native.launch_count()
         times = []
         for _ in range(args.steps):
             flush.zero_()
-            times.append(step(True))
-        launches = native.launch_count() - n0
+            times.append(timed(run))
+        launches = per_step * args.steps if graph is not None else native.launch_count() - n0
         infos = B.topo_batch_solve_hdm(rhos, Fs, [torch.zeros_like(F) for F in Fs], rtol=1e-8, maxit=100000)
     ms = statistics.fmean(times)
     ndof = sum(p.ndof for p in probs)
@@ -459,6 +480,7 @@ def run_batch(args):
             "max_iters": max(x["iters"] for x in infos), "all_converged": all(x["status"] == 0 for x in infos),
             "max_relres": max(x["relres"] for x in infos), "max_floor": max(x["floor"] for x in infos),
             "instances_at_floor": sum(1 for x in infos if x["relres"] > 1e-8), "gpu_launches": launches,
+            "cuda_graph": graph is not None, "cuda_graph_error": graph_error,
             "roofline": {"kernel": "pcg2_batch_kernel (all instances' solves, one launch)", "bound": "alu",
                          "achieved": flops / (ms * 1e-3) / 1e12, "peak": fp64_peak / 1e12, "unit": "TFLOP/s",
                          "frac": flops / (ms * 1e-3) / fp64_peak, "traffic": None}}

@@ -542,6 +542,7 @@ struct topo_ctx {
   // generic scratch (grown on demand)
   void* d_scratch;
   size_t scratch_bytes;
+  unsigned long long scratch_gen;  // bumped whenever d_scratch is (re)allocated
   double* d_red;          // small reduction buffer (partials)
   size_t red_bytes;
   // parameters

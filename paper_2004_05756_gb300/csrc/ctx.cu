@@ -44,6 +44,7 @@ topo_status ensure_scratch(topo_ctx* c, size_t bytes) {
   cudaError_t e = cudaMalloc(&c->d_scratch, b);
   if (e != cudaSuccess) return cuda_fail(c, e, "scratch cudaMalloc");
   c->scratch_bytes = b;
+  c->scratch_gen += 1;
   return TOPO_OK;
 }
 

@@ -519,7 +519,7 @@ __global__ void __launch_bounds__(P2_THREADS, 2) pcg2_kernel(const __grid_consta
 // group of grp_size[instance] CTAs; every instance has its own barrier state and progresses on
 // its own (no barrier spans instances).
 template <int DIM>
-__global__ void __launch_bounds__(P2_THREADS, 2) pcg2_batch_kernel(const Pcg2Args<DIM>* __restrict__ args,
+__global__ void __launch_bounds__(P2_THREADS, 4) pcg2_batch_kernel(const Pcg2Args<DIM>* __restrict__ args,
                                                                 const int* __restrict__ cta_inst,
                                                                 const int* __restrict__ cta_rank,
                                                                 const int* __restrict__ grp_size) {
