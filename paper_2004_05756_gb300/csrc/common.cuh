@@ -535,7 +535,7 @@ struct topo_ctx {
   int nstencil;
   int* d_stencil_off;     // [nstencil * 3]
   double* d_stencil_w;    // [nstencil]
-  double* d_Hs;           // [nel]
+  double* d_Hsinv;        // [nel]: 1 / Hs_e, the reciprocal filter normaliser
   // device status word + grid barrier state
   topo::GridSync* d_sync;
   topo::GridBar* d_bar;    // state of the second barrier form

@@ -147,10 +147,10 @@ struct FilterArgs {
   const int* off;   // [ns * 3]
   const double* w;  // [ns]
   int ns;
-  const double* Hs;
+  const double* Hsinv;  // 1 / Hs_e
   const double* in;
   double* out;
-  int mode;  // 0 = Hs, 1 = forward, 2 = adjoint
+  int mode;  // 0 = 1 / Hs, 1 = forward, 2 = adjoint
 };
 
 __global__ void filter_kernel(const __grid_constant__ FilterArgs a) {
@@ -177,10 +177,11 @@ __global__ void filter_kernel(const __grid_constant__ FilterArgs a) {
       else if (a.mode == 1)
         v = a.in[en];
       else
-        v = a.in[en] / a.Hs[en];
+        v = a.in[en] * a.Hsinv[en];  // FP64 division is slow here: multiply by 1 / Hs
       acc = fma(sw[s], v, acc);
     }
-    if (a.mode == 1) acc /= a.Hs[e];
+    if (a.mode == 0) acc = 1.0 / acc;  // once per context
+    if (a.mode == 1) acc *= a.Hsinv[e];
     a.out[e] = acc;
   }
 }
@@ -290,7 +291,7 @@ static topo_status filter_launch(topo_ctx* c, const double* in, double* out, int
   a.off = c->d_stencil_off;
   a.w = c->d_stencil_w;
   a.ns = c->nstencil;
-  a.Hs = c->d_Hs;
+  a.Hsinv = c->d_Hsinv;
   a.in = in;
   a.out = out;
   a.mode = mode;
@@ -435,7 +436,7 @@ extern "C" topo_status topo_create(const topo_problem* prob, void* cuda_stream, 
   c->nstencil = (int)w.size();
   e = cudaMalloc(&c->d_stencil_off, off.size() * sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&c->d_stencil_w, w.size() * sizeof(double));
-  if (e == cudaSuccess) e = cudaMalloc(&c->d_Hs, g.nel * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&c->d_Hsinv, g.nel * sizeof(double));
   if (e == cudaSuccess) e = cudaMalloc(&c->d_sync, sizeof(GridSync));
   if (e == cudaSuccess) e = cudaMalloc(&c->d_bar, sizeof(GridBar));
   if (e != cudaSuccess) {
@@ -446,7 +447,7 @@ extern "C" topo_status topo_create(const topo_problem* prob, void* cuda_stream, 
   cudaMemcpy(c->d_stencil_w, w.data(), w.size() * sizeof(double), cudaMemcpyHostToDevice);
   cudaMemset(c->d_sync, 0, sizeof(GridSync));
   cudaMemset(c->d_bar, 0, sizeof(GridBar));
-  topo_status s = filter_launch(c, nullptr, c->d_Hs, 0);
+  topo_status s = filter_launch(c, nullptr, c->d_Hsinv, 0);
   if (s == TOPO_OK) {
     e = cudaStreamSynchronize(c->stream);
     if (e != cudaSuccess) s = TOPO_ERR_CUDA;
@@ -466,7 +467,7 @@ extern "C" topo_status topo_destroy(topo_ctx* c) {
   cudaFree(c->d_fixed_list);
   cudaFree(c->d_stencil_off);
   cudaFree(c->d_stencil_w);
-  cudaFree(c->d_Hs);
+  cudaFree(c->d_Hsinv);
   cudaFree(c->d_sync);
   cudaFree(c->d_bar);
   cudaFree(c->d_scratch);

@@ -19,10 +19,9 @@ __global__ void __launch_bounds__(256) rom_assemble_partial_kernel(const double*
                                                                    int npair, long long rows_per_cta,
                                                                    double* partial);
 void launch_rom_assemble_final(cudaStream_t stream, const double* partial, int G, int k, double* H);
-__global__ void cholesky_kernel(double* H, int k, int* status, int* ok_flag, const int* gate);
-__global__ void chol_solve_kernel(const double* L, int k, const double* rhs, double* y, int mode, const int* ok_flag,
-                                  const int* gate);
-__global__ void dot_small_kernel(const double* b, const double* y, int k, double* J);
+// k x k reduced solve (rom.cu): Cholesky of H_work into L, yhat, Jk; *ok = factorisation succeeded.
+topo_status launch_reduced_solve(topo_ctx* c, int k, const double* b, double* H_work, double* yhat, double* Jk,
+                                 int* ok);
 
 // 8 MiB shared by all calls in the process: a 256-byte flag block, E(rho) for N_e + 1 rows,
 // and the per-CTA partial sums of the reduced matrix.
@@ -93,13 +92,5 @@ extern "C" topo_status topo_rom_solve_elem_noalloc(topo_ctx* c, const double* rh
   note_launch();
   launch_rom_assemble_final(c->stream, partial, (int)G, k, H_work);
   // k <= 64: the factor (32 KB) fits the default shared-memory window, no attribute change
-  const size_t sm_chol = (size_t)k * k * sizeof(double);
-  cholesky_kernel<<<1, 256, sm_chol, c->stream>>>(H_work, k, &c->d_sync->status, ok, nullptr);
-  note_launch();
-  chol_solve_kernel<<<1, 128, sm_chol + k * sizeof(double), c->stream>>>(H_work, k, b, yhat, 0, ok, nullptr);
-  note_launch();
-  dot_small_kernel<<<1, 128, 0, c->stream>>>(b, yhat, k, Jk);
-  note_launch();
-  TOPO_CUDA_TRY(c, cudaGetLastError());
-  return TOPO_OK;
+  return launch_reduced_solve(c, k, b, H_work, yhat, Jk, ok);
 }

@@ -239,6 +239,90 @@ __global__ void cholesky_kernel(double* H, int k, int* status, int* ok_flag, con
   }
 }
 
+// The whole k x k reduced solve in one warp for k <= KMAX <= 32: FP64 Cholesky H = L L^T with
+// lane i holding row i in registers, then y = H^{-1} b by forward and backward substitution
+// and J = b^T y. L is written back into H (lower triangle, zeros above) as cholesky_kernel
+// does; the substitutions multiply by the reciprocal pivots computed during the factorisation,
+// so the solve takes k square roots and k divisions (each a long FP64 dependency chain here).
+// A pivot <= 0 (or NaN) sets TOPO_ERR_NOT_SPD and writes NaN to y and J.
+template <int KMAX>
+__global__ void __launch_bounds__(32) chol_small_kernel(double* H, int k, const double* b, double* y, double* J,
+                                                        int* status, int* ok_flag) {
+  __shared__ double Ls[KMAX][KMAX + 1];
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x;
+  double a[KMAX];
+#pragma unroll
+  for (int c = 0; c < KMAX; ++c) a[c] = (lane < k && c < k) ? H[lane * k + c] : 0.0;
+  double myinv = 0.0;  // 1 / L[lane][lane]
+  bool bad = false;
+#pragma unroll
+  for (int j = 0; j < KMAX; ++j) {
+    if (j < k && !bad) {
+      const double d = __shfl_sync(FULL, a[j], j);
+      if (!(d > 0.0)) {
+        bad = true;  // the same value in every lane: uniform
+      } else {
+        const double ljj = sqrt(d), inv = 1.0 / ljj;
+        if (lane == j) {
+          a[j] = ljj;
+          myinv = inv;
+        } else if (lane > j) {
+          a[j] *= inv;
+        }
+#pragma unroll
+        for (int c = j + 1; c < KMAX; ++c) {
+          const double lcj = __shfl_sync(FULL, a[j], c);  // L[c][j], held by lane c
+          if (c < k && lane >= c) a[c] = fma(-a[j], lcj, a[c]);
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < KMAX; ++c)
+    if (lane < k && c < k) {
+      const double v = c <= lane ? a[c] : 0.0;
+      H[lane * k + c] = v;
+      Ls[lane][c] = v;
+    }
+  __syncwarp();
+  if (bad) {
+    if (lane < k) y[lane] = __longlong_as_double(0x7ff8000000000000LL);
+    if (lane == 0) {
+      *J = __longlong_as_double(0x7ff8000000000000LL);
+      *ok_flag = 0;
+      if (status) atomicCAS(status, 0, (int)TOPO_ERR_NOT_SPD);
+    }
+    return;
+  }
+  // L z = b (column-oriented: lane c finishes z_c, the lanes below subtract its share)
+  const double bl = lane < k ? b[lane] : 0.0;
+  double r = bl, z = 0.0;
+#pragma unroll
+  for (int c = 0; c < KMAX; ++c)
+    if (c < k) {
+      const double zc = __shfl_sync(FULL, r * myinv, c);
+      if (lane == c) z = zc;
+      if (lane > c) r = fma(-a[c], zc, r);
+    }
+  // L^T y = z (from the last row up; L[c][lane] from shared memory)
+  double r2 = z, yv = 0.0;
+#pragma unroll
+  for (int c = KMAX - 1; c >= 0; --c)
+    if (c < k) {
+      const double yc = __shfl_sync(FULL, r2 * myinv, c);
+      if (lane == c) yv = yc;
+      if (lane < c) r2 = fma(-Ls[c][lane], yc, r2);
+    }
+  if (lane < k) y[lane] = yv;
+  double t = lane < k ? bl * yv : 0.0;
+  t = warp_sum(t);
+  if (lane == 0) {
+    *J = t;
+    *ok_flag = 1;
+  }
+}
+
 // Solve L L^T x = rhs (L lower, row-major). mode 0: y = x; mode 1: y += x. Skipped (y left
 // unchanged) when *skip is non-zero; NaN output when the factorisation failed.
 __global__ void chol_solve_kernel(const double* L, int k, const double* rhs, double* y, int mode, const int* ok_flag,
@@ -435,10 +519,20 @@ static size_t project_scratch(topo_ctx* c, int k, long long ld, topo_prec prec) 
 
 // FP64 Cholesky of H_work (overwritten with L), yhat = H^{-1} b, Jk = b^T yhat. A non-positive
 // pivot sets TOPO_ERR_NOT_SPD in the device status and writes NaN.
-topo_status reduced_solve(topo_ctx* c, int k, const double* b, double* H_work, double* yhat, double* Jk) {
-  topo_status s = ensure_red(c, 256);
-  if (s) return s;
-  int* ok = (int*)c->d_red;
+topo_status launch_reduced_solve(topo_ctx* c, int k, const double* b, double* H_work, double* yhat, double* Jk,
+                                 int* ok) {
+  if (k <= 16) {
+    chol_small_kernel<16><<<1, 32, 0, c->stream>>>(H_work, k, b, yhat, Jk, &c->d_sync->status, ok);
+    note_launch();
+    TOPO_CUDA_TRY(c, cudaGetLastError());
+    return TOPO_OK;
+  }
+  if (k <= 32) {
+    chol_small_kernel<32><<<1, 32, 0, c->stream>>>(H_work, k, b, yhat, Jk, &c->d_sync->status, ok);
+    note_launch();
+    TOPO_CUDA_TRY(c, cudaGetLastError());
+    return TOPO_OK;
+  }
   const size_t sm_chol = (size_t)k * k * sizeof(double);
   const size_t sm_solve = sm_chol + k * sizeof(double);
   if (sm_solve > 48 * 1024) {
@@ -453,6 +547,12 @@ topo_status reduced_solve(topo_ctx* c, int k, const double* b, double* H_work, d
   note_launch();
   TOPO_CUDA_TRY(c, cudaGetLastError());
   return TOPO_OK;
+}
+
+topo_status reduced_solve(topo_ctx* c, int k, const double* b, double* H_work, double* yhat, double* Jk) {
+  topo_status s = ensure_red(c, 256);
+  if (s) return s;
+  return launch_reduced_solve(c, k, b, H_work, yhat, Jk, (int*)c->d_red);
 }
 
 }  // namespace topo

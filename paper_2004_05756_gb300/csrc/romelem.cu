@@ -119,17 +119,20 @@ __global__ void __launch_bounds__(256) rom_assemble_partial_kernel(const double*
   const long long r0 = blockIdx.x * rows_per_cta;
   const long long r1 = min(rows, r0 + rows_per_cta);
   if (p >= npair) return;
-  // four interleaved accumulators (fixed order) keep four loads in flight
-  double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+  // eight interleaved accumulators (fixed order) keep eight streaming loads in flight
+  double acc[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) acc[q] = 0.0;
   long long r = r0;
-  for (; r + 3 < r1; r += 4) {
-    a0 = fma(__ldg(E + r), Hel[r * npair + p], a0);
-    a1 = fma(__ldg(E + r + 1), Hel[(r + 1) * npair + p], a1);
-    a2 = fma(__ldg(E + r + 2), Hel[(r + 2) * npair + p], a2);
-    a3 = fma(__ldg(E + r + 3), Hel[(r + 3) * npair + p], a3);
+  for (; r + 7 < r1; r += 8) {
+    double h[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) h[q] = __ldcs(Hel + (r + q) * npair + p);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc[q] = fma(__ldg(E + r + q), h[q], acc[q]);
   }
-  for (; r < r1; ++r) a0 = fma(__ldg(E + r), Hel[r * npair + p], a0);
-  partial[(size_t)blockIdx.x * npair + p] = (a0 + a1) + (a2 + a3);
+  for (; r < r1; ++r) acc[0] = fma(__ldg(E + r), __ldcs(Hel + r * npair + p), acc[0]);
+  partial[(size_t)blockIdx.x * npair + p] = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
 }
 
 // H (k x k row-major, symmetric) from the G partial packed sums in a fixed order: a CTA takes
@@ -221,7 +224,7 @@ extern "C" topo_status topo_rom_solve_elem(topo_ctx* c, const double* rho, const
     return fail(c, TOPO_ERR_INVALID, "topo_rom_solve_elem: null or misaligned pointer");
   const int npair = k * (k + 1) / 2;
   const long long rows = c->g.nel + 1;
-  long long G = 2LL * c->num_sms;
+  long long G = 4LL * c->num_sms;  // enough streaming loads in flight for HBM
   long long per = (rows + G - 1) / G;
   G = (rows + per - 1) / per;
   const size_t eoff = ((size_t)rows * sizeof(double) + 255) & ~(size_t)255;

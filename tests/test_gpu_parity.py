@@ -330,7 +330,8 @@ def test_full_size_solve_600x200(torch, prec):
     assert abs(fem.compliance(p, host_cols(U)) - Jo) <= 1e-6 * abs(Jo)
 
 
-@pytest.mark.parametrize("case,k", [("q4_60x20", 5), ("q4_37x13", 16), ("h8_6x5x4", 5), ("h8_11x9x6", 12), ("q4_1x1", 3)])
+@pytest.mark.parametrize("case,k", [("q4_60x20", 5), ("q4_37x13", 16), ("h8_6x5x4", 5), ("h8_11x9x6", 12), ("q4_1x1", 3),
+                                    ("q4_60x20", 17), ("q4_60x20", 32), ("q4_60x20", 33), ("h8_11x9x6", 1)])
 def test_rom_elem_path(torch, case, k):
     """H(rho) = sum_e E(rho_e) Hel_e + Phi_D^T Phi_D equals Phi^T K(rho) Phi (operator
     convention, Dirichlet rows of Phi non-zero on purpose), and the reduced solve matches the
@@ -355,6 +356,30 @@ def test_rom_elem_path(torch, case, k):
     yo = rom.solve_reduced(0.5 * (Ho + Ho.T), b)
     assert relerr(y.cpu().numpy(), yo) < 1e-9
     assert abs(Jk.item() - b @ yo) <= 1e-10 * abs(b @ yo)
+
+
+@pytest.mark.parametrize("k", [4, 20, 40])
+def test_rom_elem_not_spd_sets_status(torch, k):
+    """Negated element matrices make H negative definite: the reduced solve of the element path
+    (one-warp kernel for k <= 32, the CTA kernels above) reports TOPO_ERR_NOT_SPD and NaN."""
+    from paper_2004_05756_gb300.native import TopoError
+    p = CASES["q4_37x13"]()
+    T = ctx_for(p)
+    rng = np.random.default_rng(5)
+    Phi, _ = np.linalg.qr(rng.standard_normal((p.ndof, k)))
+    npair = k * (k + 1) // 2
+    Hel = torch.zeros((p.nel + 1) * npair, dtype=torch.float64, device="cuda")
+    T.topo_rom_elem(cols(Phi), k, Hel)
+    Hel.neg_()
+    Hw = torch.zeros(k * k, dtype=torch.float64, device="cuda")
+    y = torch.zeros(k, dtype=torch.float64, device="cuda")
+    Jk = torch.zeros(1, dtype=torch.float64, device="cuda")
+    T.topo_rom_solve_elem(dev(rng.uniform(0.1, 1, p.nel)), Hel, k, dev(np.ones(k)), Hw, y, Jk)
+    with pytest.raises(TopoError) as ei:
+        T.topo_check()
+    assert ei.value.status == 4
+    assert np.isnan(y.cpu().numpy()).all() and np.isnan(Jk.item())
+    T.topo_check()  # cleared
 
 
 def test_rom_elem_matches_phi_path_600x200(torch):
