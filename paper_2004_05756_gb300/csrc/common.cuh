@@ -332,7 +332,7 @@ __device__ inline double block_sum(double v, double* red) {
   return t;
 }
 
-// Three block sums at once (result in thread 0; blockDim.x <= 256, a multiple of 32; red holds
+// Three block sums at once (result in thread 0; blockDim.x <= 512, a multiple of 32; red holds
 // 3 * 32 doubles). Within a warp the values are reduced by a butterfly that halves the number
 // of values each lane carries at the first two levels, so the warp spends 6 FP64 additions on
 // all three sums instead of 15 (FP64 issue is scarce on this part); the order is fixed, so
@@ -357,14 +357,21 @@ __device__ inline void block_sum3(double& a, double& b, double& c, double* red) 
   if (l == 16) red[64 + w] = v;
   __syncthreads();
   if (w == 0) {
-    const int q = l >> 3, ww = l & 7;  // lane (q, ww): value q of warp ww
-    double t = (q < 3 && ww < nw) ? red[q * 32 + ww] : 0.0;
+    // lanes 0-15: value 0 of warp l; lanes 16-31: value 1 of warp l - 16; then value 2
+    const int ww = l & 15;
+    double t = ww < nw ? red[(l >> 4) * 32 + ww] : 0.0;
     t += __shfl_xor_sync(0xffffffffu, t, 1);
     t += __shfl_xor_sync(0xffffffffu, t, 2);
     t += __shfl_xor_sync(0xffffffffu, t, 4);
+    t += __shfl_xor_sync(0xffffffffu, t, 8);
+    double u = l < nw ? red[64 + l] : 0.0;
+    u += __shfl_xor_sync(0xffffffffu, u, 1);
+    u += __shfl_xor_sync(0xffffffffu, u, 2);
+    u += __shfl_xor_sync(0xffffffffu, u, 4);
+    u += __shfl_xor_sync(0xffffffffu, u, 8);
     a = __shfl_sync(0xffffffffu, t, 0);
-    b = __shfl_sync(0xffffffffu, t, 8);
-    c = __shfl_sync(0xffffffffu, t, 16);
+    b = __shfl_sync(0xffffffffu, t, 16);
+    c = __shfl_sync(0xffffffffu, u, 0);
   }
   __syncthreads();
 }

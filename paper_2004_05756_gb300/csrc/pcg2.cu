@@ -511,7 +511,7 @@ __device__ __forceinline__ void pcg2_body(const Pcg2Args<DIM>& a, const unsigned
 }
 
 template <int DIM>
-__global__ void __launch_bounds__(P2_THREADS, 2) pcg2_kernel(const __grid_constant__ Pcg2Args<DIM> a) {
+__global__ void __launch_bounds__(P2_THREADS_SOLO, 1) pcg2_kernel(const __grid_constant__ Pcg2Args<DIM> a) {
   pcg2_body<DIM>(a, gridDim.x, blockIdx.x, a.gb);
 }
 
@@ -603,12 +603,12 @@ topo_status solve_stencil_fp64(topo_ctx* c, const double* rho, const double* F, 
   const Grid& g = c->g;
   const long long nunits = (long long)((g.nnx + 31) / 32) * g.nny * g.nnz;
   int occ = 0;
-  TOPO_CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pcg2_kernel<DIM>, P2_THREADS, 0));
+  TOPO_CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pcg2_kernel<DIM>, P2_THREADS_SOLO, 0));
   if (occ < 1) return fail(c, TOPO_ERR_CUDA, "pcg2 kernel cannot be resident");
   const int per_sm = c->pcg_blocks_per_sm > 0 ? std::min(c->pcg_blocks_per_sm, occ) : std::min(occ, 2);
   long long G = (long long)per_sm * c->num_sms;
   if (c->pcg_max_ctas > 0 && G > c->pcg_max_ctas) G = c->pcg_max_ctas;  // a share of the GPU
-  const long long maxG = (nunits + 7) / 8;  // at least one unit per warp
+  const long long maxG = (nunits + P2_THREADS_SOLO / 32 - 1) / (P2_THREADS_SOLO / 32);  // >= 1 unit per warp
   if (G > maxG) G = std::max(1LL, maxG);
   Pcg2Args<DIM> a;
   topo_status st = build_pcg2_args<DIM>(c, rho, F, U, m, ld, rtol, maxit, (int)G, &a, c->d_sync);
@@ -618,7 +618,7 @@ topo_status solve_stencil_fp64(topo_ctx* c, const double* rho, const double* F, 
   TOPO_CUDA_TRY(c, cudaMemsetAsync(a.info, 0, 32, c->stream));
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)G);
-  cfg.blockDim = dim3(P2_THREADS);
+  cfg.blockDim = dim3(P2_THREADS_SOLO);
   cfg.stream = c->stream;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;

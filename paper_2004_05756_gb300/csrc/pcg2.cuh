@@ -6,7 +6,8 @@
 namespace topo {
 
 constexpr int P2_MAX_COLS = 32;
-constexpr int P2_THREADS = 256;
+constexpr int P2_THREADS = 256;       // batched kernel: up to 4 CTAs per SM
+constexpr int P2_THREADS_SOLO = 512;  // single solve: one CTA per SM (half the barrier arrivals)
 
 template <int DIM>
 struct Pcg2Args {

@@ -95,8 +95,9 @@ class Server:
         self.rtol = rtol
         self.maxit = maxit
         props = torch.cuda.get_device_properties(torch.cuda.current_device())
-        # every persistent solve of a request uses this many CTAs (2 per SM split over the slots)
-        self.ctas = max(1, (2 * props.multi_processor_count) // slots)
+        # every persistent solve of a request uses this many CTAs (the SMs split over the slots;
+        # one solve CTA fills an SM)
+        self.ctas = max(1, props.multi_processor_count // slots)
         self.streams = [torch.cuda.Stream() for _ in range(slots)]
         self.lock = threading.Condition()
         self.in_use = 0
