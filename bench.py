@@ -32,6 +32,22 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+# DRAM bytes (read + write) of one pcg2_kernel launch of the default step, from a one-pass ncu
+# capture of `python bench.py --steps 1 --warmup 3 --no-cpu-baseline`
+# (profiles/pcg2_kernel_fp64_mbb600x200.md). It is reported only while the kernel sources hash to
+# the value they had when it was taken.
+PCG_TRAFFIC = {"bytes": 5.16e6 + 11.80e6, "sources_sha256_16": "da33574bf4d0d601"}
+
+
+def pcg_traffic():
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("pcg2.cu", "pcg2.cuh", "common.cuh"):
+        with open(os.path.join(ROOT, "paper_2004_05756_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return PCG_TRAFFIC["bytes"] if h.hexdigest()[:16] == PCG_TRAFFIC["sources_sha256_16"] else None
+
+
 METRIC = "design evals/s (ROM vs plain FP64 HDM) at 1e-6 rel compliance err; p50/p99 ms"
 UNIT = "design evals/s"
 
@@ -389,7 +405,8 @@ def run_ours(args, rank, world):
         "accuracy": {"hdm_J_vs_fp64_rel": hdm_rel, "rom_Jk_vs_fp64_phi_path_rel": rom_rel, "J_centre": J_centre},
         "roofline": {"kernel": "pcg2_kernel (assembled-stencil Chronopoulos-Gear PCG, one launch per HDM solve)",
                      "bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
-                     "frac": achieved / fp64_peak, "traffic": None, "launch_ms": solve_ms,
+                     "frac": achieved / fp64_peak, "traffic": pcg_traffic(), "traffic_unit": "bytes per launch",
+                     "launch_ms": solve_ms,
                      "peak_source": "derived: 152 SMs x 4 FP64 flop/clk x 2.07 GHz (measured FMA peak 1.19)",
                      "flop_per_dof_iter": flop_dof, "hbm_peak_gbs": hbm_peak},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
