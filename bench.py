@@ -33,9 +33,9 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 # DRAM bytes (read + write) of one pcg2_kernel launch of the default step, from a one-pass ncu
-# capture of `python bench.py --steps 1 --warmup 3 --no-cpu-baseline`
-# (profiles/pcg2_kernel_fp64_mbb600x200.md). It is reported only while the kernel sources hash to
-# the value they had when it was taken.
+# capture (dram__bytes_read.sum, dram__bytes_write.sum) of
+# `python bench.py --steps 1 --warmup 3 --no-cpu-baseline`. It is reported only while the kernel
+# sources hash to the value they had when it was taken.
 PCG_TRAFFIC = {"bytes": 5.16e6 + 11.80e6, "sources_sha256_16": "da33574bf4d0d601"}
 
 
