@@ -528,7 +528,10 @@ def run_serving(args):
     warm = serving.poisson_requests(2, rate_per_s=100.0, seed=99, q4=((100, 50), (120, 60)),
                                     h8=((16, 16, 16), (20, 20, 20)))
     srv.run(warm, realtime=False)
-    reqs = serving.poisson_requests(args.requests, rate_per_s=args.rate, seed=7)
+    if args.sessions > 0:
+        reqs = serving.session_requests(args.requests, rate_per_s=args.rate, sessions=args.sessions, seed=7)
+    else:
+        reqs = serving.poisson_requests(args.requests, rate_per_s=args.rate, seed=7)
     t0 = time.perf_counter()
     res = srv.run(reqs, realtime=True)
     wall = time.perf_counter() - t0
@@ -536,9 +539,12 @@ def run_serving(args):
     return {"metric": METRIC, "value": s["evals_per_s"], "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 1,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": f"serving: {len(reqs)} Poisson requests at {args.rate}/s, 50/50 Q4 100x50..800x400 "
-                                   f"and H8 32^3..96x48x48, {args.slots} slots", "slots": args.slots,
-                       "rate_per_s": args.rate},
+                                   f"and H8 32^3..96x48x48, {args.slots} slots, " +
+                                   (f"{args.sessions} sessions (resident basis, window {srv.kmax})" if args.sessions
+                                    else "standalone requests (one-snapshot basis)"), "slots": args.slots,
+                       "rate_per_s": args.rate, "sessions": args.sessions},
             "p50_ms": s["p50_ms"], "p99_ms": s["p99_ms"], "hdm_fallbacks": s["hdm_fallbacks"],
+            "rom_evals": s["rom_evals"], "mean_basis_size": s["mean_basis_size"],
             "max_concurrency": srv.max_concurrency, "wall_s": wall}
 
 
@@ -560,6 +566,8 @@ def main():
     ap.add_argument("--slots", type=int, default=4, help="serving: concurrent request slots")
     ap.add_argument("--requests", type=int, default=32, help="serving: requests in the stream")
     ap.add_argument("--rate", type=float, default=2.0, help="serving: Poisson arrival rate (requests/s)")
+    ap.add_argument("--sessions", type=int, default=8,
+                    help="serving: optimisation sessions the requests belong to (0 = standalone requests)")
     args = ap.parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

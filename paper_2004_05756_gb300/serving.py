@@ -1,24 +1,37 @@
 """Serving form: continuous batching of design-evaluation requests on one GPU.
 
 A request is one trust-region design evaluation in the shape of one major iteration of the
-paper's Algorithm 2, for one problem (2D Q4 MBB or 3D H8 cantilever) and one seeded design:
+paper's Algorithm 2, for one problem (2D Q4 MBB or 3D H8 cantilever):
 
   1. filter the centre design and solve the full-order model there (the new snapshot);
-  2. build the reduced basis from the snapshot window (here the centre state) and the
-     element reduced matrices of the basis;
-  3. evaluate the candidate design with the reduced model: reduced solve, residual estimate
+  2. build the reduced basis from the snapshot window and the element reduced matrices of the
+     basis;
+  3. evaluate the proposed candidate with the reduced model: reduced solve, residual estimate
      theta = ||f - K(rho) Phi y|| (the error-aware trust-region constraint, Eq. trcon-topopt);
-  4. if theta > Delta = tau ||f|| (tau = 0.1: the scaling of the initial radius, Eq. trrad0,
-     since r(0, rho) = -f), fall back to a full-order solve at the candidate;
+  4. the trust-region constraint theta <= Delta = tau ||f|| (tau = 0.1: the scaling of the
+     initial radius, Eq. trrad0, since r(0, rho) = -f) decides the candidate the way the
+     subproblem's constraint does: the largest step from the centre toward the proposal,
+     s = 1, 1/2, ..., 2^-tr_halvings, whose reduced evaluation satisfies it is taken; if none
+     does, the proposal (s = 1) is evaluated with a full-order solve started from its reduced
+     state u_k;
   5. compliance and filtered gradient at the candidate (from u_k, or from the HDM state).
 
-The server keeps `slots` workers. Each owns a CUDA stream; a request admitted to a slot keeps
-its densities, basis, element reduced matrices and CG state resident in device memory until it
-completes. Requests are admitted in arrival order as soon as a slot is free AND the request's
-estimated device memory fits the free budget (admission by free HBM), so requests that arrive
-while others run start as capacity frees up and their kernels overlap on the GPU. Every
-persistent solve of a request uses a fixed share of the GPU (total CTAs / slots), which also
-fixes its reduction order: a request's results are bitwise the same alone and in a mix.
+Requests either stand alone (their window is the one centre snapshot) or belong to a session:
+the consecutive evaluations of one optimisation run. A session keeps its context, snapshot
+window (the last kmax centre states), basis, element reduced matrices and last centre state
+resident in device memory between its requests, so its basis grows with the run and its centre
+solves start from the previous centre's state (a warm start of the iterative solve; the
+converged result is the same fixed point). The designs of a session follow a seeded random
+walk: the centre of step t is the previous centre plus a smoothed perturbation of amplitude
+0.02, the candidate the centre plus one of amplitude 0.05.
+
+The server keeps `slots` request slots. Requests start in arrival order as soon as a slot is
+free and, for a standalone request or the first request of a session, its estimated device
+memory fits the free budget (admission by free HBM). Requests of one session run in order;
+requests of different sessions and standalone requests overlap on the GPU. A session's memory
+is released after its last request. Every persistent solve uses a fixed share of the GPU (its
+SMs divided by the slots), which also fixes its reduction order: a request's results are
+bitwise the same alone and in a mix.
 
 All arithmetic runs in libtopo's kernels; this module only schedules and marshals.
 """
@@ -41,6 +54,9 @@ class Request:
     shape: tuple
     seed: int
     arrival: float = 0.0  # seconds after the stream starts
+    session: int | None = None  # optimisation run this request belongs to (None: standalone)
+    step: int = 0  # index of the request within its session
+    last: bool = True  # the session's last request (its state is released afterwards)
 
 
 @dataclasses.dataclass
@@ -53,36 +69,80 @@ class Result:
     Jk: float
     grad_norm: float
     hdm_iters: int
+    k: int
+    step: float  # trust-region step taken toward the proposed candidate (1 on fallback)
+    rom_evals: int
     t_arrival: float
     t_start: float
     t_done: float
+    session: int | None = None
+    index: int = 0  # position of the request within its session
 
     @property
     def latency(self) -> float:
         return self.t_done - self.t_arrival
 
 
-def estimate_bytes(dim: int, shape, k: int = 1) -> int:
-    """Device memory a request keeps resident (FP64): the assembled stencil of the solve
-    (3^d d^2 words per node), PCG vectors and scratch, densities, the basis, the element
-    reduced matrices and a few vectors of the request itself."""
+def _sizes(dim: int, shape):
     if dim == 2:
         nx, ny = shape
-        nodes, nel = (nx + 1) * (ny + 1), nx * ny
-    else:
-        nx, ny, nz = shape
-        nodes, nel = (nx + 1) * (ny + 1) * (nz + 1), nx * ny * nz
+        return (nx + 1) * (ny + 1), nx * ny
+    nx, ny, nz = shape
+    return (nx + 1) * (ny + 1) * (nz + 1), nx * ny * nz
+
+
+def estimate_bytes(dim: int, shape, k: int = 1) -> int:
+    """Device memory a request (or a session with a window of k snapshots) keeps resident
+    (FP64): the assembled stencil of the solve (3^d d^2 words per node), PCG vectors and
+    scratch, densities, the window and the basis, the element reduced matrices and a few
+    vectors of the request itself."""
+    nodes, nel = _sizes(dim, shape)
     ndof = dim * nodes
     nc = (9 if dim == 2 else 27) * dim * dim
-    words = nc * nodes + 8 * ndof + 6 * nel + k * ndof + (k * (k + 1) // 2) * (nel + 1) + 6 * ndof
+    words = nc * nodes + 8 * ndof + 6 * nel + 2 * k * ndof + (k * (k + 1) // 2) * (nel + 1) + 6 * ndof
     return 8 * words + (4 << 20)
 
 
+class _Session:
+    """Resident state of one optimisation run (device tensors on the session's own stream)."""
+
+    def __init__(self, srv: "Server", req: Request):
+        torch, native = srv.torch, srv.native
+        self.p = w.build_problem(req.dim, req.shape)
+        self.stream = torch.cuda.Stream()
+        self.kmax = srv.kmax
+        p = self.p
+        f64 = dict(dtype=torch.float64, device="cuda")
+        with torch.cuda.stream(self.stream):
+            self.T = native.Topo(p, stream=self.stream)
+            self.T.topo_set_param(native.TOPO_PARAM_PCG_MAX_CTAS, srv.ctas)
+            self.window = torch.zeros((self.kmax, p.ndof), **f64)
+            self.Phi = torch.zeros((self.kmax, p.ndof), **f64)
+            self.Hel = torch.zeros((p.nel + 1) * self.kmax * (self.kmax + 1) // 2, **f64)
+            self.u_prev = torch.zeros((1, p.ndof), **f64)
+        self.nwin = 0
+        self.seed = req.seed
+        self.psi = w.design_field(p, req.seed)  # centre of step 0
+
+    def designs(self, step: int):
+        """Centre and candidate of the given step (the steps of a session arrive in order)."""
+        if step > 0:
+            self.psi = w.perturbed_designs(self.p, self.psi, 1, amplitude=0.02,
+                                           first_seed=w.seed_for(f"walk{self.seed}", 2 * step))[:, 0]
+        psi_x = w.perturbed_designs(self.p, self.psi, 1, amplitude=0.05,
+                                    first_seed=w.seed_for(f"walk{self.seed}", 2 * step + 1))[:, 0]
+        return self.psi, psi_x
+
+    def close(self):
+        self.stream.synchronize()
+        self.T.close()
+
+
 class Server:
-    """Continuous-batching server over libtopo contexts (one per admitted request)."""
+    """Continuous-batching server over libtopo contexts."""
 
     def __init__(self, slots: int = 4, budget_bytes: int | None = None, tau: float = 0.1, rtol: float = 1e-8,
-                 maxit: int = 400000):
+                 maxit: int = 400000, kmax: int = 8, tr_halvings: int = 6):
         import torch
         from . import build, native
         build.build()
@@ -94,6 +154,8 @@ class Server:
         self.tau = tau
         self.rtol = rtol
         self.maxit = maxit
+        self.kmax = kmax
+        self.tr_halvings = tr_halvings
         props = torch.cuda.get_device_properties(torch.cuda.current_device())
         # every persistent solve of a request uses this many CTAs (the SMs split over the slots;
         # one solve CTA fills an SM)
@@ -105,8 +167,73 @@ class Server:
         self.max_concurrency = 0
         self.concurrency = 0
 
-    # -- one request ------------------------------------------------------------------------
-    def _evaluate(self, req: Request, stream) -> dict:
+    # -- one evaluation -----------------------------------------------------------------------
+    def _evaluate(self, T, p, psi_c, psi_x, window, nwin, Phi, Hel, U0, stream) -> dict:
+        """Steps 1-5 on context T. The new centre state goes to slot (nwin - 1) % kmax of the
+        window (kmax x N); U0 is the centre solve's initial guess and receives its solution."""
+        torch = self.torch
+        f64 = dict(dtype=torch.float64, device="cuda")
+        with torch.cuda.stream(stream):
+            rho = torch.empty(p.nel, **f64)
+            T.topo_filter(torch.as_tensor(psi_c).to(**f64), rho)
+            F = torch.as_tensor(p.F[:, :1].T.copy()).to(**f64)
+            f = F[0]
+            info = T.topo_solve_hdm(rho, F, U0, rtol=self.rtol, maxit=self.maxit, prec="fp64")
+            iters = info["iters"]
+            kmax = window.shape[0]
+            window[(nwin - 1) % kmax].copy_(U0[0])
+            m = min(nwin, kmax)
+            H = torch.zeros(m * m, **f64)
+            b = torch.zeros(m, **f64)
+            k = T.topo_rom_build(rho, window[:m], Phi, H, b, f)
+            T.topo_rom_elem(Phi[:k], k, Hel)
+            fnorm = float(np.linalg.norm(p.F[:, 0]))
+            delta = self.tau * fnorm
+            Hw = torch.zeros(k * k, **f64)
+
+            def rom_at(psi):
+                rho_s = torch.empty(p.nel, **f64)
+                T.topo_filter(torch.as_tensor(psi).to(**f64), rho_s)
+                y = torch.zeros(k, **f64)
+                Jk = torch.zeros(1, **f64)
+                T.topo_rom_solve_elem(rho_s, Hel, k, b[:k], Hw, y, Jk)
+                rn = torch.zeros(2, **f64)
+                uk = torch.zeros(p.ndof, **f64)
+                T.topo_rom_error(rho_s, Phi[:k], k, y, f, rn, uk)
+                return rho_s, uk, Jk.item(), rn[0].item()
+
+            # the largest step toward the proposal that the trust-region constraint admits
+            first = None
+            s, nrom, acc = 1.0, 0, None
+            for h in range(self.tr_halvings + 1):
+                ev = rom_at(psi_x if h == 0 else psi_c + s * (psi_x - psi_c))
+                nrom += 1
+                if first is None:
+                    first = ev
+                if ev[3] <= delta:
+                    acc = ev
+                    break
+                s *= 0.5
+            used_hdm = acc is None
+            if used_hdm:  # full-order solve at the proposal, from its reduced state
+                rho_x, uk, Jk, theta = first
+                s = 1.0
+                Ux = uk.reshape(1, -1).clone()
+                info2 = T.topo_solve_hdm(rho_x, F, Ux, rtol=self.rtol, maxit=self.maxit, prec="fp64")
+                iters += info2["iters"]
+            else:
+                rho_x, uk, Jk, theta = acc
+                Ux = uk.reshape(1, -1)
+            J = torch.zeros(1, **f64)
+            dc = torch.empty(p.nel, **f64)
+            dpsi = torch.empty(p.nel, **f64)
+            T.topo_compliance_grad(rho_x, Ux, F, J, dc, dpsi)
+            T.topo_check()
+            return dict(J=J.item(), theta=theta, delta=delta, used_hdm=bool(used_hdm), Jk=Jk,
+                        grad_norm=float(torch.linalg.vector_norm(dpsi).item()), hdm_iters=iters, k=k, step=s,
+                        rom_evals=nrom)
+
+    def _standalone(self, req: Request, stream) -> dict:
         torch, native = self.torch, self.native
         p = w.build_problem(req.dim, req.shape)
         f64 = dict(dtype=torch.float64, device="cuda")
@@ -115,107 +242,143 @@ class Server:
             T.topo_set_param(native.TOPO_PARAM_PCG_MAX_CTAS, self.ctas)
             psi_c = w.design_field(p, req.seed)
             psi_x = w.perturbed_designs(p, psi_c, 1, amplitude=0.05, first_seed=req.seed % 100000 + 1)[:, 0]
-            rho = torch.empty(p.nel, **f64)
-            T.topo_filter(torch.as_tensor(psi_c).to(**f64), rho)
-            F = torch.as_tensor(p.F[:, :1].T.copy()).to(**f64)
-            f = F[0]
-            U = torch.zeros((1, p.ndof), **f64)
-            info = T.topo_solve_hdm(rho, F, U, rtol=self.rtol, maxit=self.maxit, prec="fp64")
-            iters = info["iters"]
-            Phi = torch.zeros_like(U)
-            H = torch.zeros(1, **f64)
-            b = torch.zeros(1, **f64)
-            k = T.topo_rom_build(rho, U, Phi, H, b, f)
-            Hel = torch.zeros((p.nel + 1) * k * (k + 1) // 2, **f64)
-            T.topo_rom_elem(Phi[:k], k, Hel)
-            rho_x = torch.empty(p.nel, **f64)
-            T.topo_filter(torch.as_tensor(psi_x).to(**f64), rho_x)
-            Hw = torch.zeros(k * k, **f64)
-            y = torch.zeros(k, **f64)
-            Jk = torch.zeros(1, **f64)
-            T.topo_rom_solve_elem(rho_x, Hel, k, b[:k], Hw, y, Jk)
-            rn = torch.zeros(2, **f64)
-            uk = torch.zeros(p.ndof, **f64)
-            T.topo_rom_error(rho_x, Phi[:k], k, y, f, rn, uk)
-            theta = rn[0].item()
-            fnorm = float(np.linalg.norm(p.F[:, 0]))
-            delta = self.tau * fnorm
-            used_hdm = theta > delta
-            Ux = uk.reshape(1, -1)
-            if used_hdm:
-                Ux = torch.zeros((1, p.ndof), **f64)
-                info2 = T.topo_solve_hdm(rho_x, F, Ux, rtol=self.rtol, maxit=self.maxit, prec="fp64")
-                iters += info2["iters"]
-            J = torch.zeros(1, **f64)
-            dc = torch.empty(p.nel, **f64)
-            dpsi = torch.empty(p.nel, **f64)
-            T.topo_compliance_grad(rho_x, Ux, F, J, dc, dpsi)
-            T.topo_check()
-            out = dict(J=J.item(), theta=theta, delta=delta, used_hdm=bool(used_hdm), Jk=Jk.item(),
-                       grad_norm=float(torch.linalg.vector_norm(dpsi).item()), hdm_iters=iters)
+            window = torch.zeros((1, p.ndof), **f64)
+            Phi = torch.zeros((1, p.ndof), **f64)
+            Hel = torch.zeros(p.nel + 1, **f64)
+            U0 = torch.zeros((1, p.ndof), **f64)
+            out = self._evaluate(T, p, psi_c, psi_x, window, 1, Phi, Hel, U0, stream)
             T.close()
         return out
 
-    # -- the stream -----------------------------------------------------------------------
+    def _in_session(self, S: _Session, req: Request) -> dict:
+        psi_c, psi_x = S.designs(req.step)
+        S.nwin += 1
+        return self._evaluate(S.T, S.p, psi_c, psi_x, S.window, S.nwin, S.Phi, S.Hel, S.u_prev, S.stream)
+
+    # -- the stream -----------------------------------------------------------------------------
+    def _acquire(self, need: int) -> int:
+        with self.lock:
+            while not self.free_slots or self.in_use + need > self.budget:
+                self.lock.wait()
+            slot = self.free_slots.pop(0)
+            self.in_use += need
+            self.concurrency += 1
+            self.max_concurrency = max(self.max_concurrency, self.concurrency)
+            return slot
+
+    def _release(self, slot: int, freed: int):
+        with self.lock:
+            self.in_use -= freed
+            self.free_slots.append(slot)
+            self.concurrency -= 1
+            self.lock.notify_all()
+
     def run(self, requests: list[Request], realtime: bool = True) -> list[Result]:
-        """Serve the requests; arrival times are honoured when realtime is true (requests are
-        then admitted no earlier than their arrival), otherwise all arrive at t = 0."""
+        """Serve the requests; arrival times are honoured when realtime is true (requests then
+        start no earlier than their arrival), otherwise all arrive at t = 0."""
         reqs = sorted(requests, key=lambda r: r.arrival)
-        results: list[Result | None] = [None] * len(reqs)
+        results: dict[int, Result] = {}
         errors = []
         t0 = time.perf_counter()
-        threads = []
 
-        def worker(idx: int, req: Request, slot: int, need: int, t_arr: float):
-            t_start = time.perf_counter() - t0
-            try:
-                out = self._evaluate(req, self.streams[slot])
-                results[idx] = Result(rid=req.rid, t_arrival=t_arr, t_start=t_start,
-                                      t_done=time.perf_counter() - t0, **out)
-            except Exception as e:  # surfaced after the stream
-                errors.append((req.rid, e))
-            finally:
-                with self.lock:
-                    self.in_use -= need
-                    self.free_slots.append(slot)
-                    self.concurrency -= 1
-                    self.lock.notify_all()
-
-        for idx, req in enumerate(reqs):
-            t_arr = req.arrival if realtime else 0.0
+        def wait_arrival(req):
             if realtime:
-                wait = t0 + req.arrival - time.perf_counter()
-                if wait > 0:
-                    time.sleep(wait)
+                dt = t0 + req.arrival - time.perf_counter()
+                if dt > 0:
+                    time.sleep(dt)
+            return req.arrival if realtime else 0.0
+
+        def standalone_worker(req: Request):
+            t_arr = wait_arrival(req)
             need = estimate_bytes(req.dim, req.shape)
             if need > self.budget:
                 errors.append((req.rid, MemoryError(f"request needs {need} B > budget {self.budget} B")))
-                continue
-            with self.lock:
-                while not self.free_slots or self.in_use + need > self.budget:
-                    self.lock.wait()
-                slot = self.free_slots.pop(0)
-                self.in_use += need
-                self.concurrency += 1
-                self.max_concurrency = max(self.max_concurrency, self.concurrency)
-            th = threading.Thread(target=worker, args=(idx, req, slot, need, t_arr), daemon=True)
+                return
+            slot = self._acquire(need)
+            t_start = time.perf_counter() - t0
+            try:
+                out = self._standalone(req, self.streams[slot])
+                results[req.rid] = Result(rid=req.rid, t_arrival=t_arr, t_start=t_start,
+                                          t_done=time.perf_counter() - t0, **out)
+            except Exception as e:  # surfaced after the stream
+                errors.append((req.rid, e))
+            finally:
+                self._release(slot, need)
+
+        def session_worker(sid: int, sreqs: list[Request]):
+            S = None
+            held = 0
+            try:
+                for n, req in enumerate(sreqs):
+                    t_arr = wait_arrival(req)
+                    need = 0
+                    if S is None:  # the session's memory is admitted with its first request
+                        need = estimate_bytes(req.dim, req.shape, self.kmax)
+                        if need > self.budget:
+                            raise MemoryError(f"session {sid} needs {need} B > budget {self.budget} B")
+                    slot = self._acquire(need)
+                    held += need
+                    last = n == len(sreqs) - 1
+                    t_start = time.perf_counter() - t0
+                    try:
+                        if S is None:
+                            S = _Session(self, req)
+                        out = self._in_session(S, req)
+                        results[req.rid] = Result(rid=req.rid, t_arrival=t_arr, t_start=t_start,
+                                                  t_done=time.perf_counter() - t0, session=sid, index=req.step,
+                                                  **out)
+                    finally:
+                        if last and S is not None:
+                            S.close()
+                            S = None
+                        self._release(slot, held if last else 0)
+                        if last:
+                            held = 0
+            except Exception as e:  # surfaced after the stream
+                errors.append((sid, e))
+                if S is not None:
+                    S.close()
+                if held:
+                    with self.lock:
+                        self.in_use -= held
+                        self.lock.notify_all()
+
+        threads = []
+        sessions: dict[int, list[Request]] = {}
+        for req in reqs:
+            if req.session is None:
+                threads.append(threading.Thread(target=standalone_worker, args=(req,), daemon=True))
+            else:
+                sessions.setdefault(req.session, []).append(req)
+        for sid, sreqs in sessions.items():
+            sreqs.sort(key=lambda r: r.step)
+            threads.append(threading.Thread(target=session_worker, args=(sid, sreqs), daemon=True))
+        for th in threads:
             th.start()
-            threads.append(th)
         for th in threads:
             th.join()
         if errors:
             rid, e = errors[0]
-            raise RuntimeError(f"request {rid} failed: {e}") from e
-        return [r for r in results if r is not None]
+            raise RuntimeError(f"request or session {rid} failed: {e}") from e
+        return [results[r.rid] for r in reqs if r.rid in results]
 
 
 def poisson_requests(count: int, rate_per_s: float, seed: int = 7, q4=((100, 50), (800, 400)),
                      h8=((32, 32, 32), (96, 48, 48))) -> list[Request]:
-    """The seeded serving stream: Poisson arrivals, half 2D Q4, half 3D H8, sizes log-uniform
-    between the given corners."""
+    """The seeded standalone stream: Poisson arrivals, half 2D Q4, half 3D H8, sizes
+    log-uniform between the given corners."""
     raw = w.serving_stream(count, rate_per_s=rate_per_s, seed=seed, q4_range=q4, h8_range=h8)
     return [Request(rid=i, dim=r["dim"], shape=tuple(r["shape"]), seed=r["seed"] % (2 ** 31), arrival=r["arrival"])
             for i, r in enumerate(raw)]
+
+
+def session_requests(count: int, rate_per_s: float, sessions: int = 8, seed: int = 7, q4=((100, 50), (800, 400)),
+                     h8=((32, 32, 32), (96, 48, 48))) -> list[Request]:
+    """The seeded session stream: Poisson arrivals of the next evaluation of one of `sessions`
+    optimisation runs (half 2D Q4, half 3D H8)."""
+    raw = w.session_stream(count, rate_per_s=rate_per_s, sessions=sessions, seed=seed, q4_range=q4, h8_range=h8)
+    return [Request(rid=i, dim=r["dim"], shape=tuple(r["shape"]), seed=r["seed"] % (2 ** 31), arrival=r["arrival"],
+                    session=r["session"], step=r["step"], last=r["last"]) for i, r in enumerate(raw)]
 
 
 def summarize(results: list[Result], wall: float) -> dict:
@@ -223,4 +386,6 @@ def summarize(results: list[Result], wall: float) -> dict:
     pick = lambda q: lat[min(len(lat) - 1, int(math.ceil(q * len(lat))) - 1)] if lat else None
     return dict(requests=len(results), evals_per_s=len(results) / wall if wall > 0 else None,
                 p50_ms=1e3 * pick(0.50), p99_ms=1e3 * pick(0.99),
-                hdm_fallbacks=sum(r.used_hdm for r in results))
+                hdm_fallbacks=sum(r.used_hdm for r in results),
+                rom_evals=sum(r.rom_evals for r in results),
+                mean_basis_size=(sum(r.k for r in results) / len(results)) if results else None)

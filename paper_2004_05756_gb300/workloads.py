@@ -235,6 +235,37 @@ def serving_stream(count: int = 2000, rate_per_s: float = 100.0, seed: int = 7,
     return out
 
 
+def session_stream(count: int, rate_per_s: float, sessions: int = 8, seed: int = 7,
+                   q4_range=((100, 50), (800, 400)), h8_range=((32, 32, 32), (96, 48, 48))):
+    """Poisson stream of requests that belong to `sessions` concurrent optimisation runs (half
+    2D Q4, half 3D H8, sizes log-uniform between the corners): each request is the next
+    trust-region evaluation of a session picked at random. Returns dicts with arrival time,
+    session id, step within the session, last-request flag, problem shape and the session's
+    seed."""
+    rng = np.random.default_rng(seed)
+    shapes = []
+    for s in range(sessions):
+        is3d = s % 2 == 1
+        lo, hi = h8_range if is3d else q4_range
+        u = rng.uniform()
+        shapes.append((3 if is3d else 2,
+                       tuple(int(round(math.exp(math.log(a) + u * (math.log(b) - math.log(a))))) for a, b in zip(lo, hi))))
+    t = 0.0
+    steps = [0] * sessions
+    out = []
+    for r in range(count):
+        t += rng.exponential(1.0 / rate_per_s)
+        s = int(rng.integers(0, sessions))
+        dim, shape = shapes[s]
+        out.append(dict(arrival=t, session=s, step=steps[s], dim=dim, shape=shape, seed=seed_for("session", s)))
+        steps[s] += 1
+    seen = set()
+    for d in reversed(out):  # mark each session's last request
+        d["last"] = d["session"] not in seen
+        seen.add(d["session"])
+    return out
+
+
 def build_problem(dim: int, shape) -> Problem:
     if dim == 2:
         return mbb_2d(shape[0], shape[1], rmin=1.5)

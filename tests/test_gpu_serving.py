@@ -31,6 +31,25 @@ def test_alone_equals_mix_bitwise():
         assert (alone.J, alone.theta, alone.Jk, alone.used_hdm) == (m.J, m.theta, m.Jk, m.used_hdm), req
 
 
+def _oracle_step(p, psi_c, psi_x, Phi, halvings=6):
+    """The candidate of a request by the oracle: the largest step s = 1, 1/2, ... toward the
+    proposal whose reduced residual satisfies theta <= 0.1 ||f||, else the proposal itself by
+    a direct solve. Returns (s, theta, J_k, J, fallback)."""
+    f = p.F[:, 0]
+    delta = 0.1 * np.linalg.norm(f)
+    s, first = 1.0, None
+    for h in range(halvings + 1):
+        psi = psi_x if h == 0 else psi_c + s * (psi_x - psi_c)
+        ev = rom.rom_eval(p, hatfilter.filter_fwd(p, psi), Phi, f)
+        if first is None:
+            first = ev
+        if ev["resnorm"] <= delta:
+            return s, ev["resnorm"], ev["Jk"], ev["Jk"], False
+        s *= 0.5
+    rho_x = hatfilter.filter_fwd(p, psi_x)
+    return 1.0, first["resnorm"], first["Jk"], fem.compliance(p, fem.solve(p, rho_x)), True
+
+
 def test_request_matches_oracle():
     require_cuda()
     from paper_2004_05756_gb300.serving import Request, Server
@@ -39,17 +58,13 @@ def test_request_matches_oracle():
     p = w.build_problem(d, shape)
     psi_c = w.design_field(p, seed)
     psi_x = w.perturbed_designs(p, psi_c, 1, amplitude=0.05, first_seed=seed % 100000 + 1)[:, 0]
-    rho_c = hatfilter.filter_fwd(p, psi_c)
-    rho_x = hatfilter.filter_fwd(p, psi_x)
-    u_c = fem.solve(p, rho_c)[:, 0]
+    u_c = fem.solve(p, hatfilter.filter_fwd(p, psi_c))[:, 0]
     Phi = rom.basis(u_c[:, None])
-    ev = rom.rom_eval(p, rho_x, Phi, p.F[:, 0])
-    assert res.theta == pytest.approx(ev["resnorm"], rel=1e-6)
-    assert res.Jk == pytest.approx(ev["Jk"], rel=1e-8)
-    delta = 0.1 * np.linalg.norm(p.F[:, 0])
-    assert res.used_hdm == (ev["resnorm"] > delta)
-    Jo = fem.compliance(p, fem.solve(p, rho_x)) if res.used_hdm else ev["Jk"]
-    assert res.J == pytest.approx(Jo, rel=1e-8)
+    s, theta, Jk, J, fallback = _oracle_step(p, psi_c, psi_x, Phi)
+    assert res.step == s and res.used_hdm == fallback
+    assert res.theta == pytest.approx(theta, rel=1e-6)
+    assert res.Jk == pytest.approx(Jk, rel=1e-8)
+    assert res.J == pytest.approx(J, rel=1e-8)
 
 
 def test_admission_by_memory_budget():
@@ -60,3 +75,62 @@ def test_admission_by_memory_budget():
     srv = Server(slots=3, budget_bytes=int(1.2 * biggest))
     out = srv.run(reqs, realtime=False)
     assert len(out) == len(reqs) and srv.max_concurrency == 1
+
+
+SESS = [(2, (40, 20)), (3, (8, 8, 8)), (2, (30, 15))]
+
+
+def _session_requests(steps=4):
+    from paper_2004_05756_gb300.serving import Request
+    out = []
+    for t in range(steps):
+        for s, (d, shape) in enumerate(SESS):
+            out.append(Request(rid=len(out), dim=d, shape=shape, seed=100 + s, arrival=0.01 * len(out), session=s,
+                               step=t, last=t == steps - 1))
+    return out
+
+
+def test_sessions_alone_equal_mix_and_basis_grows():
+    """Sessions keep their basis between requests: results are bitwise the same when a
+    session runs alone and when its requests interleave with the others', the basis grows
+    with the session, and the reduced model takes over from the full-order fallback."""
+    require_cuda()
+    from paper_2004_05756_gb300.serving import Server
+    reqs = _session_requests()
+    srv = Server(slots=3, kmax=4)
+    mix = {r.rid: r for r in srv.run(reqs, realtime=True)}
+    assert srv.max_concurrency >= 2
+    for s in range(len(SESS)):
+        mine = [r for r in _session_requests() if r.session == s]
+        alone = Server(slots=3, kmax=4).run(mine, realtime=False)
+        for a in alone:
+            m = mix[a.rid]
+            assert (a.J, a.theta, a.Jk, a.used_hdm, a.k, a.step) == (m.J, m.theta, m.Jk, m.used_hdm, m.k, m.step), \
+                (s, a.index)
+        assert [a.k for a in sorted(alone, key=lambda r: r.index)] == [1, 2, 3, 4]
+    # the trust-region step search finds admissible candidates: the reduced model answers
+    assert sum(not r.used_hdm for r in mix.values()) >= len(mix) // 2, \
+        [(r.session, r.index, r.step, r.theta / r.delta) for r in mix.values()]
+
+
+def test_session_request_matches_oracle():
+    """Step 1 of a session: a two-snapshot window (centres of steps 0 and 1), the reduced
+    evaluation at the candidate, against the oracle's direct solves and reduced model."""
+    require_cuda()
+    from paper_2004_05756_gb300.serving import Request, Server
+    d, shape = SESS[0]
+    reqs = [Request(rid=t, dim=d, shape=shape, seed=100, arrival=0.0, session=0, step=t, last=t == 1)
+            for t in range(2)]
+    res = sorted(Server(slots=1, kmax=4).run(reqs, realtime=False), key=lambda r: r.index)[1]
+    p = w.build_problem(d, shape)
+    psi0 = w.design_field(p, 100)
+    psi1 = w.perturbed_designs(p, psi0, 1, amplitude=0.02, first_seed=w.seed_for("walk100", 2))[:, 0]
+    psix = w.perturbed_designs(p, psi1, 1, amplitude=0.05, first_seed=w.seed_for("walk100", 3))[:, 0]
+    U = np.stack([fem.solve(p, hatfilter.filter_fwd(p, q))[:, 0] for q in (psi0, psi1)], 1)
+    Phi = rom.basis(U)
+    s, theta, Jk, J, fallback = _oracle_step(p, psi1, psix, Phi)
+    assert res.k == Phi.shape[1] == 2
+    assert res.step == s and res.used_hdm == fallback
+    assert res.theta == pytest.approx(theta, rel=1e-6)
+    assert res.Jk == pytest.approx(Jk, rel=1e-7)
+    assert res.J == pytest.approx(J, rel=1e-7)
