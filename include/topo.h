@@ -81,7 +81,8 @@ typedef enum {
   TOPO_PARAM_MAX_OUTER = 1,    /* max FP64 refinement steps (default 30) */
   TOPO_PARAM_WAIT_CYCLES = 2,  /* spin limit of device-side waits, in SM clock cycles (default 2e9) */
   TOPO_PARAM_ROM_REFINE = 3,   /* max FP64 refinement steps of the reduced solve (default 8) */
-  TOPO_PARAM_TILE_X = 4,       /* apply tile width in nodes (autotuner hint; 0 = default) */
+  TOPO_PARAM_TILE_X = 4,       /* columns per CTA of the 2D node-centric block apply (the
+                                  autotuned split of a K(rho) V launch; 0 = default) */
   TOPO_PARAM_PCG_BLOCKS_PER_SM = 5, /* CTAs per SM of the persistent PCG (0 = occupancy) */
   TOPO_PARAM_INNER_CAP = 6,        /* max FP32 inner iterations per refinement step (default 2000) */
   TOPO_PARAM_HDM_KERNEL = 7,       /* FP64 solve: 0 = K(rho) assembled once per solve as a per-node

@@ -53,6 +53,156 @@ __global__ void __launch_bounds__(TileShape<DIM>::NT) apply_kernel(const __grid_
   }
 }
 
+// ---------------------------------------------------------------------------------------
+// Node-centric 2D apply for blocks of columns. A CTA owns a 32 x 8 node tile, one node per
+// thread. Each thread forms its node's 3 x 3-block stencil row (36 coefficients, kept in
+// registers) once from the moduli of the 4 elements around it, with the Dirichlet convention
+// folded in (a fixed row is the identity, a fixed neighbour column zero). The columns are
+// then processed in batches of AB: the tile's 34 x 10 halo box of every column of a batch is
+// copied into shared memory with asynchronous copies (zero-filled outside the grid), two
+// batches ahead of the one being computed (a ring of NBUF = 3 buffers); per node and column
+// that is 9 shared loads, 36 FMAs and one vector store. Half the flops of the element form, V read from DRAM
+// about once, and the copies of a whole batch in flight at once.
+// Needs an even leading dimension and V, Y aligned to a (x, y) pair.
+// ---------------------------------------------------------------------------------------
+template <typename T> struct Vec2;
+template <> struct Vec2<float> { using type = float2; };
+template <> struct Vec2<double> { using type = double2; };
+
+template <int BYTES>
+__device__ __forceinline__ void cp_async_zfill(void* dst, const void* src, bool valid) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  const int n = valid ? BYTES : 0;  // 0: the BYTES destination bytes are zero-filled
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;" ::"r"(d), "l"(src), "n"(BYTES), "r"(n) : "memory");
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) apply2_kernel(const __grid_constant__ ApplyArgs<2, T> a) {
+  using V2 = typename Vec2<T>::type;
+  constexpr int AB = 32 / (int)sizeof(T);  // columns per batch: 8 (FP32) or 4 (FP64)
+  constexpr int HX = 34, HB = 340;         // halo box: 34 x 10 nodes
+  constexpr int NBUF = 3;
+  extern __shared__ __align__(16) unsigned char apply2_smem[];
+  V2 (*sv)[AB][HB] = reinterpret_cast<V2 (*)[AB][HB]>(apply2_smem);  // [NBUF][AB][HB]
+  if (a.gate && *a.gate == 0) return;
+  const Grid& g = a.g;
+  const int tiles_x = (g.nnx + 31) / 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const int i0 = (int)(blockIdx.x % tiles_x) * 32, j0 = (int)(blockIdx.x / tiles_x) * 8;
+  const int i = i0 + tx, j = j0 + ty;
+  const bool own = i < g.nnx && j < g.nny;
+  const long long n = own ? i + (long long)g.nnx * j : 0;
+  T C[9][4];
+  {
+    const T E0 = (T)g.E0, Emin = (T)g.Emin, es = a.escale;
+    // moduli of the elements around the node: q = qa + 2 qb is element (i - 1 + qa, j - 1 + qb)
+    T E[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int ei = i - 1 + (q & 1), ej = j - 1 + (q >> 1);
+      const bool in = own && ei >= 0 && ei < g.nx && ej >= 0 && ej < g.ny;
+      E[q] = in ? es * young<T>((T)a.rho[ei + (long long)g.nx * ej], E0, Emin, g.ipenal) : (T)0;
+    }
+    const bool rfix0 = own && is_fixed(g, 2 * n), rfix1 = own && is_fixed(g, 2 * n + 1);
+#pragma unroll
+    for (int nb = 0; nb < 9; ++nb) {
+      const int dx = nb % 3 - 1, dy = nb / 3 - 1;
+      T acc[4] = {(T)0, (T)0, (T)0, (T)0};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int qa = q & 1, qb = q >> 1;
+        const int cx = dx + 1 - qa, cy = dy + 1 - qb;
+        if (cx < 0 || cx > 1 || cy < 0 || cy > 1) continue;
+        const int L = lidx2(1 - qa, 1 - qb), M = lidx2(cx, cy);
+#pragma unroll
+        for (int r = 0; r < 2; ++r)
+#pragma unroll
+          for (int d = 0; d < 2; ++d)
+            acc[r * 2 + d] = fma(E[q], a.ke.k[(2 * L + r) * 8 + 2 * M + d], acc[r * 2 + d]);
+      }
+      const int ii = i + dx, jj = j + dy;
+      const bool nin = own && ii >= 0 && ii < g.nnx && jj >= 0 && jj < g.nny;
+      const long long m = nin ? ii + (long long)g.nnx * jj : 0;
+#pragma unroll
+      for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int d = 0; d < 2; ++d) {
+          T v = acc[r * 2 + d];
+          if (!nin || is_fixed(g, 2 * m + d)) v = (T)0;
+          if (r == 0 ? rfix0 : rfix1) v = (nb == 4 && r == d) ? (T)1 : (T)0;
+          C[nb][r * 2 + d] = v;
+        }
+    }
+  }
+  const int c0 = blockIdx.y * a.cols_per_cta;
+  const int c1 = min(a.m, c0 + a.cols_per_cta);
+  const int nbatch = c1 > c0 ? (c1 - c0 + AB - 1) / AB : 0;
+  // copies: warp w moves halo rows (column, row) = w, w + 8, ... of a batch, lane = x offset
+  // (lanes 0 and 1 also take the last two nodes of the 34-node row)
+  const int lane = tx, warp = ty;
+  const int gi0 = i0 - 1 + lane, gi1 = i0 + 31 + lane;
+  const bool xin0 = gi0 >= 0 && gi0 < g.nnx, xin1 = lane < 2 && gi1 < g.nnx;
+  const long long pitch = a.ld / 2;  // column stride in (x, y) pairs
+  const V2* V2base = reinterpret_cast<const V2*>(a.V);
+  auto issue = [&](int b, int buf) {
+    const int cb = c0 + b * AB;
+    V2* dst = &sv[buf][0][0];
+    for (int pr = warp; pr < AB * 10; pr += 8) {
+      const int col = pr / 10, hy = pr - col * 10;
+      const int gj = j0 - 1 + hy;
+      const bool yin = cb + col < c1 && gj >= 0 && gj < g.nny;
+      const V2* row = V2base + (long long)(cb + col) * pitch + (long long)g.nnx * gj;
+      V2* d = dst + col * HB + hy * HX;
+      cp_async_zfill<sizeof(V2)>(d + lane, (yin && xin0) ? row + gi0 : V2base, yin && xin0);
+      if (lane < 2) cp_async_zfill<sizeof(V2)>(d + 32 + lane, (yin && xin1) ? row + gi1 : V2base, yin && xin1);
+    }
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  V2* ybase = reinterpret_cast<V2*>(a.Y) + n;
+  if (nbatch > 0) issue(0, 0);
+  if (nbatch > 1) issue(1, 1);
+  int buf = 0;
+  for (int b = 0; b < nbatch; ++b) {
+    if (b + 2 < nbatch) {
+      issue(b + 2, buf == 0 ? 2 : buf - 1);  // the buffer after the next one
+      asm volatile("cp.async.wait_group 2;" ::: "memory");  // batch b has landed
+    } else if (b + 1 < nbatch) {
+      asm volatile("cp.async.wait_group 1;" ::: "memory");
+    } else {
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
+    }
+    __syncthreads();
+    const int cb = c0 + b * AB;
+    if (own) {
+      const V2* sb = &sv[buf][0][ty * HX + tx];  // the node's 3 x 3 neighbourhood starts here
+#pragma unroll
+      for (int col = 0; col < AB; ++col) {
+        if (cb + col >= c1) break;
+        T y0 = (T)0, y1 = (T)0;
+#pragma unroll
+        for (int nb = 0; nb < 9; ++nb) {
+          const V2 t = sb[col * HB + (nb / 3) * HX + (nb % 3)];
+          y0 = fma(C[nb][0], t.x, y0);
+          y0 = fma(C[nb][1], t.y, y0);
+          y1 = fma(C[nb][2], t.x, y1);
+          y1 = fma(C[nb][3], t.y, y1);
+        }
+        V2 o;
+        o.x = y0;
+        o.y = y1;
+        ybase[(long long)(cb + col) * pitch] = o;
+      }
+    }
+    __syncthreads();  // the buffer of batch b is refilled by batch b + 3
+    buf = buf == 2 ? 0 : buf + 1;
+  }
+}
+
+template <typename T>
+constexpr size_t apply2_smem_bytes() {
+  return 3 * (32 / sizeof(T)) * 340 * 2 * sizeof(T);
+}
+
 template <int DIM, typename T>
 static topo_status apply_impl(topo_ctx* c, const double* rho, const T* V, T* Y, int m, int ld,
                               const typename KeOf<DIM, T>::type& ke, double escale, const int* gate) {
@@ -66,7 +216,9 @@ static topo_status apply_impl(topo_ctx* c, const double* rho, const T* V, T* Y, 
   a.Y = Y;
   a.ld = ld;
   a.m = m;
-  long long tiles = num_tiles<DIM>(c->g);
+  const bool pairs = DIM == 2 && (ld % 2 == 0) && ((uintptr_t)V % (2 * sizeof(T)) == 0) &&
+                     ((uintptr_t)Y % (2 * sizeof(T)) == 0);
+  long long tiles = pairs ? (long long)((c->g.nnx + 31) / 32) * ((c->g.nny + 7) / 8) : num_tiles<DIM>(c->g);
   // enough CTAs to fill the GPU several times over, each reusing its staged E for a run
   // of columns
   long long want_ctas = 8LL * c->num_sms;
@@ -75,8 +227,21 @@ static topo_status apply_impl(topo_ctx* c, const double* rho, const T* V, T* Y, 
   if (groups < 1) groups = 1;
   if (groups > 65535) groups = 65535;
   a.cols_per_cta = (int)((m + groups - 1) / groups);
+  // node-centric kernel: 32 columns per CTA amortise the coefficient set-up best at
+  // 600x200, m = 64 (measured against 16, 22, 64); TOPO_PARAM_TILE_X overrides
+  if (pairs) a.cols_per_cta = std::min(m, c->apply_cols > 0 ? c->apply_cols : 32);
   groups = (m + a.cols_per_cta - 1) / a.cols_per_cta;
   dim3 grid((unsigned)tiles, (unsigned)groups);
+  if constexpr (DIM == 2) {
+    if (pairs) {
+      const size_t sm = apply2_smem_bytes<T>();
+      TOPO_CUDA_TRY(c, cudaFuncSetAttribute(apply2_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+      apply2_kernel<T><<<grid, 256, sm, c->stream>>>(a);
+      note_launch();
+      TOPO_CUDA_TRY(c, cudaGetLastError());
+      return TOPO_OK;
+    }
+  }
   apply_kernel<DIM, T><<<grid, TileShape<DIM>::NT, 0, c->stream>>>(a);
   note_launch();
   TOPO_CUDA_TRY(c, cudaGetLastError());

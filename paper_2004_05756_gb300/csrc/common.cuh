@@ -562,6 +562,7 @@ struct topo_ctx {
   int hdm_kernel;  // 0: assembled-stencil Chronopoulos-Gear PCG (FP64); 1: element-form PCG
   int pcg_max_ctas;  // cap on the CTAs of one persistent solve (0 = none)
   int rom_tensor;    // FP32 projection contraction: 1 tensor cores (tcgen05), 0 SIMT FP32
+  int apply_cols;    // columns per CTA of the 2D node-centric apply (0 = default split)
   char err[512];
 };
 

@@ -498,7 +498,9 @@ extern "C" topo_status topo_set_param(topo_ctx* c, topo_param which, double v) {
       c->rom_refine = (int)v;
       return TOPO_OK;
     case TOPO_PARAM_TILE_X:
-      return TOPO_OK;  // fixed tile shapes in this build; accepted for API stability
+      if (!(v >= 0 && v <= 1e6)) return fail(c, TOPO_ERR_INVALID, "apply columns per CTA must be in [0,1e6]");
+      c->apply_cols = (int)v;
+      return TOPO_OK;
     case TOPO_PARAM_INNER_CAP:
       if (!(v >= 1 && v <= 1e7)) return fail(c, TOPO_ERR_INVALID, "inner cap must be in [1,1e7]");
       c->inner_cap = (int)v;

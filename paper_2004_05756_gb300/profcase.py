@@ -34,6 +34,7 @@ def main(argv=None):
     ap.add_argument("--hdm-kernel", type=int, default=0, help="FP64 solve: 0 stencil C-G PCG, 1 element-form PCG")
     ap.add_argument("--blocks-per-sm", type=int, default=0, help="CTAs per SM of the persistent solve (0 = default)")
     ap.add_argument("--rom-tensor", type=int, default=1, help="FP32 projection contraction: 1 tcgen05, 0 SIMT")
+    ap.add_argument("--apply-cols", type=int, default=0, help="columns per CTA of the 2D block apply (0 = default)")
     a = ap.parse_args(argv)
     import torch
 
@@ -47,6 +48,7 @@ def main(argv=None):
     T.topo_set_param(native.TOPO_PARAM_HDM_KERNEL, a.hdm_kernel)
     T.topo_set_param(native.TOPO_PARAM_PCG_BLOCKS_PER_SM, a.blocks_per_sm)
     T.topo_set_param(native.TOPO_PARAM_ROM_TENSOR, a.rom_tensor)
+    T.topo_set_param(native.TOPO_PARAM_TILE_X, a.apply_cols)
     f64 = dict(dtype=torch.float64, device="cuda")
     psi = torch.as_tensor(w.design_field(p, 0)).to(**f64)
     rho = torch.empty(p.nel, **f64)
@@ -103,7 +105,7 @@ def main(argv=None):
     e1.record()
     e1.synchronize()
     print(f"{a.call} {a.prec} shape={a.shape} m={a.m} k={k} hdm_kernel={a.hdm_kernel} bps={a.blocks_per_sm} "
-          f"rom_tensor={a.rom_tensor}: "
+          f"rom_tensor={a.rom_tensor} apply_cols={a.apply_cols}: "
           f"{e0.elapsed_time(e1) / a.reps * 1e3:.1f} us/call")
     T.topo_check()
 
