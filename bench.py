@@ -355,6 +355,28 @@ def run_ours(args, rank, world):
         # FP64 PCG iterations and J at the first timed centre, for the DESIGN/roofline notes
         J_centre = J.item()
 
+        # K(rho) V for a block of m = 64 columns (the spec operator at its roofline size):
+        # FP32 (HBM-bound) and FP64 (ALU-bound), timed with CUDA events, L2 flushed before each
+        apply_rf = None
+        if p.dim == 2:
+            ma = 64
+            apply_rf = {}
+            for pr, dt in (("fp32", torch.float32), ("fp64", torch.float64)):
+                Va = torch.randn((ma, N), dtype=dt, device=dev)
+                Ya = torch.empty_like(Va)
+                T.topo_apply_K(rho, Va, Ya, pr)  # warm-up
+                ts = []
+                for _ in range(5):
+                    flush.zero_()
+                    a0, a1 = ev(), ev()
+                    a0.record(stream)
+                    T.topo_apply_K(rho, Va, Ya, pr)
+                    a1.record(stream)
+                    a1.synchronize()
+                    ts.append(a0.elapsed_time(a1))
+                apply_rf[pr] = statistics.median(ts)
+                del Va, Ya
+
     K = args.steps
     step_ms = statistics.fmean(stats["step"])
     t_local = sum(stats["step"]) / 1e3
@@ -423,6 +445,17 @@ def run_ours(args, rank, world):
                      "peak_source": peak_source,
                      "flop_per_dof_iter": flop_dof, "hbm_peak_gbs": hbm_peak},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "apply_roofline": None if apply_rf is None else {
+            "call": "topo_apply_K, m = 64 columns (node-centric 2D block apply)",
+            "fp32": {"bound": "hbm", "ms": apply_rf["fp32"], "unit": "GB/s",
+                     "achieved": (2 * 64 * N * 4 + p.nel * 8) / (apply_rf["fp32"] * 1e-3) / 1e9,
+                     "peak": hbm_peak, "frac": (2 * 64 * N * 4 + p.nel * 8) / (apply_rf["fp32"] * 1e-3) / 1e9 / hbm_peak,
+                     "bytes": 2 * 64 * N * 4 + p.nel * 8,
+                     "bytes_def": "read V + write Y (FP32) + read rho, once each"},
+            "fp64": {"bound": "alu", "ms": apply_rf["fp64"], "unit": "TFLOP/s",
+                     "achieved": 36.0 * 64 * N / (apply_rf["fp64"] * 1e-3) / 1e12,
+                     "peak": fp64_peak, "frac": 36.0 * 64 * N / (apply_rf["fp64"] * 1e-3) / 1e12 / fp64_peak,
+                     "flop_def": "36 flop per DOF and column (18 FMA: 3x3 blocks of 2x2 per node row)"}},
         "gpu_launches": launches, "clocks": clocks, "wall_s_timed": t_wall,
     }
     return out, p, psi0
