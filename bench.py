@@ -369,7 +369,7 @@ def run_ours(args, rank, world):
         # FP64 PCG iterations and J at the first timed centre, for the DESIGN/roofline notes
         J_centre = J.item()
 
-        # K(rho) V for a block of m = 64 columns (the spec operator at its roofline size):
+        # K(rho) V for a block of m = 64 columns (the method's central operator at its roofline size):
         # FP32 (HBM-bound) and FP64 (ALU-bound), timed with CUDA events, L2 flushed before each
         apply_rf = None
         if p.dim == 2:
@@ -412,7 +412,7 @@ def run_ours(args, rank, world):
     iters = statistics.fmean(stats["iters"])
     outer = statistics.fmean(stats["outer"])
     # FP64 peak derived from unit counts and clocks: 152 SMs x 2 FP64 FMA/clk (4 flop) x 2.07 GHz
-    # (NVIDIA's nominal FP64 rate is 1.25 TFLOP/s; this build's own FMA microbenchmark measured 1.19).
+    # (NVIDIA's nominal FP64 rate is 1.25 TFLOP/s; an FMA microbenchmark on GB300 measured 1.19).
     fp64_peak = 152 * 4 * 2.07e9 / 1e12
     # FP32: 152 SMs x 128 FMA/clk (256 flop) x 2.07 GHz
     fp32_peak = 152 * 256 * 2.07e9 / 1e12

@@ -136,7 +136,7 @@ __device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(__flo
 
 // s + c += v, compensated (Knuth's TwoSum): s carries the rounded sum, c the accumulated
 // rounding errors, so the pair holds the running sum to about 2^-48 relative. FP32 only:
-// FP64 runs at 1/64 of the FP32 rate on this part.
+// FP64 runs at 1/64 of the FP32 rate on GB300.
 __device__ __forceinline__ void two_sum_add(float& s, float& c, float v) {
   const float t = __fadd_rn(s, v);
   const float bp = __fsub_rn(t, s);

@@ -263,7 +263,7 @@ extern "C" topo_status topo_batch_create(const topo_problem* probs, int count, v
   if (!probs || count < 1) return TOPO_ERR_INVALID;
   for (int i = 1; i < count; ++i)
     if (probs[i].dim != probs[0].dim) return TOPO_ERR_INVALID;
-  if (probs[0].dim != 2) return TOPO_ERR_INVALID;  // batched solves: 2D Q4 in this build
+  if (probs[0].dim != 2) return TOPO_ERR_INVALID;  // batched solves are 2D Q4 only
   topo_batch* b = new topo_batch();
   b->count = count;
   b->stream = (cudaStream_t)cuda_stream;

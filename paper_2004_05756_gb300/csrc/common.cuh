@@ -335,7 +335,7 @@ __device__ inline double block_sum(double v, double* red) {
 // Three block sums at once (result in thread 0; blockDim.x <= 512, a multiple of 32; red holds
 // 3 * 32 doubles). Within a warp the values are reduced by a butterfly that halves the number
 // of values each lane carries at the first two levels, so the warp spends 6 FP64 additions on
-// all three sums instead of 15 (FP64 issue is scarce on this part); the order is fixed, so
+// all three sums instead of 15 (FP64 issue is scarce on GB300); the order is fixed, so
 // the result is deterministic.
 __device__ inline void block_sum3(double& a, double& b, double& c, double* red) {
   const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
