@@ -86,6 +86,10 @@ struct Ctl {
   long long limit;      // cycles per wait
 };
 
+// Teardown waits (copies and MMAs already in flight) get a fixed generous bound, independent
+// of the caller's wait limit: the CTA must not leave while its copies can still land.
+constexpr long long kTeardownCycles = 4000000000LL;
+
 // Wait for the phase of `bar` with the given parity to complete. Gives up (false) when another
 // wait of the CTA already expired (honour_abort) or after ctl.limit cycles, recording the
 // timeout.
@@ -214,8 +218,9 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         ++issued;
       }
       // copies in flight land before the CTA may leave
+      const Ctl td{abort_flag, status, kTeardownCycles};
       for (int ci = max(0, issued - STAGES); ci < issued; ++ci)
-        wait_bar(su32(&full[ci % STAGES]), (ci / STAGES) & 1, ctl, false);
+        wait_bar(su32(&full[ci % STAGES]), (ci / STAGES) & 1, td, false);
     }
   } else if (warp == 1) {
     // ---- MMA issuer ----
@@ -245,7 +250,8 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       }
       // every MMA issued by this thread completes before TMEM is released
       tc_commit(su32(done));
-      wait_bar(su32(done), 0, ctl, false);
+      const Ctl td{abort_flag, status, kTeardownCycles};
+      wait_bar(su32(done), 0, td, false);
     }
   } else if (warp < 6) {
     // ---- split: x -> hi (in place) + lo (8 KB above) ----

@@ -436,3 +436,34 @@ def test_solve_accepts_rounding_floor_on_void_loads():
         r[fem.fixed_dofs(p)] = 0
         Jo = fem.compliance(p, Uo[:, c], p.F[:, c])
         assert abs(fem.compliance(p, Ug[:, c], p.F[:, c]) - Jo) <= 2 * np.linalg.norm(Uo[:, c]) * np.linalg.norm(r)
+
+
+def test_barrier_timeout_reports_and_context_survives(torch):
+    """Failure detection without a fault: with a device wait limit of 1,000 SM cycles a grid
+    barrier of the persistent solve gives up; every CTA leaves, the host reads
+    TOPO_ERR_TIMEOUT, and the same context then solves normally with the default limit."""
+    from paper_2004_05756_gb300.native import TOPO_PARAM_WAIT_CYCLES, TopoError
+    p = w.mbb_2d(600, 200)
+    T = ctx_for(p)
+    psi, rho = _design(p)
+    F = cols(p.F)
+    status = None
+    T.topo_set_param(TOPO_PARAM_WAIT_CYCLES, 1e3)
+    for _ in range(3):  # arrival skew over 152 SMs exceeds 1,000 cycles; retry if not
+        U = torch.zeros_like(F)
+        try:
+            T.topo_solve_hdm(dev(rho), F, U, rtol=1e-8, maxit=100000)
+            T.topo_check()
+        except TopoError as e:
+            status = e.status
+            break
+    assert status == 5, status  # TOPO_ERR_TIMEOUT
+    T.topo_check()  # the sticky status was cleared
+    T.topo_set_param(TOPO_PARAM_WAIT_CYCLES, 2e9)
+    U = torch.zeros_like(F)
+    info = T.topo_solve_hdm(dev(rho), F, U, rtol=1e-8, maxit=100000)
+    T.topo_check()
+    assert info["status"] == 0 and info["relres"] <= 1e-8
+    Jg = float((F * U).sum().item())
+    Jo = fem.compliance(p, fem.solve(p, rho))
+    assert abs(Jg - Jo) <= 1e-6 * abs(Jo)
