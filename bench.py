@@ -375,9 +375,13 @@ def run_ours(args, rank, world):
         if p.dim == 2:
             ma = 64
             apply_rf = {}
-            for pr, dt in (("fp32", torch.float32), ("fp64", torch.float64)):
-                Va = torch.randn((ma, N), dtype=dt, device=dev)
-                Ya = torch.empty_like(Va)
+            # FP32 with a 16-byte column pitch (the TMA-staged form), FP32 with the contiguous
+            # pitch N (N % 4 == 2 here: the cp.async-staged form) and FP64
+            for key, pr, dt, pad in (("fp32", "fp32", torch.float32, 4), ("fp32_cpasync", "fp32", torch.float32, 1),
+                                     ("fp64", "fp64", torch.float64, 1)):
+                ldp = -(-N // pad) * pad
+                Va = torch.randn((ma, ldp), dtype=dt, device=dev)[:, :N]
+                Ya = torch.empty((ma, ldp), dtype=dt, device=dev)[:, :N]
                 T.topo_apply_K(rho, Va, Ya, pr)  # warm-up
                 ts = []
                 for _ in range(5):
@@ -388,7 +392,7 @@ def run_ours(args, rank, world):
                     a1.record(stream)
                     a1.synchronize()
                     ts.append(a0.elapsed_time(a1))
-                apply_rf[pr] = statistics.median(ts)
+                apply_rf[key] = statistics.median(ts)
                 del Va, Ya
 
     K = args.steps
@@ -464,8 +468,14 @@ def run_ours(args, rank, world):
             "fp32": {"bound": "hbm", "ms": apply_rf["fp32"], "unit": "GB/s",
                      "achieved": (2 * 64 * N * 4 + p.nel * 8) / (apply_rf["fp32"] * 1e-3) / 1e9,
                      "peak": hbm_peak, "frac": (2 * 64 * N * 4 + p.nel * 8) / (apply_rf["fp32"] * 1e-3) / 1e9 / hbm_peak,
-                     "bytes": 2 * 64 * N * 4 + p.nel * 8,
+                     "bytes": 2 * 64 * N * 4 + p.nel * 8, "ld": -(-N // 4) * 4,
+                     "staging": "TMA halo-row boxes, persistent grid",
                      "bytes_def": "read V + write Y (FP32) + read rho, once each"},
+            "fp32_cpasync": {"bound": "hbm", "ms": apply_rf["fp32_cpasync"], "unit": "GB/s",
+                             "achieved": (2 * 64 * N * 4 + p.nel * 8) / (apply_rf["fp32_cpasync"] * 1e-3) / 1e9,
+                             "peak": hbm_peak,
+                             "frac": (2 * 64 * N * 4 + p.nel * 8) / (apply_rf["fp32_cpasync"] * 1e-3) / 1e9 / hbm_peak,
+                             "ld": N, "staging": "per-thread cp.async (leading dimension not a multiple of 4)"},
             "fp64": {"bound": "alu", "ms": apply_rf["fp64"], "unit": "TFLOP/s",
                      "achieved": 36.0 * 64 * N / (apply_rf["fp64"] * 1e-3) / 1e12,
                      "peak": fp64_peak, "frac": 36.0 * 64 * N / (apply_rf["fp64"] * 1e-3) / 1e12 / fp64_peak,

@@ -90,10 +90,15 @@ typedef enum {
   TOPO_PARAM_PCG_MAX_CTAS = 8,     /* cap on the CTAs of one persistent FP64 solve (0 = whole GPU);
                                       lets solves of several contexts share the GPU concurrently and
                                       fixes their reduction order independently of load */
-  TOPO_PARAM_ROM_TENSOR = 9        /* contraction Phi^T W of the FP32 projection forms of
+  TOPO_PARAM_ROM_TENSOR = 9,       /* contraction Phi^T W of the FP32 projection forms of
                                       topo_rom_solve: 1 = tensor cores (tcgen05 kind::tf32 on an exact
                                       hi/lo split of each FP32 operand, FP32 accumulate per 256 rows,
                                       FP64 beyond; default), 0 = SIMT FP32 */
+  TOPO_PARAM_APPLY_STAGES = 10     /* 2D FP32 block apply with ld % 4 == 0 and V 16-byte aligned:
+                                      2, 3 (default) or 4 = halo rows staged by TMA (one box per
+                                      halo row and 8 columns) with that many tile-column units in
+                                      flight per CTA of a persistent grid; 0 = per-thread cp.async
+                                      staging (the form used for other leading dimensions) */
 } topo_param;
 
 /* Create a context for one problem; computes K_e (2x2(x2) Gauss quadrature), the filter

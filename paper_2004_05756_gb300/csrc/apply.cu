@@ -4,7 +4,11 @@
 // One CTA per node tile; the element moduli of the tile are staged once and reused for
 // every column the CTA processes; each column's halo'd node box is staged in shared memory
 // with coalesced loads (Dirichlet DOFs zeroed), then every thread forms its node's rows.
+#include <algorithm>
+#include <type_traits>
+
 #include "common.cuh"
+#include "tma.cuh"
 
 namespace topo {
 
@@ -69,11 +73,71 @@ template <typename T> struct Vec2;
 template <> struct Vec2<float> { using type = float2; };
 template <> struct Vec2<double> { using type = double2; };
 
+// acc += c * v componentwise, each component one fused multiply-add rounded to nearest: one
+// packed FP32x2 instruction on sm_100 and later, two FP64 FMAs for double.
+__device__ __forceinline__ void fma_pair(float2 c, float2 v, float2& acc) { acc = __ffma2_rn(c, v, acc); }
+__device__ __forceinline__ void fma_pair(double2 c, double2 v, double2& acc) {
+  acc.x = fma(c.x, v.x, acc.x);
+  acc.y = fma(c.y, v.y, acc.y);
+}
+
 template <int BYTES>
 __device__ __forceinline__ void cp_async_zfill(void* dst, const void* src, bool valid) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
   const int n = valid ? BYTES : 0;  // 0: the BYTES destination bytes are zero-filled
   asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;" ::"r"(d), "l"(src), "n"(BYTES), "r"(n) : "memory");
+}
+
+// Stencil row of node (i, j) of a 2D Q4 grid: C[nb][2 r + d] couples DOF r of the node with
+// DOF d of neighbour nb = (dx + 1) + 3 (dy + 1), summed over the up to four elements around
+// the node with their SIMP moduli; Dirichlet rows are the identity, Dirichlet columns and
+// neighbours outside the grid zero. Returns the 9-bit mask of neighbours outside the grid.
+template <typename T>
+__device__ __forceinline__ unsigned node_stencil_q4(const ApplyArgs<2, T>& a, int i, int j, bool own, long long n,
+                                                    T (&C)[9][4]) {
+  const Grid& g = a.g;
+  unsigned outside = 0;
+  const T E0 = (T)g.E0, Emin = (T)g.Emin, es = a.escale;
+  // moduli of the elements around the node: q = qa + 2 qb is element (i - 1 + qa, j - 1 + qb)
+  T E[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int ei = i - 1 + (q & 1), ej = j - 1 + (q >> 1);
+    const bool in = own && ei >= 0 && ei < g.nx && ej >= 0 && ej < g.ny;
+    E[q] = in ? es * young<T>((T)a.rho[ei + (long long)g.nx * ej], E0, Emin, g.ipenal) : (T)0;
+  }
+  const bool rfix0 = own && is_fixed(g, 2 * n), rfix1 = own && is_fixed(g, 2 * n + 1);
+#pragma unroll
+  for (int nb = 0; nb < 9; ++nb) {
+    const int dx = nb % 3 - 1, dy = nb / 3 - 1;
+    T acc[4] = {(T)0, (T)0, (T)0, (T)0};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int qa = q & 1, qb = q >> 1;
+      const int cx = dx + 1 - qa, cy = dy + 1 - qb;
+      if (cx < 0 || cx > 1 || cy < 0 || cy > 1) continue;
+      const int L = lidx2(1 - qa, 1 - qb), M = lidx2(cx, cy);
+#pragma unroll
+      for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int d = 0; d < 2; ++d)
+          acc[r * 2 + d] = fma(E[q], a.ke.k[(2 * L + r) * 8 + 2 * M + d], acc[r * 2 + d]);
+    }
+    const int ii = i + dx, jj = j + dy;
+    const bool nin = own && ii >= 0 && ii < g.nnx && jj >= 0 && jj < g.nny;
+    if (own && !nin) outside |= 1u << nb;
+    const long long m = nin ? ii + (long long)g.nnx * jj : 0;
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+      for (int d = 0; d < 2; ++d) {
+        T v = acc[r * 2 + d];
+        if (!nin || is_fixed(g, 2 * m + d)) v = (T)0;
+        if (r == 0 ? rfix0 : rfix1) v = (nb == 4 && r == d) ? (T)1 : (T)0;
+        C[nb][r * 2 + d] = v;
+      }
+  }
+  return outside;
 }
 
 template <typename T>
@@ -92,46 +156,16 @@ __global__ void __launch_bounds__(256) apply2_kernel(const __grid_constant__ App
   const int i = i0 + tx, j = j0 + ty;
   const bool own = i < g.nnx && j < g.nny;
   const long long n = own ? i + (long long)g.nnx * j : 0;
-  T C[9][4];
+  V2 Cp[9][2];  // (C[nb][0], C[nb][1]) and (C[nb][2], C[nb][3]): the x and y parts of both rows
   {
-    const T E0 = (T)g.E0, Emin = (T)g.Emin, es = a.escale;
-    // moduli of the elements around the node: q = qa + 2 qb is element (i - 1 + qa, j - 1 + qb)
-    T E[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int ei = i - 1 + (q & 1), ej = j - 1 + (q >> 1);
-      const bool in = own && ei >= 0 && ei < g.nx && ej >= 0 && ej < g.ny;
-      E[q] = in ? es * young<T>((T)a.rho[ei + (long long)g.nx * ej], E0, Emin, g.ipenal) : (T)0;
-    }
-    const bool rfix0 = own && is_fixed(g, 2 * n), rfix1 = own && is_fixed(g, 2 * n + 1);
+    T C[9][4];
+    node_stencil_q4(a, i, j, own, n, C);
 #pragma unroll
     for (int nb = 0; nb < 9; ++nb) {
-      const int dx = nb % 3 - 1, dy = nb / 3 - 1;
-      T acc[4] = {(T)0, (T)0, (T)0, (T)0};
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int qa = q & 1, qb = q >> 1;
-        const int cx = dx + 1 - qa, cy = dy + 1 - qb;
-        if (cx < 0 || cx > 1 || cy < 0 || cy > 1) continue;
-        const int L = lidx2(1 - qa, 1 - qb), M = lidx2(cx, cy);
-#pragma unroll
-        for (int r = 0; r < 2; ++r)
-#pragma unroll
-          for (int d = 0; d < 2; ++d)
-            acc[r * 2 + d] = fma(E[q], a.ke.k[(2 * L + r) * 8 + 2 * M + d], acc[r * 2 + d]);
-      }
-      const int ii = i + dx, jj = j + dy;
-      const bool nin = own && ii >= 0 && ii < g.nnx && jj >= 0 && jj < g.nny;
-      const long long m = nin ? ii + (long long)g.nnx * jj : 0;
-#pragma unroll
-      for (int r = 0; r < 2; ++r)
-#pragma unroll
-        for (int d = 0; d < 2; ++d) {
-          T v = acc[r * 2 + d];
-          if (!nin || is_fixed(g, 2 * m + d)) v = (T)0;
-          if (r == 0 ? rfix0 : rfix1) v = (nb == 4 && r == d) ? (T)1 : (T)0;
-          C[nb][r * 2 + d] = v;
-        }
+      Cp[nb][0].x = C[nb][0];
+      Cp[nb][0].y = C[nb][1];
+      Cp[nb][1].x = C[nb][2];
+      Cp[nb][1].y = C[nb][3];
     }
   }
   const int c0 = blockIdx.y * a.cols_per_cta;
@@ -164,7 +198,7 @@ __global__ void __launch_bounds__(256) apply2_kernel(const __grid_constant__ App
   int buf = 0;
   for (int b = 0; b < nbatch; ++b) {
     if (b + 2 < nbatch) {
-      issue(b + 2, buf == 0 ? 2 : buf - 1);  // the buffer after the next one
+      issue(b + 2, buf == 0 ? NBUF - 1 : buf - 1);  // the buffer after the next one
       asm volatile("cp.async.wait_group 2;" ::: "memory");  // batch b has landed
     } else if (b + 1 < nbatch) {
       asm volatile("cp.async.wait_group 1;" ::: "memory");
@@ -178,29 +212,227 @@ __global__ void __launch_bounds__(256) apply2_kernel(const __grid_constant__ App
 #pragma unroll
       for (int col = 0; col < AB; ++col) {
         if (cb + col >= c1) break;
-        T y0 = (T)0, y1 = (T)0;
-#pragma unroll
-        for (int nb = 0; nb < 9; ++nb) {
-          const V2 t = sb[col * HB + (nb / 3) * HX + (nb % 3)];
-          y0 = fma(C[nb][0], t.x, y0);
-          y0 = fma(C[nb][1], t.y, y0);
-          y1 = fma(C[nb][2], t.x, y1);
-          y1 = fma(C[nb][3], t.y, y1);
-        }
         V2 o;
-        o.x = y0;
-        o.y = y1;
+        if constexpr (std::is_same<T, float>::value) {
+          // row r of the node: sum over neighbours of the x part C[nb][2r] t.x and, separately,
+          // of the y part C[nb][2r+1] t.y (one packed FMA each); the two partial sums are added
+          // at the end. The TMA-staged form uses the same order.
+          V2 p0, p1;
+          p0.x = p0.y = p1.x = p1.y = (T)0;
+#pragma unroll
+          for (int nb = 0; nb < 9; ++nb) {
+            const V2 t = sb[col * HB + (nb / 3) * HX + (nb % 3)];
+            fma_pair(Cp[nb][0], t, p0);
+            fma_pair(Cp[nb][1], t, p1);
+          }
+          o.x = p0.x + p0.y;
+          o.y = p1.x + p1.y;
+        } else {
+          // FP64 is bound by the FP64 pipe: one chain per row, no extra additions
+          T y0 = (T)0, y1 = (T)0;
+#pragma unroll
+          for (int nb = 0; nb < 9; ++nb) {
+            const V2 t = sb[col * HB + (nb / 3) * HX + (nb % 3)];
+            y0 = fma(Cp[nb][0].x, t.x, y0);
+            y0 = fma(Cp[nb][0].y, t.y, y0);
+            y1 = fma(Cp[nb][1].x, t.x, y1);
+            y1 = fma(Cp[nb][1].y, t.y, y1);
+          }
+          o.x = y0;
+          o.y = y1;
+        }
         ybase[(long long)(cb + col) * pitch] = o;
       }
     }
     __syncthreads();  // the buffer of batch b is refilled by batch b + 3
-    buf = buf == 2 ? 0 : buf + 1;
+    buf = buf == NBUF - 1 ? 0 : buf + 1;
   }
 }
 
 template <typename T>
 constexpr size_t apply2_smem_bytes() {
   return 3 * (32 / sizeof(T)) * 340 * 2 * sizeof(T);
+}
+
+// ---------------------------------------------------------------------------------------
+// 2D node-centric block apply in FP32 with the halo rows staged by TMA: the form for 16-byte
+// aligned column pitches (ld % 4 == 0, V 16-byte aligned). Same stencil rows and the same
+// products in the same order as apply2_kernel, so both forms give identical results.
+//
+// Work unit = one 32 x 8 node tile times one batch of AB = 8 columns, numbered tile-major.
+// A persistent grid (every resident CTA slot of the GPU) splits the units evenly, each CTA a
+// contiguous range, so there is no wave tail; a thread forms its node's stencil row again
+// only when its CTA's range enters the next tile. Per unit one thread issues ten TMA boxes, one per
+// halo row, of 72 floats (36 nodes from the even node at or before the row's first halo node,
+// so that x is 16-byte aligned) by AB columns, all completing on the unit's mbarrier; NBUF
+// units are in flight per CTA. Rows and columns outside V read as zero. Halo positions
+// outside the grid hold whatever lies beside them in V (the end of the previous or the start
+// of the next grid row): a thread zeroes each such slot that it reads before reading it, so a
+// non-finite value there never enters a product.
+// Every mbarrier wait is bounded by wait_cycles; on expiry the status becomes
+// TOPO_ERR_TIMEOUT, the CTA stops after the unit in hand and waits for its copies in flight.
+// ---------------------------------------------------------------------------------------
+namespace tmaapply {
+constexpr int AB = 8;                         // columns per unit
+constexpr int BOXN = 36;                      // nodes per halo row box
+constexpr int ROWS = 10;                      // halo rows of a 32 x 8 tile
+constexpr int BOX_BYTES = 2 * BOXN * AB * 4;  // 2304 = 18 x 128: every box 128-byte aligned
+constexpr int UNIT_BYTES = ROWS * BOX_BYTES;  // 23040
+constexpr size_t smem_bytes(int nbuf) { return 128 + (size_t)nbuf * UNIT_BYTES + 8 * (size_t)nbuf; }
+}  // namespace tmaapply
+
+// Resident CTAs per SM that each ring depth is built for: the shared memory of NBUF units
+// (23 KB each) and the registers fit 4, 3 and 2 CTAs for NBUF = 2, 3, 4.
+template <int NBUF>
+__global__ void __launch_bounds__(256, NBUF == 2 ? 4 : (NBUF == 3 ? 3 : 2))
+    apply2_tma_kernel(const __grid_constant__ CUtensorMap tmV, const __grid_constant__ ApplyArgs<2, float> a,
+                      long long units, int* status, long long wait_cycles) {
+  using namespace tmaapply;
+  extern __shared__ unsigned char apply2_tma_smem[];
+  unsigned char* base = apply2_tma_smem + ((128u - (su32(apply2_tma_smem) & 127u)) & 127u);
+  uint64_t* full = reinterpret_cast<uint64_t*>(base + NBUF * UNIT_BYTES);
+  __shared__ int abort_word;
+  if (a.gate && *a.gate == 0) return;
+  const Grid& g = a.g;
+  const int tiles_x = (g.nnx + 31) / 32;
+  const int nb = (a.m + AB - 1) / AB;  // units per tile
+  const long long u_begin = units * blockIdx.x / gridDim.x;
+  const int nunits = (int)(units * (blockIdx.x + 1) / gridDim.x - u_begin);
+  // unit q of this CTA -> its tile t and first column c0
+  auto unit_of = [&](int q, int& t, int& c0) {
+    const long long u = u_begin + q;
+    t = (int)(u / nb);
+    c0 = (int)(u - (long long)t * nb) * AB;
+  };
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const uint32_t buf0 = su32(base);
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < NBUF; ++s) mbar_init(su32(&full[s]), 1);
+    abort_word = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmV) : "memory");
+  }
+  __syncthreads();
+  auto issue = [&](int q) {  // thread 0: the ten halo-row boxes of the CTA's unit q
+    int t, c0;
+    unit_of(q, t, c0);
+    const int i0 = (t % tiles_x) * 32, j0 = (t / tiles_x) * 8;
+    const uint32_t bar = su32(&full[q % NBUF]);
+    const uint32_t dst = buf0 + (uint32_t)(q % NBUF) * UNIT_BYTES;
+    mbar_expect_tx(bar, UNIT_BYTES);
+#pragma unroll 1
+    for (int hy = 0; hy < ROWS; ++hy) {
+      const long long node = (long long)g.nnx * (j0 - 1 + hy) + (i0 - 1);
+      tma_load_2d(dst + hy * BOX_BYTES, &tmV, (int)(2 * (node - (node & 1))), c0, bar);
+    }
+  };
+  int issued = 0;
+  if (threadIdx.x == 0)
+    for (; issued < NBUF - 1 && issued < nunits; ++issued) issue(issued);
+  const Ctl ctl{&abort_word, status, wait_cycles};
+  const float2* __restrict__ sv = reinterpret_cast<const float2*>(base);
+  float2* __restrict__ svw = reinterpret_cast<float2*>(base);
+  float2* Y2 = reinterpret_cast<float2*>(a.Y);
+  const long long pitch = a.ld / 2;  // column stride in (x, y) pairs
+  int cur_tile = -1;
+  float2 Cp[9][2];
+  int off[3] = {0, 0, 0};  // float2 offset of halo rows ty .. ty + 2 at the node's column, in a unit
+  unsigned outside = 0;
+  bool own = false;
+  long long n = 0;
+  int q = 0;
+  bool failed = false;
+  for (; q < nunits; ++q) {
+    if (threadIdx.x == 0 && issued < nunits) issue(issued++);  // into the buffer unit q - 1 released
+    int t, c0;
+    unit_of(q, t, c0);
+    if (t != cur_tile) {
+      cur_tile = t;
+      const int i0 = (t % tiles_x) * 32, j0 = (t / tiles_x) * 8;
+      const int i = i0 + tx, j = j0 + ty;
+      own = i < g.nnx && j < g.nny;
+      n = own ? i + (long long)g.nnx * j : 0;
+      {
+        float C[9][4];
+        outside = node_stencil_q4(a, i, j, own, n, C);
+#pragma unroll
+        for (int nbr = 0; nbr < 9; ++nbr) {
+          Cp[nbr][0] = make_float2(C[nbr][0], C[nbr][1]);
+          Cp[nbr][1] = make_float2(C[nbr][2], C[nbr][3]);
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        const long long node = (long long)g.nnx * (j0 - 1 + ty + r) + (i0 - 1);
+        off[r] = (ty + r) * (BOXN * AB) + tx + (int)(node & 1);
+      }
+    }
+    const int s = q % NBUF;
+    if (!wait_bar(su32(&full[s]), (uint32_t)((q / NBUF) & 1), ctl, false)) failed = true;
+    if (!failed && own) {
+      const int sb = s * (UNIT_BYTES / 8);
+      if (outside) {
+#pragma unroll
+        for (int nbr = 0; nbr < 9; ++nbr)
+          if (outside & (1u << nbr))
+#pragma unroll
+            for (int col = 0; col < AB; ++col) svw[sb + off[nbr / 3] + col * BOXN + nbr % 3] = make_float2(0.f, 0.f);
+      }
+#pragma unroll
+      for (int col = 0; col < AB; ++col) {
+        if (c0 + col >= a.m) break;
+        float2 p0 = make_float2(0.f, 0.f), p1 = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int nbr = 0; nbr < 9; ++nbr) {
+          const float2 v = sv[sb + off[nbr / 3] + col * BOXN + nbr % 3];
+          fma_pair(Cp[nbr][0], v, p0);
+          fma_pair(Cp[nbr][1], v, p1);
+        }
+        Y2[n + (long long)(c0 + col) * pitch] = make_float2(p0.x + p0.y, p1.x + p1.y);
+      }
+      // the zeroed slots are generic-proxy writes; the TMA that refills this buffer must see
+      // them as ordered before it
+      if (outside) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    if (__syncthreads_or(failed)) break;
+  }
+  if (failed && threadIdx.x == 0) {
+    // copies still in flight: units q .. issued - 1, each in its own buffer
+    const Ctl td{&abort_word, status, kTeardownCycles};
+    for (int r = q; r < issued; ++r) wait_bar(su32(&full[r % NBUF]), (uint32_t)((r / NBUF) & 1), td, false);
+  }
+}
+
+template <int NBUF>
+static topo_status launch_apply2_tma_n(topo_ctx* c, const CUtensorMap& map, const ApplyArgs<2, float>& a,
+                                       long long units) {
+  const size_t sm = tmaapply::smem_bytes(NBUF);
+  TOPO_CUDA_TRY(c, cudaFuncSetAttribute(apply2_tma_kernel<NBUF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  static int per_sm = 0;  // resident CTAs per SM of this instantiation (the same on every GB300)
+  if (per_sm == 0) {
+    int v = 0;
+    TOPO_CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, apply2_tma_kernel<NBUF>, 256, sm));
+    per_sm = v > 0 ? v : 1;
+  }
+  const long long grid = std::min(units, (long long)per_sm * c->num_sms);
+  apply2_tma_kernel<NBUF><<<(unsigned)grid, 256, sm, c->stream>>>(map, a, units, &c->d_sync->status, c->wait_cycles);
+  note_launch();
+  TOPO_CUDA_TRY(c, cudaGetLastError());
+  return TOPO_OK;
+}
+
+static topo_status launch_apply2_tma(topo_ctx* c, const ApplyArgs<2, float>& a) {
+  const Grid& g = c->g;
+  CUtensorMap map;
+  if (!encode_map_f32_2d(&map, a.V, a.ld, g.ndof, a.m, 2 * tmaapply::BOXN, tmaapply::AB, false))
+    return fail(c, TOPO_ERR_CUDA, "cuTensorMapEncodeTiled failed for the block apply operand");
+  const long long tiles = (long long)((g.nnx + 31) / 32) * ((g.nny + 7) / 8);
+  const long long units = tiles * ((a.m + tmaapply::AB - 1) / tmaapply::AB);
+  switch (c->apply_stages) {
+    case 2: return launch_apply2_tma_n<2>(c, map, a, units);
+    case 4: return launch_apply2_tma_n<4>(c, map, a, units);
+    default: return launch_apply2_tma_n<3>(c, map, a, units);
+  }
 }
 
 template <int DIM, typename T>
@@ -232,6 +464,10 @@ static topo_status apply_impl(topo_ctx* c, const double* rho, const T* V, T* Y, 
   if (pairs) a.cols_per_cta = std::min(m, c->apply_cols > 0 ? c->apply_cols : 32);
   groups = (m + a.cols_per_cta - 1) / a.cols_per_cta;
   dim3 grid((unsigned)tiles, (unsigned)groups);
+  if constexpr (DIM == 2 && std::is_same<T, float>::value) {
+    if (pairs && c->apply_stages > 0 && ld % 4 == 0 && ((uintptr_t)V & 15) == 0 && c->g.ndof < (1LL << 30))
+      return launch_apply2_tma(c, a);
+  }
   if constexpr (DIM == 2) {
     if (pairs) {
       const size_t sm = apply2_smem_bytes<T>();

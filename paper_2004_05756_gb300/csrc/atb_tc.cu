@@ -33,6 +33,7 @@
 #include <mutex>
 
 #include "common.cuh"
+#include "tma.cuh"
 
 namespace topo {
 namespace {
@@ -50,8 +51,6 @@ constexpr int SMEM_BYTES = 1024 + STAGES * STAGE_BYTES + 512;
 // bits 24-28; M = N = 128.
 constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
 
-__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
 // Shared-memory matrix descriptor: K-major operand in 8-row x 128-B atoms with the 128-byte
 // swizzle; start address >> 4 (bits 0-13), leading offset unused for this layout, stride
 // between 8-row atoms 1024 B (bits 32-45), descriptor version 1 (bits 46-47), swizzle mode 2
@@ -59,59 +58,6 @@ __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvt
 __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
   return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)(1024 >> 4) << 32) | ((uint64_t)1 << 46) |
          ((uint64_t)2 << 61);
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-struct Ctl {
-  volatile int* abort;  // shared: set by the first wait that expires
-  int* status;          // global context status word
-  long long limit;      // cycles per wait
-};
-
-// Teardown waits (copies and MMAs already in flight) get a fixed generous bound, independent
-// of the caller's wait limit: the CTA must not leave while its copies can still land.
-constexpr long long kTeardownCycles = 4000000000LL;
-
-// Wait for the phase of `bar` with the given parity to complete. Gives up (false) when another
-// wait of the CTA already expired (honour_abort) or after ctl.limit cycles, recording the
-// timeout.
-__device__ bool wait_bar(uint32_t bar, uint32_t parity, const Ctl& ctl, bool honour_abort) {
-  const long long t0 = clock64();
-  while (!mbar_try(bar, parity)) {
-    if (honour_abort && *ctl.abort) return false;
-    if (clock64() - t0 > ctl.limit) {
-      *ctl.abort = 1;
-      atomicCAS(ctl.status, 0, (int)TOPO_ERR_TIMEOUT);
-      return false;
-    }
-  }
-  return true;
-}
-
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-          dst),
-      "l"((uint64_t)map), "r"(x), "r"(y), "r"(bar)
-      : "memory");
 }
 
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
@@ -346,11 +292,13 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   }
 }
 
+}  // namespace
+
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
-EncodeTiledFn encode_fn() {
+static EncodeTiledFn encode_fn() {
   static std::once_flag once;
   static EncodeTiledFn fn = nullptr;
   std::call_once(once, [] {
@@ -364,21 +312,24 @@ EncodeTiledFn encode_fn() {
   return fn;
 }
 
-// 2D map of an FP32 column-major N x k block: x = row (contiguous), y = column; box 32 x 64
-// with the 128-byte swizzle; rows >= N and columns >= k read as zero.
-bool make_map(CUtensorMap* m, const float* A, long long lda, int k, long long N) {
+bool encode_map_f32_2d(CUtensorMap* m, const float* A, long long ld, long long rows, long long cols, unsigned box_x,
+                       unsigned box_y, bool swizzle128) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return false;
-  cuuint64_t dims[2] = {(cuuint64_t)N, (cuuint64_t)k};
-  cuuint64_t strides[1] = {(cuuint64_t)lda * sizeof(float)};
-  cuuint32_t box[2] = {KCH, 64};
+  cuuint64_t dims[2] = {(cuuint64_t)rows, (cuuint64_t)cols};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * sizeof(float)};
+  cuuint32_t box[2] = {box_x, box_y};
   cuuint32_t estr[2] = {1, 1};
   return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)A, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            swizzle128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-}  // namespace
+// 2D map of an FP32 column-major N x k block: x = row (contiguous), y = column; box 32 x 64
+// with the 128-byte swizzle; rows >= N and columns >= k read as zero.
+static bool make_map(CUtensorMap* m, const float* A, long long lda, int k, long long N) {
+  return encode_map_f32_2d(m, A, lda, N, k, KCH, 64, true);
+}
 
 topo_status launch_atb_tc_partial(topo_ctx* c, const float* A, long long lda, int k1, const float* B, long long ldb,
                                   int k2, long long N, double* partial, size_t partial_cap, int* G_out) {

@@ -563,6 +563,7 @@ struct topo_ctx {
   int pcg_max_ctas;  // cap on the CTAs of one persistent solve (0 = none)
   int rom_tensor;    // FP32 projection contraction: 1 tensor cores (tcgen05), 0 SIMT FP32
   int apply_cols;    // columns per CTA of the 2D node-centric apply (0 = default split)
+  int apply_stages;  // 2D FP32 block apply: 0 cp.async staging, 2-4 TMA units in flight per CTA
   char err[512];
 };
 

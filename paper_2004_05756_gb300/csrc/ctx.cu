@@ -337,6 +337,7 @@ extern "C" topo_status topo_create(const topo_problem* prob, void* cuda_stream, 
   c->max_outer = 30;
   c->wait_cycles = 2000000000LL;
   c->rom_tensor = 1;
+  c->apply_stages = 3;
   c->rom_refine = 8;
   c->pcg_blocks_per_sm = 0;
   c->inner_cap = 2000;
@@ -516,6 +517,10 @@ extern "C" topo_status topo_set_param(topo_ctx* c, topo_param which, double v) {
     case TOPO_PARAM_ROM_TENSOR:
       if (!(v == 0 || v == 1)) return fail(c, TOPO_ERR_INVALID, "rom tensor must be 0 or 1");
       c->rom_tensor = (int)v;
+      return TOPO_OK;
+    case TOPO_PARAM_APPLY_STAGES:
+      if (!(v == 0 || v == 2 || v == 3 || v == 4)) return fail(c, TOPO_ERR_INVALID, "apply stages must be 0, 2, 3 or 4");
+      c->apply_stages = (int)v;
       return TOPO_OK;
     case TOPO_PARAM_PCG_BLOCKS_PER_SM:
       if (!(v >= 0 && v <= 8)) return fail(c, TOPO_ERR_INVALID, "blocks per SM must be in [0,8]");

@@ -1,7 +1,7 @@
 """Run one hot libtopo call on a named workload, a few times, for profiler captures.
 
     python -m paper_2004_05756_gb300.profcase --call pcg --prec fp64 --maxit 200
-    python -m paper_2004_05756_gb300.profcase --call apply --prec fp32 --m 64
+    python -m paper_2004_05756_gb300.profcase --call apply --prec fp32 --m 64 --ld-pad 4
     python -m paper_2004_05756_gb300.profcase --call rom_solve_elem --k 16
     python -m paper_2004_05756_gb300.profcase --call rom_solve --prec fp32 --k 64 --shape 96x48x48
 
@@ -35,6 +35,9 @@ def main(argv=None):
     ap.add_argument("--blocks-per-sm", type=int, default=0, help="CTAs per SM of the persistent solve (0 = default)")
     ap.add_argument("--rom-tensor", type=int, default=1, help="FP32 projection contraction: 1 tcgen05, 0 SIMT")
     ap.add_argument("--apply-cols", type=int, default=0, help="columns per CTA of the 2D block apply (0 = default)")
+    ap.add_argument("--apply-stages", type=int, default=3,
+                    help="2D FP32 block apply: TMA units in flight per CTA (2-4), 0 = cp.async staging")
+    ap.add_argument("--ld-pad", type=int, default=1, help="round the leading dimension of V, Y up to a multiple")
     a = ap.parse_args(argv)
     import torch
 
@@ -49,6 +52,7 @@ def main(argv=None):
     T.topo_set_param(native.TOPO_PARAM_PCG_BLOCKS_PER_SM, a.blocks_per_sm)
     T.topo_set_param(native.TOPO_PARAM_ROM_TENSOR, a.rom_tensor)
     T.topo_set_param(native.TOPO_PARAM_TILE_X, a.apply_cols)
+    T.topo_set_param(native.TOPO_PARAM_APPLY_STAGES, a.apply_stages)
     f64 = dict(dtype=torch.float64, device="cuda")
     psi = torch.as_tensor(w.design_field(p, 0)).to(**f64)
     rho = torch.empty(p.nel, **f64)
@@ -70,8 +74,9 @@ def main(argv=None):
         if a.call != "rom_elem":
             T.topo_rom_elem(Phi, k, Hel)
     dt = torch.float64 if a.prec == "fp64" else torch.float32
-    V = torch.randn((a.m, p.ndof), dtype=dt, device="cuda")
-    Y = torch.empty_like(V)
+    ldp = -(-p.ndof // a.ld_pad) * a.ld_pad
+    V = torch.randn((a.m, ldp), dtype=dt, device="cuda")[:, :p.ndof]
+    Y = torch.empty((a.m, ldp), dtype=dt, device="cuda")[:, :p.ndof]
     U = torch.zeros((1, p.ndof), **f64)
     J = torch.zeros(1, **f64)
     dc = torch.empty(p.nel, **f64)
@@ -105,7 +110,7 @@ def main(argv=None):
     e1.record()
     e1.synchronize()
     print(f"{a.call} {a.prec} shape={a.shape} m={a.m} k={k} hdm_kernel={a.hdm_kernel} bps={a.blocks_per_sm} "
-          f"rom_tensor={a.rom_tensor} apply_cols={a.apply_cols}: "
+          f"rom_tensor={a.rom_tensor} apply_cols={a.apply_cols} apply_stages={a.apply_stages} ld={ldp}: "
           f"{e0.elapsed_time(e1) / a.reps * 1e3:.1f} us/call")
     T.topo_check()
 
