@@ -602,7 +602,8 @@ def run_serving(args):
                        "rate_per_s": args.rate, "sessions": args.sessions},
             "p50_ms": s["p50_ms"], "p99_ms": s["p99_ms"], "hdm_fallbacks": s["hdm_fallbacks"],
             "rom_evals": s["rom_evals"], "mean_basis_size": s["mean_basis_size"],
-            "max_concurrency": srv.max_concurrency, "wall_s": wall}
+            "max_concurrency": srv.max_concurrency, "session_evictions": srv.evictions,
+            "session_restores": srv.restores, "wall_s": wall}
 
 
 def main():

@@ -29,7 +29,11 @@ The server keeps `slots` request slots. Requests start in arrival order as soon 
 free and, for a standalone request or the first request of a session, its estimated device
 memory fits the free budget (admission by free HBM). Requests of one session run in order;
 requests of different sessions and standalone requests overlap on the GPU. A session's memory
-is released after its last request. Every persistent solve uses a fixed share of the GPU (its
+is released after its last request. When a request does not fit, the least recently used idle
+session (resident, between two of its requests) is evicted: its window, basis, element
+reduced matrices and last centre state are copied to pinned host memory and its device memory
+is freed. Its next request admits the memory again and copies the state back, so an evicted
+session's results are the same as if it had stayed resident. Every persistent solve uses a fixed share of the GPU (its
 SMs divided by the slots), which also fixes its reduction order: a request's results are
 bitwise the same alone and in a mix.
 
@@ -38,6 +42,7 @@ All arithmetic runs in libtopo's kernels; this module only schedules and marshal
 from __future__ import annotations
 
 import dataclasses
+import heapq
 import math
 import threading
 import time
@@ -106,16 +111,18 @@ def estimate_bytes(dim: int, shape, k: int = 1) -> int:
 class _Session:
     """Resident state of one optimisation run (device tensors on the session's own stream)."""
 
-    def __init__(self, srv: "Server", req: Request):
-        torch, native = srv.torch, srv.native
+    STATE = ("window", "Phi", "Hel", "u_prev")  # device tensors that carry the run
+
+    def __init__(self, srv: "Server", req: Request, held: int):
+        torch = srv.torch
+        self.srv = srv
         self.p = w.build_problem(req.dim, req.shape)
         self.stream = torch.cuda.Stream()
         self.kmax = srv.kmax
         p = self.p
         f64 = dict(dtype=torch.float64, device="cuda")
         with torch.cuda.stream(self.stream):
-            self.T = native.Topo(p, stream=self.stream)
-            self.T.topo_set_param(native.TOPO_PARAM_PCG_MAX_CTAS, srv.ctas)
+            self._open_context()
             self.window = torch.zeros((self.kmax, p.ndof), **f64)
             self.Phi = torch.zeros((self.kmax, p.ndof), **f64)
             self.Hel = torch.zeros((p.nel + 1) * self.kmax * (self.kmax + 1) // 2, **f64)
@@ -123,6 +130,48 @@ class _Session:
         self.nwin = 0
         self.seed = req.seed
         self.psi = w.design_field(p, req.seed)  # centre of step 0
+        # admission state, guarded by the server's lock
+        self.held = held          # device bytes admitted for the session
+        self.counted = True       # held is part of the server's in-use total
+        self.resident = True      # state on the device (False: spilled to host)
+        self.busy = True          # a request of the session holds a slot
+        self.evicting = False
+        self.last_use = time.perf_counter()
+        self._host = None
+
+    def _open_context(self):
+        native = self.srv.native
+        self.T = native.Topo(self.p, stream=self.stream)
+        self.T.topo_set_param(native.TOPO_PARAM_PCG_MAX_CTAS, self.srv.ctas)
+
+    def evict(self):
+        """Copy the state to pinned host memory, then free the context and device tensors."""
+        torch = self.srv.torch
+        with torch.cuda.stream(self.stream):
+            host = {}
+            for name in self.STATE:
+                t = getattr(self, name)
+                host[name] = torch.empty(t.shape, dtype=t.dtype, pin_memory=True)
+                host[name].copy_(t, non_blocking=True)
+        self.stream.synchronize()
+        self.T.close()
+        self.T = None
+        for name in self.STATE:
+            setattr(self, name, None)
+        self._host = host
+        self.resident = False
+        torch.cuda.empty_cache()  # the blocks belong to this session's stream: hand them back
+
+    def restore(self):
+        """Recreate the context and copy the spilled state back (bitwise the same)."""
+        torch = self.srv.torch
+        with torch.cuda.stream(self.stream):
+            self._open_context()
+            for name in self.STATE:
+                setattr(self, name, self._host[name].to("cuda", non_blocking=True))
+        self.stream.synchronize()
+        self._host = None
+        self.resident = True
 
     def designs(self, step: int):
         """Centre and candidate of the given step (the steps of a session arrive in order)."""
@@ -135,7 +184,9 @@ class _Session:
 
     def close(self):
         self.stream.synchronize()
-        self.T.close()
+        if self.T is not None:
+            self.T.close()
+            self.T = None
 
 
 class Server:
@@ -166,6 +217,10 @@ class Server:
         self.free_slots = list(range(slots))
         self.max_concurrency = 0
         self.concurrency = 0
+        self.sessions: dict[int, _Session] = {}  # live sessions, resident or spilled
+        self.waiting: list[tuple] = []  # (arrival, request id) of the requests waiting to start
+        self.evictions = 0
+        self.restores = 0
 
     # -- one evaluation -----------------------------------------------------------------------
     def _evaluate(self, T, p, psi_c, psi_x, window, nwin, Phi, Hel, U0, stream) -> dict:
@@ -256,15 +311,57 @@ class Server:
         return self._evaluate(S.T, S.p, psi_c, psi_x, S.window, S.nwin, S.Phi, S.Hel, S.u_prev, S.stream)
 
     # -- the stream -----------------------------------------------------------------------------
-    def _acquire(self, need: int) -> int:
+    def _evict_one(self, keep) -> bool:
+        """With the lock held: spill the least recently used idle session other than `keep`.
+        The copy runs with the lock released; returns False when no session is idle."""
+        idle = [S for S in self.sessions.values() if S.resident and not S.busy and not S.evicting and S is not keep]
+        if not idle:
+            return False
+        V = min(idle, key=lambda S: S.last_use)
+        V.evicting = True
+        self.lock.release()
+        try:
+            V.evict()
+        finally:
+            self.lock.acquire()
+            V.evicting = False
+            V.counted = False
+            self.in_use -= V.held
+            self.evictions += 1
+            self.lock.notify_all()
+        return True
+
+    def _acquire(self, req: Request, need: int, owner: _Session | None = None) -> tuple[int, int]:
+        """Take a slot and admit `need` bytes, or for a live session its own bytes if it was
+        spilled. Requests start in arrival order: only the earliest waiting request may start,
+        and it evicts idle sessions while the budget is short. Returns (slot, admitted)."""
+        key = (req.arrival, req.rid)
         with self.lock:
-            while not self.free_slots or self.in_use + need > self.budget:
+            heapq.heappush(self.waiting, key)
+            while True:
+                if self.waiting[0] != key:
+                    self.lock.wait()
+                    continue
+                if owner is not None:
+                    if owner.evicting:
+                        self.lock.wait()
+                        continue
+                    need = 0 if owner.counted else owner.held
+                if self.free_slots and self.in_use + need <= self.budget:
+                    break
+                if self.free_slots and self._evict_one(owner):
+                    continue
                 self.lock.wait()
+            heapq.heappop(self.waiting)
+            self.lock.notify_all()  # the next request in line may start too
             slot = self.free_slots.pop(0)
             self.in_use += need
+            if owner is not None:
+                owner.busy = True
+                owner.counted = True
             self.concurrency += 1
             self.max_concurrency = max(self.max_concurrency, self.concurrency)
-            return slot
+            return slot, need
 
     def _release(self, slot: int, freed: int):
         with self.lock:
@@ -294,7 +391,7 @@ class Server:
             if need > self.budget:
                 errors.append((req.rid, MemoryError(f"request needs {need} B > budget {self.budget} B")))
                 return
-            slot = self._acquire(need)
+            slot, _ = self._acquire(req, need)
             t_start = time.perf_counter() - t0
             try:
                 out = self._standalone(req, self.streams[slot])
@@ -307,41 +404,58 @@ class Server:
 
         def session_worker(sid: int, sreqs: list[Request]):
             S = None
-            held = 0
             try:
                 for n, req in enumerate(sreqs):
                     t_arr = wait_arrival(req)
-                    need = 0
                     if S is None:  # the session's memory is admitted with its first request
                         need = estimate_bytes(req.dim, req.shape, self.kmax)
                         if need > self.budget:
                             raise MemoryError(f"session {sid} needs {need} B > budget {self.budget} B")
-                    slot = self._acquire(need)
-                    held += need
+                        slot, _ = self._acquire(req, need)
+                    else:  # re-admits the session's memory if it was evicted meanwhile
+                        slot, _ = self._acquire(req, 0, owner=S)
                     last = n == len(sreqs) - 1
                     t_start = time.perf_counter() - t0
                     try:
                         if S is None:
-                            S = _Session(self, req)
+                            try:
+                                S = _Session(self, req, need)
+                            except BaseException:
+                                with self.lock:
+                                    self.in_use -= need
+                                raise
+                            with self.lock:
+                                self.sessions[sid] = S
+                        elif not S.resident:
+                            S.restore()
+                            with self.lock:
+                                self.restores += 1
                         out = self._in_session(S, req)
                         results[req.rid] = Result(rid=req.rid, t_arrival=t_arr, t_start=t_start,
                                                   t_done=time.perf_counter() - t0, session=sid, index=req.step,
                                                   **out)
                     finally:
-                        if last and S is not None:
-                            S.close()
-                            S = None
-                        self._release(slot, held if last else 0)
-                        if last:
-                            held = 0
+                        freed = 0
+                        if S is not None:
+                            with self.lock:
+                                S.busy = False
+                                S.last_use = time.perf_counter()
+                            if last:
+                                S.close()
+                                with self.lock:
+                                    self.sessions.pop(sid, None)
+                                freed = S.held
+                                S = None
+                        self._release(slot, freed)
             except Exception as e:  # surfaced after the stream
                 errors.append((sid, e))
                 if S is not None:
-                    S.close()
-                if held:
                     with self.lock:
-                        self.in_use -= held
+                        self.sessions.pop(sid, None)
+                        if S.counted:
+                            self.in_use -= S.held
                         self.lock.notify_all()
+                    S.close()
 
         threads = []
         sessions: dict[int, list[Request]] = {}

@@ -1,6 +1,7 @@
 """Serving form: continuous batching of design-evaluation requests. Each request's results
 are bitwise the same alone and in the mix; one request is checked against the oracle; a tight
-memory budget admits one request at a time."""
+memory budget admits one request at a time; under a budget too small for all sessions at once,
+idle sessions are spilled to host memory and restored with the same results."""
 import numpy as np
 import pytest
 
@@ -134,3 +135,25 @@ def test_session_request_matches_oracle():
     assert res.theta == pytest.approx(theta, rel=1e-6)
     assert res.Jk == pytest.approx(Jk, rel=1e-7)
     assert res.J == pytest.approx(J, rel=1e-7)
+
+
+def test_idle_sessions_evicted_under_memory_pressure_same_results():
+    """A budget that holds the largest session and little more: sessions are admitted by
+    evicting idle ones (state copied to pinned host memory, device memory freed) and restored
+    for their next request. Every result equals the run with room for all sessions, bitwise."""
+    require_cuda()
+    from paper_2004_05756_gb300.serving import Server, estimate_bytes
+    reqs = _session_requests(steps=3)
+    roomy = Server(slots=3, kmax=4)
+    ref = {r.rid: r for r in roomy.run(reqs, realtime=False)}
+    assert roomy.evictions == 0
+    need = {s: estimate_bytes(d, shape, 4) for s, (d, shape) in enumerate(SESS)}
+    budget = max(need.values()) + min(need.values()) // 2
+    tight = Server(slots=3, kmax=4, budget_bytes=budget)
+    got = {r.rid: r for r in tight.run(_session_requests(steps=3), realtime=False)}
+    assert tight.evictions >= 1 and tight.restores >= 1, (tight.evictions, tight.restores)
+    assert tight.in_use == 0 and not tight.sessions
+    assert set(got) == set(ref)
+    for rid, a in ref.items():
+        b = got[rid]
+        assert (a.J, a.theta, a.Jk, a.used_hdm, a.k, a.step) == (b.J, b.theta, b.Jk, b.used_hdm, b.k, b.step), rid
