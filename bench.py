@@ -234,7 +234,7 @@ def run_ours(args, rank, world):
         stream.synchronize()
 
     ev = lambda: torch.cuda.Event(enable_timing=True)
-    stats = dict(step=[], hdm=[], solve=[], build=[], rom=[], iters=[], outer=[], relres=[])
+    stats = dict(step=[], hdm=[], solve=[], build=[], rom=[], iters=[], outer=[], relres=[], poly=[])
 
     def step(s, record=True, host_io=None):
         """One trust-region-shaped pass; host_io = (pinned inputs, pinned outputs) for e2e."""
@@ -286,6 +286,7 @@ def run_ours(args, rank, world):
             stats["rom"].extend(a.elapsed_time(bq) for a, bq in rom_ev)
             stats["iters"].append(info["iters"])
             stats["outer"].append(info["outer"])
+            stats["poly"].append(info.get("poly", 0))
             stats["relres"].append(info["relres"])
         return info
 
@@ -321,7 +322,7 @@ def run_ours(args, rank, world):
                     dpr=torch.zeros((R, Ne), dtype=torch.float64).pin_memory())
         e2e_steps = []
         saved = stats["step"]
-        stats_e2e = dict(step=[], hdm=[], solve=[], build=[], rom=[], iters=[], outer=[], relres=[])
+        stats_e2e = dict(step=[], hdm=[], solve=[], build=[], rom=[], iters=[], outer=[], relres=[], poly=[])
         stats_main = stats
         for s in range(args.warmup, args.warmup + args.steps):
             flush.zero_()
@@ -420,8 +421,12 @@ def run_ours(args, rank, world):
     fp64_peak = 152 * 4 * 2.07e9 / 1e12
     # FP32: 152 SMs x 128 FMA/clk (256 flop) x 2.07 GHz
     fp32_peak = 152 * 256 * 2.07e9 / 1e12
+    poly = int(max(stats["poly"])) if stats.get("poly") else 0
     if prec == "fp64":
-        flop_dof = 51.0 if p.dim == 2 else 177.0
+        # per iteration: one stencil apply (36 flop/DOF in 2D, 162 in 3D) plus the vector updates
+        # and dot products; each further step of a degree-d polynomial preconditioner applies the
+        # stencil once more and updates three vectors (6 flop/DOF)
+        flop_dof = (51.0 if p.dim == 2 else 177.0) + max(0, poly - 1) * ((36.0 if p.dim == 2 else 162.0) + 6.0)
         peak, peak_source = fp64_peak, "derived: 152 SMs x 4 FP64 flop/clk x 2.07 GHz (measured FMA peak 1.19)"
         rkernel = "pcg2_kernel (assembled-stencil Chronopoulos-Gear PCG, one launch per HDM solve)"
     else:
@@ -461,7 +466,7 @@ def run_ours(args, rank, world):
                      "traffic": pcg_traffic() if (prec == "fp64" and args.config == "mbb600x200") else None,
                      "traffic_unit": "bytes per launch", "launch_ms": solve_ms,
                      "peak_source": peak_source,
-                     "flop_per_dof_iter": flop_dof, "hbm_peak_gbs": hbm_peak},
+                     "flop_per_dof_iter": flop_dof, "pcg_poly": poly, "hbm_peak_gbs": hbm_peak},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "apply_roofline": None if apply_rf is None else {
             "call": "topo_apply_K, m = 64 columns (node-centric 2D block apply)",

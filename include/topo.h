@@ -73,6 +73,8 @@ typedef struct {
   double floor;   /* 2 eps || |K| |u| ||_2 / ||f||_2: the FP64 rounding floor of any residual of
                      u. The FP64 solves accept relres <= max(rtol, floor): designs that put loads
                      on near-void material cannot go below it (0 when not computed) */
+  int poly;       /* degree of the polynomial preconditioner of the FP64 stencil solve (1 =
+                     Jacobi; each iteration then applies K poly times); 0 for the other solvers */
 } topo_solve_info;
 
 /* Tunable parameters (topo_set_param). */
@@ -94,11 +96,18 @@ typedef enum {
                                       topo_rom_solve: 1 = tensor cores (tcgen05 kind::tf32 on an exact
                                       hi/lo split of each FP32 operand, FP32 accumulate per 256 rows,
                                       FP64 beyond; default), 0 = SIMT FP32 */
-  TOPO_PARAM_APPLY_STAGES = 10     /* 2D FP32 block apply with ld % 4 == 0 and V 16-byte aligned:
+  TOPO_PARAM_APPLY_STAGES = 10,    /* 2D FP32 block apply with ld % 4 == 0 and V 16-byte aligned:
                                       2, 3 (default) or 4 = halo rows staged by TMA (one box per
                                       halo row and 8 columns) with that many tile-column units in
                                       flight per CTA of a persistent grid; 0 = per-thread cp.async
                                       staging (the form used for other leading dimensions) */
+  TOPO_PARAM_PCG_POLY = 11         /* FP64 solve (TOPO_PARAM_HDM_KERNEL 0): preconditioner
+                                      z = p(D^-1 K) D^-1 r, p from d steps of the Chebyshev
+                                      iteration on [lambda_max/100, lambda_max], lambda_max the
+                                      Gershgorin bound of D^-1 K; d = 1 is Jacobi, 2-8 trade d - 1
+                                      more operator applies (halo exchanges, no grid barrier) per
+                                      iteration for fewer iterations and reductions; 0 = automatic
+                                      (default) */
 } topo_param;
 
 /* Create a context for one problem; computes K_e (2x2(x2) Gauss quadrature), the filter

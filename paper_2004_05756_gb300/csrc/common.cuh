@@ -564,6 +564,7 @@ struct topo_ctx {
   int rom_tensor;    // FP32 projection contraction: 1 tensor cores (tcgen05), 0 SIMT FP32
   int apply_cols;    // columns per CTA of the 2D node-centric apply (0 = default split)
   int apply_stages;  // 2D FP32 block apply: 0 cp.async staging, 2-4 TMA units in flight per CTA
+  int pcg_poly;      // FP64 stencil PCG: degree of the Chebyshev polynomial preconditioner (0 = auto)
   char err[512];
 };
 

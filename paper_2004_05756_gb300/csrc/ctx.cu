@@ -338,6 +338,7 @@ extern "C" topo_status topo_create(const topo_problem* prob, void* cuda_stream, 
   c->wait_cycles = 2000000000LL;
   c->rom_tensor = 1;
   c->apply_stages = 3;
+  c->pcg_poly = 0;
   c->rom_refine = 8;
   c->pcg_blocks_per_sm = 0;
   c->inner_cap = 2000;
@@ -521,6 +522,10 @@ extern "C" topo_status topo_set_param(topo_ctx* c, topo_param which, double v) {
     case TOPO_PARAM_APPLY_STAGES:
       if (!(v == 0 || v == 2 || v == 3 || v == 4)) return fail(c, TOPO_ERR_INVALID, "apply stages must be 0, 2, 3 or 4");
       c->apply_stages = (int)v;
+      return TOPO_OK;
+    case TOPO_PARAM_PCG_POLY:
+      if (!(v >= 0 && v <= 8 && v == (int)v)) return fail(c, TOPO_ERR_INVALID, "pcg poly must be an integer in [0,8]");
+      c->pcg_poly = (int)v;
       return TOPO_OK;
     case TOPO_PARAM_PCG_BLOCKS_PER_SM:
       if (!(v >= 0 && v <= 8)) return fail(c, TOPO_ERR_INVALID, "blocks per SM must be in [0,8]");

@@ -38,7 +38,7 @@ __device__ __forceinline__ void unit_coords(const Grid& g, long long u, int& i0,
 // elements. Dirichlet convention: a fixed row is the identity, a fixed neighbour column zero.
 template <int DIM>
 __device__ void assemble_node(const Grid& g, const typename KeOf<DIM, double>::type& ke, const double* rho,
-                              int i, int j, int k, long long n, double* C) {
+                              int i, int j, int k, long long n, double* C, float* C32 = nullptr) {
   constexpr int NB = StencilGeom<DIM>::NB, ND = DIM == 2 ? 8 : 24, NE = DIM == 2 ? 4 : 8;
   double E[NE];
 #pragma unroll
@@ -82,6 +82,7 @@ __device__ void assemble_node(const Grid& g, const typename KeOf<DIM, double>::t
         if (!nin || is_fixed(g, DIM * m + d)) v = 0.0;
         if (rfix[r]) v = (nb == centre && r == d) ? 1.0 : 0.0;
         C[(long long)((nb * DIM + r) * DIM + d) * g.nnodes + n] = v;
+        if (C32) C32[(long long)((nb * DIM + r) * DIM + d) * g.nnodes + n] = (float)v;
       }
   }
 }
@@ -172,17 +173,71 @@ __device__ __forceinline__ void stencil_apply(const Grid& g, const double* __res
   for (int d = 0; d < DIM; ++d) vown[d] = __ldcg(v + DIM * n + d);
 }
 
+// y = C32 v in FP32 for node (i, j, k) (the polynomial preconditioner); vown: v at the node.
+template <int DIM>
+__device__ __forceinline__ void stencil_apply32(const Grid& g, const float* __restrict__ C, const float* v, int i,
+                                                int j, int k, long long n, float* y, float* vown) {
+  constexpr int NB = StencilGeom<DIM>::NB;
+#pragma unroll
+  for (int r = 0; r < DIM; ++r) y[r] = 0.f;
+  if constexpr (DIM == 2) {
+    // as the FP64 form: a neighbour outside the grid has zero coefficients and reads the node
+    float2 vv[NB];
+#pragma unroll
+    for (int nb = 0; nb < NB; ++nb) {
+      const int ii = i + nb % 3 - 1, jj = j + nb / 3 - 1;
+      const bool nin = ii >= 0 && ii < g.nnx && jj >= 0 && jj < g.nny;
+      const long long m = nin ? ii + (long long)g.nnx * jj : n;
+      vv[nb] = __ldcg(reinterpret_cast<const float2*>(v) + m);
+    }
+    const float* gp = C + n;
+#pragma unroll
+    for (int nb = 0; nb < NB; ++nb) {
+      float cc[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) cc[q] = __ldg(gp + (long long)(nb * 4 + q) * g.nnodes);
+      y[0] = fmaf(cc[0], vv[nb].x, y[0]);
+      y[0] = fmaf(cc[1], vv[nb].y, y[0]);
+      y[1] = fmaf(cc[2], vv[nb].x, y[1]);
+      y[1] = fmaf(cc[3], vv[nb].y, y[1]);
+    }
+    vown[0] = vv[4].x;
+    vown[1] = vv[4].y;
+    return;
+  }
+#pragma unroll
+  for (int nb = 0; nb < NB; ++nb) {
+    const int dx = nb % 3 - 1, dy = (nb / 3) % 3 - 1, dz = DIM == 3 ? nb / 9 - 1 : 0;
+    const int ii = i + dx, jj = j + dy, kk = k + dz;
+    const bool nin = ii >= 0 && ii < g.nnx && jj >= 0 && jj < g.nny && (DIM == 2 || (kk >= 0 && kk < g.nnz));
+    if (!nin) continue;
+    const long long m = ii + (long long)g.nnx * (jj + (long long)g.nny * kk);
+    float vv[DIM];
+#pragma unroll
+    for (int d = 0; d < DIM; ++d) vv[d] = __ldcg(v + DIM * m + d);
+#pragma unroll
+    for (int r = 0; r < DIM; ++r)
+#pragma unroll
+      for (int d = 0; d < DIM; ++d) y[r] = fmaf(__ldg(C + (long long)((nb * DIM + r) * DIM + d) * g.nnodes + n), vv[d], y[r]);
+  }
+#pragma unroll
+  for (int d = 0; d < DIM; ++d) vown[d] = __ldcg(v + DIM * n + d);
+}
+
 // The solver, run by a group of G co-resident CTAs (this CTA is number `rank` of the group)
 // that share the barrier state gb.
-template <int DIM>
+// POLY: the polynomial preconditioner is compiled in (degree a.poly, 1 = Jacobi); without it
+// the degree is the constant 1 and the Jacobi kernel is unchanged.
+template <int DIM, bool POLY>
 __device__ __forceinline__ void pcg2_body(const Pcg2Args<DIM>& a, const unsigned G, const unsigned rank,
                                           GridBar* gb) {
   __shared__ double red[96];
   __shared__ double sh_gamma[P2_MAX_COLS], sh_alpha[P2_MAX_COLS], sh_beta[P2_MAX_COLS], sh_tol2[P2_MAX_COLS],
       sh_ff[P2_MAX_COLS], sh_rr[P2_MAX_COLS], sh_den[P2_MAX_COLS];
   __shared__ int sh_done[P2_MAX_COLS];
-  __shared__ double sh_sum[4 * P2_MAX_COLS];
+  __shared__ double sh_sum[P2_SLOTS * P2_MAX_COLS];
   __shared__ double sh_floor2[P2_MAX_COLS];
+  __shared__ double sh_c1[P2_MAX_POLY], sh_c2[P2_MAX_POLY], sh_itheta;  // Chebyshev coefficients
   __shared__ int s_okw;
   const Grid& g = a.g;
   const int m = a.m;
@@ -194,13 +249,13 @@ __device__ __forceinline__ void pcg2_body(const Pcg2Args<DIM>& a, const unsigned
   // after it; a CTA can only reuse a buffer after the next barrier, i.e. after every CTA has
   // finished reading it.
   auto P = [&](int slot, int c) -> double* {
-    return part + ((size_t)((((bar + 1) & 1) * 4 + slot) * m + c)) * G + rank;
+    return part + ((size_t)((((bar + 1) & 1) * P2_SLOTS + slot) * m + c)) * G + rank;
   };
   auto R = [&](int slot, int c) -> double { return sh_sum[slot * m + c]; };
   // grid barrier, then every CTA reduces the per-CTA partials of nred slots itself
   auto sync_reduce = [&](int nred) -> bool {
     if (!grid_barrier(gb, &gs->status, bar, a.wait_cycles, G)) return false;
-    if (nred > 0) reduce_slots(part + (size_t)((bar & 1) * 4 * m) * G, G, nred, sh_sum);
+    if (nred > 0) reduce_slots(part + (size_t)((bar & 1) * P2_SLOTS * m) * G, G, nred, sh_sum);
     return true;
   };
   // this CTA's units: a contiguous, balanced range
@@ -267,16 +322,129 @@ __device__ __forceinline__ void pcg2_body(const Pcg2Args<DIM>& a, const unsigned
   };
 
   // --- stencil assembly and Jacobi diagonal ----------------------------------------------
+  // With a polynomial preconditioner, also the Gershgorin bound max_i sum_j |K_ij| / K_ii of the
+  // spectrum of D^-1 K (an upper bound, so the polynomial stays positive on the spectrum).
+  const int poly = POLY ? a.poly : 1;
+  double gmax = 0.0;
   for_owned([&](int i, int j, int k, long long n) {
-    assemble_node<DIM>(g, a.ke, a.rho, i, j, k, n, a.C);
+    assemble_node<DIM>(g, a.ke, a.rho, i, j, k, n, a.C, poly > 1 ? a.C32 : nullptr);
     const int centre = DIM == 2 ? 4 : 13;
 #pragma unroll
     for (int r = 0; r < DIM; ++r) {
       const double d = a.C[(long long)((centre * DIM + r) * DIM + r) * g.nnodes + n];
       a.dinv[DIM * n + r] = 1.0 / d;
+      if (poly > 1) {
+        a.dinv32[DIM * n + r] = (float)(1.0 / d);
+        double rs = 0.0;
+        for (int q = 0; q < StencilGeom<DIM>::NB * DIM; ++q) rs += fabs(a.C[(long long)(r * DIM + (q / DIM) * DIM * DIM + q % DIM) * g.nnodes + n]);
+        gmax = fmax(gmax, rs / d);
+      }
     }
   });
+  if (poly > 1) {
+    for (int o = 16; o; o >>= 1) gmax = fmax(gmax, __shfl_xor_sync(0xffffffffu, gmax, o));
+    if (lane == 0) red[warp] = gmax;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double bm = 0.0;
+      for (int q = 0; q < nwarps; ++q) bm = fmax(bm, red[q]);
+      *P(0, 0) = bm;
+    }
+  }
   if (!sync_reduce(0)) return;
+  if (poly > 1) {
+    // Chebyshev iteration for D^-1 K z = D^-1 r on [lmax / ratio, lmax], from z = 0, poly steps:
+    // z_0 = b / theta, then d_j = c1_j d_{j-1} + c2_j res_{j-1}, z_j = z_{j-1} + d_j, with
+    // rho_0 = 1 / sigma, rho_j = 1 / (2 sigma - rho_{j-1}), c1_j = rho_j rho_{j-1},
+    // c2_j = 2 rho_j / delta (theta, delta: centre and half-width of the interval).
+    if (threadIdx.x == 0) {
+      const double* bpart = part + (size_t)((bar & 1) * P2_SLOTS * m) * G;
+      double lmax = 0.0;
+      for (unsigned q = 0; q < G; ++q) lmax = fmax(lmax, bpart[q]);
+      if (!(lmax > 0.0) || !isfinite(lmax)) lmax = 1.0;
+      lmax *= 1.001;  // margin for the FP32 rounding of the stencil the polynomial applies
+      const double lmin = lmax / a.cheb_ratio;
+      const double th = 0.5 * (lmax + lmin), de = 0.5 * (lmax - lmin), sigma = th / de;
+      sh_itheta = 1.0 / th;
+      double ro = 1.0 / sigma;
+      for (int j = 1; j < poly; ++j) {
+        const double rn = 1.0 / (2.0 * sigma - ro);
+        sh_c1[j] = rn * ro;
+        sh_c2[j] = 2.0 * rn / de;
+        ro = rn;
+      }
+    }
+    __syncthreads();
+  }
+
+  // gamma = r.z and r.r of the last phase U, per thread, until phase W reduces them
+  double accg[P2_MAX_COLS], accr[P2_MAX_COLS];
+
+  // Polynomial preconditioner z = p(D^-1 K) D^-1 r (poly > 1), r complete for the owned nodes,
+  // evaluated in FP32 (a preconditioner needs no FP64 accuracy, and GB300 runs FP32 at 64x the
+  // FP64 rate): poly Chebyshev steps, of which the last poly - 1 apply the FP32 stencil to the
+  // previous direction. Step 0 stores b = D^-1 r as the residual, so every step updates
+  // res -= D^-1 K t. Each direction is published to the neighbouring CTAs with the release
+  // flags and read through their halo, in alternating buffers: a CTA can only overwrite a
+  // buffer after every neighbour has published the next step, i.e. has finished reading it.
+  // The last step converts z to FP64 and accumulates the per-thread r.z into accg; z itself is
+  // published by the caller. all_cols: every column (the true residual, whose convergence
+  // flags are not set yet), else the open ones.
+  auto precond = [&](bool all_cols) -> bool {
+    const float it = (float)sh_itheta;
+    for (int c = 0; c < m; ++c) {
+      if (!all_cols && sh_done[c]) continue;
+      const long long o0 = (long long)c * N;
+      for_owned([&](int i, int j, int k, long long n) {
+#pragma unroll
+        for (int d = 0; d < DIM; ++d) {
+          const long long dof = DIM * n + d, o = o0 + dof;
+          const float b = __ldg(a.dinv32 + dof) * (float)a.r[o];
+          const float zv = b * it;
+          a.res[o] = b;
+          a.t0[o] = zv;
+          a.z32[o] = zv;
+        }
+      });
+    }
+    publish_z();
+    for (int c = 0; c < m; ++c) accg[c] = 0.0;
+    for (int st = 1; st < poly; ++st) {
+      if (!wait_z()) return false;
+      const float* tin = (st & 1) ? a.t0 : a.t1;
+      float* tout = (st & 1) ? a.t1 : a.t0;
+      const bool last = st == poly - 1;
+      const float c1 = (float)sh_c1[st], c2 = (float)sh_c2[st];
+      for (int c = 0; c < m; ++c) {
+        if (!all_cols && sh_done[c]) continue;
+        const long long o0 = (long long)c * N;
+        double ag = 0.0;
+        for_owned([&](int i, int j, int k, long long n) {
+          float y[DIM], tn[DIM];
+          stencil_apply32<DIM>(g, a.C32, tin + o0, i, j, k, n, y, tn);
+#pragma unroll
+          for (int d = 0; d < DIM; ++d) {
+            const long long dof = DIM * n + d, o = o0 + dof;
+            const float rs = fmaf(-__ldg(a.dinv32 + dof), y[d], a.res[o]);
+            const float dv = fmaf(c1, tn[d], c2 * rs);
+            const float zv = a.z32[o] + dv;
+            if (last) {
+              const double zd = (double)zv;
+              a.z[o] = zd;
+              ag = fma(a.r[o], zd, ag);
+            } else {
+              a.z32[o] = zv;
+              tout[o] = dv;
+              a.res[o] = rs;
+            }
+          }
+        });
+        if (last) accg[c] = ag;
+      }
+      if (!last) publish_z();
+    }
+    return true;
+  };
 
   // --- true residual r = f - K x, z = D^-1 r -----------------------------------------------
   // r, z for owned nodes (x = caller's U, Dirichlet entries zeroed), partial gamma, r.r, f.f,
@@ -304,16 +472,22 @@ __device__ __forceinline__ void pcg2_body(const Pcg2Args<DIM>& a, const unsigned
           } else if (first) {
             x[dof] = 0.0;  // Dirichlet entries of the solution are zero (their columns are zero)
           }
-          const double zv = __ldg(a.dinv + dof) * rv;
           a.r[c * N + dof] = rv;
-          a.z[c * N + dof] = zv;
-          t0 = fma(rv, zv, t0);
+          if (poly == 1) {
+            const double zv = __ldg(a.dinv + dof) * rv;
+            a.z[c * N + dof] = zv;
+            t0 = fma(rv, zv, t0);
+          }
         }
       });
       acc[0][c] = t0;
       acc[1][c] = t1;
       acc[2][c] = t2;
       acc[3][c] = t3;
+    }
+    if (poly > 1) {  // z = p(D^-1 K) D^-1 r: needs every CTA's r complete, and so its own halo steps
+      if (!precond(true)) return false;
+      for (int c = 0; c < m; ++c) acc[0][c] = accg[c];
     }
     for (int c = 0; c < m; ++c)
       for (int q = 0; q < 4; ++q) {
@@ -338,8 +512,6 @@ __device__ __forceinline__ void pcg2_body(const Pcg2Args<DIM>& a, const unsigned
     return true;
   };
 
-  // gamma = r.z and r.r of the last phase U, per thread, until phase W reduces them
-  double accg[P2_MAX_COLS], accr[P2_MAX_COLS];
 
   // Phase W: w = K z for owned nodes and partial delta = w.z; one grid barrier reduces delta
   // together with gamma and r.r of the preceding phase U (Chronopoulos-Gear: one reduction
@@ -347,14 +519,23 @@ __device__ __forceinline__ void pcg2_body(const Pcg2Args<DIM>& a, const unsigned
   // alpha = gamma / den with den = delta - beta gamma / alpha_old = delta - beta^2 den_old
   // (alpha_old = gamma_old / den_old; two FP64 divisions per step). Restart: beta = 0,
   // den = delta; gamma and r.r come from the true residual.
+  //
+  // With the polynomial preconditioner (poly > 1), which is symmetric only up to its FP32
+  // rounding, the recurrence for den assumes a symmetry the preconditioner lacks, and den can
+  // turn negative. So the same reduction also carries e = z.s_old and f = p_old.w, and
+  // den = p.K p for the new p = z + beta p_old is formed directly, exact for any preconditioner:
+  //   den = delta + beta (e + f) + beta^2 den_old (> 0: K is SPD).
+  // beta stays gamma_new / gamma (measured at 600x200: 1,432 iterations at degree 8, against
+  // 1,658 with the flexible choice -alpha_old e / gamma_old).
   auto phase_w = [&](bool restart) -> bool {
     if (!restart && !wait_z()) return false;
-    double acc[P2_MAX_COLS];  // per column; the node loop accumulates in a register
-    for (int c = 0; c < m; ++c) acc[c] = 0.0;
+    const bool flex = poly > 1;
+    double acc[P2_MAX_COLS], acce[P2_MAX_COLS], accf[P2_MAX_COLS];  // per column
+    for (int c = 0; c < m; ++c) acc[c] = acce[c] = accf[c] = 0.0;
     for (int c = 0; c < m; ++c) {
       if (sh_done[c]) continue;
       const double* zc = a.z + c * N;
-      double ad = 0.0;
+      double ad = 0.0, ae = 0.0, af = 0.0;  // register accumulators
       for_owned([&](int i, int j, int k, long long n) {
         double y[DIM], zn[DIM];
         stencil_apply<DIM>(g, a.C, zc, i, j, k, n, y, zn);
@@ -363,9 +544,15 @@ __device__ __forceinline__ void pcg2_body(const Pcg2Args<DIM>& a, const unsigned
           const long long dof = DIM * n + d;
           a.w[c * N + dof] = y[d];
           ad = fma(y[d], zn[d], ad);
+          if (flex && !restart) {  // p and s of the previous iteration (stale on a restart)
+            ae = fma(zn[d], a.s[c * N + dof], ae);
+            af = fma(a.p[c * N + dof], y[d], af);
+          }
         }
       });
       acc[c] = ad;
+      acce[c] = ae;
+      accf[c] = af;
     }
     for (int c = 0; c < m; ++c) {
       double t0 = acc[c], t1 = restart ? 0.0 : accg[c], t2 = restart ? 0.0 : accr[c];
@@ -375,11 +562,43 @@ __device__ __forceinline__ void pcg2_body(const Pcg2Args<DIM>& a, const unsigned
         *P(1, c) = t1;
         *P(2, c) = t2;
       }
+      if (flex) {
+        double t3 = acce[c], t4 = accf[c], t5 = 0.0;
+        block_sum3(t3, t4, t5, red);
+        if (threadIdx.x == 0) {
+          *P(3, c) = t3;
+          *P(4, c) = t4;
+        }
+      }
     }
-    if (!sync_reduce(3 * m)) return false;
+    if (!sync_reduce((flex ? 5 : 3) * m)) return false;
     if (threadIdx.x == 0) {
       for (int c = 0; c < m; ++c) {
         if (sh_done[c]) continue;
+        if (flex) {
+          const double delta = R(0, c);
+          if (restart) {
+            sh_beta[c] = 0.0;
+            sh_den[c] = delta;
+          } else {
+            const double gnew = R(1, c), e = R(3, c), f = R(4, c);
+            sh_beta[c] = gnew / sh_gamma[c];
+            sh_gamma[c] = gnew;
+            sh_rr[c] = R(2, c);
+            if (sh_rr[c] <= sh_tol2[c]) {
+              sh_done[c] = 1;
+              continue;
+            }
+            const double be = sh_beta[c];
+            sh_den[c] = delta + be * (e + f) + be * be * sh_den[c];
+          }
+          sh_alpha[c] = sh_gamma[c] / sh_den[c];
+          if (!(sh_alpha[c] > 0.0) || !isfinite(sh_alpha[c])) {
+            set_status(&gs->status, TOPO_ERR_NOT_SPD);
+            sh_done[c] = 1;
+          }
+          continue;
+        }
         if (!restart) {
           const double gnew = R(1, c);
           sh_beta[c] = gnew / sh_gamma[c];
@@ -408,9 +627,11 @@ __device__ __forceinline__ void pcg2_body(const Pcg2Args<DIM>& a, const unsigned
     return true;
   };
 
-  // Phase U: p = z + beta p, s = w + beta s, x += alpha p, r -= alpha s, z = D^-1 r; per-thread
-  // gamma = r.z and r.r (reduced by the next phase W); then z is published to the neighbours.
-  auto phase_u = [&](bool restart) {
+  // Phase U: p = z + beta p, s = w + beta s, x += alpha p, r -= alpha s, z = D^-1 r (Jacobi) or
+  // the polynomial preconditioner; per-thread gamma = r.z and r.r (reduced by the next phase W);
+  // then z is published to the neighbours.
+  auto phase_u = [&](bool restart) -> bool {
+    const bool jac = poly == 1;
     for (int c = 0; c < m; ++c) accg[c] = accr[c] = 0.0;
     for (int c = 0; c < m; ++c) {
       if (sh_done[c]) continue;
@@ -441,11 +662,13 @@ __device__ __forceinline__ void pcg2_body(const Pcg2Args<DIM>& a, const unsigned
           x[2 * n] = fma(al, pv.x, x[2 * n]);
           x[2 * n + 1] = fma(al, pv.y, x[2 * n + 1]);
           const double2 rv = make_double2(fma(-al, sv.x, rr.x), fma(-al, sv.y, rr.y));
-          const double2 zv = make_double2(di.x * rv.x, di.y * rv.y);
           reinterpret_cast<double2*>(a.r)[o2] = rv;
-          reinterpret_cast<double2*>(a.z)[o2] = zv;
-          ag = fma(rv.x, zv.x, ag);
-          ag = fma(rv.y, zv.y, ag);
+          if (jac) {
+            const double2 zv = make_double2(di.x * rv.x, di.y * rv.y);
+            reinterpret_cast<double2*>(a.z)[o2] = zv;
+            ag = fma(rv.x, zv.x, ag);
+            ag = fma(rv.y, zv.y, ag);
+          }
           ar = fma(rv.x, rv.x, ar);
           ar = fma(rv.y, rv.y, ar);
         } else {
@@ -459,10 +682,12 @@ __device__ __forceinline__ void pcg2_body(const Pcg2Args<DIM>& a, const unsigned
             a.s[o] = sv;
             x[dof] = fma(al, pv, x[dof]);
             const double rv = fma(-al, sv, a.r[o]);
-            const double zv = __ldg(a.dinv + dof) * rv;
             a.r[o] = rv;
-            a.z[o] = zv;
-            ag = fma(rv, zv, ag);
+            if (jac) {
+              const double zv = __ldg(a.dinv + dof) * rv;
+              a.z[o] = zv;
+              ag = fma(rv, zv, ag);
+            }
             ar = fma(rv, rv, ar);
           }
         }
@@ -470,7 +695,9 @@ __device__ __forceinline__ void pcg2_body(const Pcg2Args<DIM>& a, const unsigned
       accg[c] = ag;
       accr[c] = ar;
     }
+    if (!jac && !precond(false)) return false;
     publish_z();
+    return true;
   };
 
   int iters = 0;
@@ -485,7 +712,7 @@ __device__ __forceinline__ void pcg2_body(const Pcg2Args<DIM>& a, const unsigned
       bool any = false;
       for (int c = 0; c < m; ++c) any = any || !sh_done[c];
       if (!any || iters >= a.maxit) break;
-      phase_u(restart);
+      if (!phase_u(restart)) return;
       restart = false;
       ++iters;
     }
@@ -512,7 +739,7 @@ __device__ __forceinline__ void pcg2_body(const Pcg2Args<DIM>& a, const unsigned
 
 template <int DIM>
 __global__ void __launch_bounds__(P2_THREADS_SOLO, 1) pcg2_kernel(const __grid_constant__ Pcg2Args<DIM> a) {
-  pcg2_body<DIM>(a, gridDim.x, blockIdx.x, a.gb);
+  pcg2_body<DIM, true>(a, gridDim.x, blockIdx.x, a.gb);
 }
 
 // Batched form: CTA b works on instance cta_inst[b] as number cta_rank[b] of that instance's
@@ -524,14 +751,14 @@ __global__ void __launch_bounds__(P2_THREADS, 4) pcg2_batch_kernel(const Pcg2Arg
                                                                 const int* __restrict__ cta_rank,
                                                                 const int* __restrict__ grp_size) {
   const int inst = cta_inst[blockIdx.x];
-  pcg2_body<DIM>(args[inst], (unsigned)grp_size[inst], (unsigned)cta_rank[blockIdx.x], args[inst].gb);
+  pcg2_body<DIM, false>(args[inst], (unsigned)grp_size[inst], (unsigned)cta_rank[blockIdx.x], args[inst].gb);
 }
 template __global__ void pcg2_batch_kernel<2>(const Pcg2Args<2>*, const int*, const int*, const int*);
 
 
 template <int DIM>
 topo_status build_pcg2_args(topo_ctx* c, const double* rho, const double* F, double* U, int m, int ld, double rtol,
-                            int maxit, int G, Pcg2Args<DIM>* out, GridSync* status) {
+                            int maxit, int G, Pcg2Args<DIM>* out, GridSync* status, int poly) {
   const Grid& g = c->g;
   const long long N = g.ndof;
   size_t off = 0;
@@ -543,7 +770,13 @@ topo_status build_pcg2_args(topo_ctx* c, const double* rho, const double* F, dou
   const size_t oC = take((size_t)StencilGeom<DIM>::NC * g.nnodes * 8), oD = take(N * 8);
   size_t ov[5];
   for (int t = 0; t < 5; ++t) ov[t] = take(N * m * 8);
-  const size_t opart = take(sizeof(double) * 8 * m * G), oflag = take(sizeof(unsigned long long) * G),
+  size_t oC32 = 0, oD32 = 0, of[4] = {0, 0, 0, 0};
+  if (poly > 1) {  // FP32 stencil, D^-1 and the four vectors of the polynomial preconditioner
+    oC32 = take((size_t)StencilGeom<DIM>::NC * g.nnodes * 4);
+    oD32 = take(N * 4);
+    for (int t = 0; t < 4; ++t) of[t] = take(N * m * 4);
+  }
+  const size_t opart = take(sizeof(double) * 2 * P2_SLOTS * m * G), oflag = take(sizeof(unsigned long long) * G),
                oinfo = take(64);
   topo_status st = ensure_scratch(c, off);
   if (st) return st;
@@ -565,6 +798,12 @@ topo_status build_pcg2_args(topo_ctx* c, const double* rho, const double* F, dou
   a.dinv = (double*)(base + oD);
   double** vecs[5] = {&a.r, &a.z, &a.w, &a.p, &a.s};
   for (int t = 0; t < 5; ++t) *vecs[t] = (double*)(base + ov[t]);
+  float** fvecs[4] = {&a.t0, &a.t1, &a.res, &a.z32};
+  for (int t = 0; t < 4; ++t) *fvecs[t] = poly > 1 ? (float*)(base + of[t]) : nullptr;
+  a.C32 = poly > 1 ? (float*)(base + oC32) : nullptr;
+  a.dinv32 = poly > 1 ? (float*)(base + oD32) : nullptr;
+  a.poly = poly > 1 ? poly : 1;
+  a.cheb_ratio = 100.0;  // interval [lambda_max / 100, lambda_max]
   a.partial = (double*)(base + opart);
   a.zflag = (unsigned long long*)(base + oflag);
   a.info = (int*)(base + oinfo);
@@ -597,6 +836,9 @@ int pcg2_occupancy() {
   return occ;
 }
 
+// Degree of the polynomial preconditioner when TOPO_PARAM_PCG_POLY is 0.
+static int pcg_poly_auto(int dim) { return dim == 2 ? 8 : 4; }
+
 template <int DIM>
 topo_status solve_stencil_fp64(topo_ctx* c, const double* rho, const double* F, double* U, int m, int ld, double rtol,
                                int maxit, topo_solve_info* info_host) {
@@ -611,7 +853,8 @@ topo_status solve_stencil_fp64(topo_ctx* c, const double* rho, const double* F, 
   const long long maxG = (nunits + P2_THREADS_SOLO / 32 - 1) / (P2_THREADS_SOLO / 32);  // >= 1 unit per warp
   if (G > maxG) G = std::max(1LL, maxG);
   Pcg2Args<DIM> a;
-  topo_status st = build_pcg2_args<DIM>(c, rho, F, U, m, ld, rtol, maxit, (int)G, &a, c->d_sync);
+  const int poly = c->pcg_poly > 0 ? c->pcg_poly : pcg_poly_auto(DIM);
+  topo_status st = build_pcg2_args<DIM>(c, rho, F, U, m, ld, rtol, maxit, (int)G, &a, c->d_sync, poly);
   if (st) return st;
   TOPO_CUDA_TRY(c, cudaMemsetAsync(c->d_bar, 0, sizeof(GridBar), c->stream));  // counter, generation, abort
   TOPO_CUDA_TRY(c, cudaMemsetAsync(a.zflag, 0, sizeof(unsigned long long) * G, c->stream));
@@ -639,6 +882,7 @@ topo_status solve_stencil_fp64(topo_ctx* c, const double* rho, const double* F, 
     info_host->outer = 0;
     info_host->relres = sqrt(hrr[0]);
     info_host->floor = sqrt(hrr[1]);
+    info_host->poly = a.poly;
     info_host->status = dev_status ? dev_status : hinfo[2];
     if (dev_status) {
       int zero = 0;
@@ -660,4 +904,4 @@ template topo_status solve_stencil_fp64<3>(topo_ctx*, const double*, const doubl
 }  // namespace topo
 
 template topo_status topo::build_pcg2_args<2>(topo_ctx*, const double*, const double*, double*, int, int, double, int,
-                                              int, topo::Pcg2Args<2>*, topo::GridSync*);
+                                              int, topo::Pcg2Args<2>*, topo::GridSync*, int);

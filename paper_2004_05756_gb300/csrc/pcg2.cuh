@@ -6,6 +6,8 @@
 namespace topo {
 
 constexpr int P2_MAX_COLS = 32;
+constexpr int P2_MAX_POLY = 8;        // highest degree of the polynomial preconditioner
+constexpr int P2_SLOTS = 8;           // reduced values per column and barrier (5 used at most)
 constexpr int P2_THREADS = 256;       // batched kernel: up to 4 CTAs per SM
 constexpr int P2_THREADS_SOLO = 512;  // single solve: one CTA per SM (half the barrier arrivals)
 
@@ -27,7 +29,16 @@ struct Pcg2Args {
   double* w;
   double* p;
   double* s;
-  double* partial;   // [2 barrier parities][4 slots][m][G]
+  // polynomial preconditioner (poly > 1 only), all FP32:
+  float* C32;        //   the stencil [NB*DIM*DIM][nnodes] and D^-1 [N]
+  float* dinv32;
+  float* t0;         //   direction vectors, alternating, whose halo its applies read; N x m each
+  float* t1;
+  float* res;        //   residual of its Chebyshev iteration; N x m
+  float* z32;        //   the accumulated result; N x m
+  int poly;          // degree of the preconditioner polynomial in D^-1 K (1 = Jacobi)
+  double cheb_ratio; // its Chebyshev interval: [lambda_max / cheb_ratio, lambda_max]
+  double* partial;   // [2 barrier parities][P2_SLOTS slots][m][G]
   unsigned long long* zflag;  // [G]: phase-U completions of each CTA (z published), reset per launch
   GridSync* gs;      // sticky status
   GridBar* gb;
@@ -50,9 +61,11 @@ cudaError_t launch_pcg2_batch2(unsigned ctas, cudaStream_t stream, const Pcg2Arg
 
 // Prepare one instance's solve for a group of G CTAs: scratch, stencil and vector pointers,
 // barrier state, info words. status is the sticky status word the solve reports into.
+// poly > 1 selects the Chebyshev polynomial preconditioner of that degree (three more scratch
+// vectors); the batched solve uses 1.
 template <int DIM>
 topo_status build_pcg2_args(topo_ctx* c, const double* rho, const double* F, double* U, int m, int ld, double rtol,
-                            int maxit, int G, Pcg2Args<DIM>* out, GridSync* status);
+                            int maxit, int G, Pcg2Args<DIM>* out, GridSync* status, int poly = 1);
 
 // Resident CTAs per SM of the batched kernel.
 int pcg2_occupancy();

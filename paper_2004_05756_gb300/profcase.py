@@ -23,7 +23,7 @@ if ROOT not in sys.path:
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("--call", required=True, choices=["pcg", "apply", "rom_elem", "rom_solve_elem", "rom_solve",
+    ap.add_argument("--call", required=True, choices=["pcg", "hdm", "apply", "rom_elem", "rom_solve_elem", "rom_solve",
                                                       "rom_error", "grad", "filter"])
     ap.add_argument("--shape", default="600x200")
     ap.add_argument("--prec", default="fp64")
@@ -38,6 +38,8 @@ def main(argv=None):
     ap.add_argument("--apply-stages", type=int, default=3,
                     help="2D FP32 block apply: TMA units in flight per CTA (2-4), 0 = cp.async staging")
     ap.add_argument("--ld-pad", type=int, default=1, help="round the leading dimension of V, Y up to a multiple")
+    ap.add_argument("--poly", type=int, default=0, help="FP64 solve: polynomial preconditioner degree (0 = auto)")
+    ap.add_argument("--rtol", type=float, default=1e-30, help="pcg/hdm: relative residual target")
     a = ap.parse_args(argv)
     import torch
 
@@ -53,6 +55,7 @@ def main(argv=None):
     T.topo_set_param(native.TOPO_PARAM_ROM_TENSOR, a.rom_tensor)
     T.topo_set_param(native.TOPO_PARAM_TILE_X, a.apply_cols)
     T.topo_set_param(native.TOPO_PARAM_APPLY_STAGES, a.apply_stages)
+    T.topo_set_param(native.TOPO_PARAM_PCG_POLY, a.poly)
     f64 = dict(dtype=torch.float64, device="cuda")
     psi = torch.as_tensor(w.design_field(p, 0)).to(**f64)
     rho = torch.empty(p.nel, **f64)
@@ -82,10 +85,15 @@ def main(argv=None):
     dc = torch.empty(p.nel, **f64)
     dp = torch.empty(p.nel, **f64)
 
+    last_info = {}
+
     def call():
         if a.call == "pcg":
             U.zero_()
-            T.topo_solve_hdm(rho, F, U, rtol=1e-30, maxit=a.maxit, prec=a.prec, info=False)
+            T.topo_solve_hdm(rho, F, U, rtol=a.rtol, maxit=a.maxit, prec=a.prec, info=False)
+        elif a.call == "hdm":  # a full solve to --rtol (iteration count printed below)
+            U.zero_()
+            last_info.update(T.topo_solve_hdm(rho, F, U, rtol=a.rtol, maxit=400000, prec=a.prec))
         elif a.call == "apply":
             T.topo_apply_K(rho, V, Y, a.prec)
         elif a.call == "rom_elem":
@@ -111,7 +119,7 @@ def main(argv=None):
     e1.synchronize()
     print(f"{a.call} {a.prec} shape={a.shape} m={a.m} k={k} hdm_kernel={a.hdm_kernel} bps={a.blocks_per_sm} "
           f"rom_tensor={a.rom_tensor} apply_cols={a.apply_cols} apply_stages={a.apply_stages} ld={ldp}: "
-          f"{e0.elapsed_time(e1) / a.reps * 1e3:.1f} us/call")
+          f"{e0.elapsed_time(e1) / a.reps * 1e3:.1f} us/call" + (f" poly={a.poly} {last_info}" if last_info else ""))
     T.topo_check()
 
 

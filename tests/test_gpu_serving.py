@@ -99,7 +99,8 @@ def test_sessions_alone_equal_mix_and_basis_grows():
     from paper_2004_05756_gb300.serving import Server
     reqs = _session_requests()
     srv = Server(slots=3, kmax=4)
-    mix = {r.rid: r for r in srv.run(reqs, realtime=True)}
+    # all requests queued at t = 0 (started in arrival order): the three sessions overlap
+    mix = {r.rid: r for r in srv.run(reqs, realtime=False)}
     assert srv.max_concurrency >= 2
     for s in range(len(SESS)):
         mine = [r for r in _session_requests() if r.session == s]
