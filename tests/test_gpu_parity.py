@@ -467,3 +467,42 @@ def test_barrier_timeout_reports_and_context_survives(torch):
     Jg = float((F * U).sum().item())
     Jo = fem.compliance(p, fem.solve(p, rho))
     assert abs(Jg - Jo) <= 1e-6 * abs(Jo)
+
+
+@pytest.mark.parametrize("case", ["q4_60x20", "q4_37x13", "h8_11x9x6"])
+def test_polynomial_preconditioner_same_solution_fewer_iterations(torch, case):
+    """The FP64 stencil solve with the FP32 Chebyshev polynomial preconditioner (degrees 2, 4, 8
+    and the automatic choice) reaches the oracle's direct solution like Jacobi (degree 1), to
+    rtol 1e-10, in fewer iterations; topo_solve_info reports the degree used."""
+    from paper_2004_05756_gb300.native import TOPO_PARAM_PCG_POLY
+    p = CASES[case]()
+    T = ctx_for(p)
+    psi, rho = _design(p)
+    Uo = fem.solve(p, rho)
+    Jo = fem.compliance(p, Uo)
+    iters = {}
+    for deg in (1, 2, 4, 8, 0):
+        T.topo_set_param(TOPO_PARAM_PCG_POLY, deg)
+        U = torch.zeros((1, p.ndof), dtype=torch.float64, device="cuda")
+        info = T.topo_solve_hdm(dev(rho), cols(p.F), U, rtol=1e-10, maxit=200000, prec="fp64")
+        T.topo_check()
+        assert info["status"] == 0 and info["relres"] <= 1e-10, (deg, info)
+        assert info["poly"] == (deg if deg else (8 if p.dim == 2 else 4))
+        Ug = host_cols(U)
+        J = fem.compliance(p, Ug)
+        assert abs(J - Jo) <= 1e-9 * abs(Jo), (deg, J, Jo)
+        r = p.F[:, 0] - fem.apply_K(p, rho, Ug[:, 0])
+        r[fem.fixed_dofs(p)] = 0
+        assert np.linalg.norm(r) <= 1e-9 * np.linalg.norm(p.F), deg
+        iters[deg] = info["iters"]
+    assert iters[2] < iters[1] and iters[4] < iters[2] and iters[8] < iters[4], iters
+
+
+def test_polynomial_degree_parameter_range(torch):
+    from paper_2004_05756_gb300.native import TOPO_PARAM_PCG_POLY, TopoError
+    T = ctx_for(CASES["q4_1x1"]())
+    for v in range(9):
+        T.topo_set_param(TOPO_PARAM_PCG_POLY, v)
+    for v in (9, -1, 2.5):
+        with pytest.raises(TopoError):
+            T.topo_set_param(TOPO_PARAM_PCG_POLY, v)
