@@ -104,10 +104,12 @@ typedef enum {
   TOPO_PARAM_PCG_POLY = 11         /* FP64 solve (TOPO_PARAM_HDM_KERNEL 0): preconditioner
                                       z = p(D^-1 K) D^-1 r, p from d steps of the Chebyshev
                                       iteration on [lambda_max/100, lambda_max], lambda_max the
-                                      Gershgorin bound of D^-1 K; d = 1 is Jacobi, 2-8 trade d - 1
-                                      more operator applies (halo exchanges, no grid barrier) per
-                                      iteration for fewer iterations and reductions; 0 = automatic
-                                      (default) */
+                                      Gershgorin bound of D^-1 K, evaluated in FP32 on an FP32 copy
+                                      of the stencil (the CG, its residuals and the stopping test
+                                      stay FP64). d = 1 is Jacobi; 2-8 trade d - 1 more operator
+                                      applies (halo exchanges, no grid barrier) per iteration for
+                                      fewer iterations and reductions; 0 = automatic (default: 8 in
+                                      2D, 4 in 3D) */
 } topo_param;
 
 /* Create a context for one problem; computes K_e (2x2(x2) Gauss quadrature), the filter
