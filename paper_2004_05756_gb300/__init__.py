@@ -7,7 +7,7 @@ without loading the CUDA library.
 """
 import importlib
 
-__all__ = ["workloads", "native", "build", "pipeline"]
+__all__ = ["workloads", "native", "build", "serving", "profcase"]
 
 
 def __getattr__(name):

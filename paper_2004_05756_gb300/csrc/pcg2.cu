@@ -107,7 +107,7 @@ __device__ __forceinline__ void stencil_apply_abs(const Grid& g, const double* _
       const double vv = __ldcg(v + DIM * m + d);
 #pragma unroll
       for (int r = 0; r < DIM; ++r) {
-        const double cc = __ldg(C + (long long)((nb * DIM + r) * DIM + d) * g.nnodes + n);
+        const double cc = __ldcg(C + (long long)((nb * DIM + r) * DIM + d) * g.nnodes + n);
         y[r] = fma(cc, vv, y[r]);
         yabs[r] = fma(fabs(cc), fabs(vv), yabs[r]);
       }
@@ -142,7 +142,7 @@ __device__ __forceinline__ void stencil_apply(const Grid& g, const double* __res
     for (int nb = 0; nb < NB; ++nb) {
       double cc[4];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) cc[q] = __ldg(gp + (long long)(nb * 4 + q) * g.nnodes);
+      for (int q = 0; q < 4; ++q) cc[q] = __ldcg(gp + (long long)(nb * 4 + q) * g.nnodes);
 #pragma unroll
       for (int r = 0; r < 2; ++r)
 #pragma unroll
@@ -167,7 +167,7 @@ __device__ __forceinline__ void stencil_apply(const Grid& g, const double* __res
 #pragma unroll
     for (int r = 0; r < DIM; ++r)
 #pragma unroll
-      for (int d = 0; d < DIM; ++d) y[r] = fma(__ldg(C + (long long)((nb * DIM + r) * DIM + d) * g.nnodes + n), vv[d], y[r]);
+      for (int d = 0; d < DIM; ++d) y[r] = fma(__ldcg(C + (long long)((nb * DIM + r) * DIM + d) * g.nnodes + n), vv[d], y[r]);
   }
 #pragma unroll
   for (int d = 0; d < DIM; ++d) vown[d] = __ldcg(v + DIM * n + d);
@@ -195,7 +195,7 @@ __device__ __forceinline__ void stencil_apply32(const Grid& g, const float* __re
     for (int nb = 0; nb < NB; ++nb) {
       float cc[4];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) cc[q] = __ldg(gp + (long long)(nb * 4 + q) * g.nnodes);
+      for (int q = 0; q < 4; ++q) cc[q] = __ldcg(gp + (long long)(nb * 4 + q) * g.nnodes);
       y[0] = fmaf(cc[0], vv[nb].x, y[0]);
       y[0] = fmaf(cc[1], vv[nb].y, y[0]);
       y[1] = fmaf(cc[2], vv[nb].x, y[1]);
@@ -218,7 +218,7 @@ __device__ __forceinline__ void stencil_apply32(const Grid& g, const float* __re
 #pragma unroll
     for (int r = 0; r < DIM; ++r)
 #pragma unroll
-      for (int d = 0; d < DIM; ++d) y[r] = fmaf(__ldg(C + (long long)((nb * DIM + r) * DIM + d) * g.nnodes + n), vv[d], y[r]);
+      for (int d = 0; d < DIM; ++d) y[r] = fmaf(__ldcg(C + (long long)((nb * DIM + r) * DIM + d) * g.nnodes + n), vv[d], y[r]);
   }
 #pragma unroll
   for (int d = 0; d < DIM; ++d) vown[d] = __ldcg(v + DIM * n + d);
@@ -399,7 +399,7 @@ __device__ __forceinline__ void pcg2_body(const Pcg2Args<DIM>& a, const unsigned
 #pragma unroll
         for (int d = 0; d < DIM; ++d) {
           const long long dof = DIM * n + d, o = o0 + dof;
-          const float b = __ldg(a.dinv32 + dof) * (float)a.r[o];
+          const float b = __ldcg(a.dinv32 + dof) * (float)a.r[o];
           const float zv = b * it;
           a.res[o] = b;
           a.t0[o] = zv;
@@ -425,7 +425,7 @@ __device__ __forceinline__ void pcg2_body(const Pcg2Args<DIM>& a, const unsigned
 #pragma unroll
           for (int d = 0; d < DIM; ++d) {
             const long long dof = DIM * n + d, o = o0 + dof;
-            const float rs = fmaf(-__ldg(a.dinv32 + dof), y[d], a.res[o]);
+            const float rs = fmaf(-__ldcg(a.dinv32 + dof), y[d], a.res[o]);
             const float dv = fmaf(c1, tn[d], c2 * rs);
             const float zv = a.z32[o] + dv;
             if (last) {
@@ -474,7 +474,7 @@ __device__ __forceinline__ void pcg2_body(const Pcg2Args<DIM>& a, const unsigned
           }
           a.r[c * N + dof] = rv;
           if (poly == 1) {
-            const double zv = __ldg(a.dinv + dof) * rv;
+            const double zv = __ldcg(a.dinv + dof) * rv;
             a.z[c * N + dof] = zv;
             t0 = fma(rv, zv, t0);
           }
@@ -646,7 +646,7 @@ __device__ __forceinline__ void pcg2_body(const Pcg2Args<DIM>& a, const unsigned
           const double2 zz = reinterpret_cast<const double2*>(a.z)[o2];
           const double2 ww = reinterpret_cast<const double2*>(a.w)[o2];
           const double2 rr = reinterpret_cast<const double2*>(a.r)[o2];
-          const double2 di = __ldg(reinterpret_cast<const double2*>(a.dinv) + n);
+          const double2 di = __ldcg(reinterpret_cast<const double2*>(a.dinv) + n);
           double2 pv, sv;
           if (restart) {  // p and s hold stale (possibly non-finite) data: take z and w exactly
             pv = zz;
@@ -684,7 +684,7 @@ __device__ __forceinline__ void pcg2_body(const Pcg2Args<DIM>& a, const unsigned
             const double rv = fma(-al, sv, a.r[o]);
             a.r[o] = rv;
             if (jac) {
-              const double zv = __ldg(a.dinv + dof) * rv;
+              const double zv = __ldcg(a.dinv + dof) * rv;
               a.z[o] = zv;
               ag = fma(rv, zv, ag);
             }

@@ -121,12 +121,17 @@ class _Session:
         self.kmax = srv.kmax
         p = self.p
         f64 = dict(dtype=torch.float64, device="cuda")
-        with torch.cuda.stream(self.stream):
-            self._open_context()
+        # The tensors come from the server's one allocation stream: blocks a spilled session
+        # frees go back to that stream's pool, where the next session's allocations reuse them
+        # without emptying the allocator's cache (which would synchronise the device).
+        with torch.cuda.stream(srv.alloc_stream):
             self.window = torch.zeros((self.kmax, p.ndof), **f64)
             self.Phi = torch.zeros((self.kmax, p.ndof), **f64)
             self.Hel = torch.zeros((p.nel + 1) * self.kmax * (self.kmax + 1) // 2, **f64)
             self.u_prev = torch.zeros((1, p.ndof), **f64)
+        self.stream.wait_stream(srv.alloc_stream)
+        with torch.cuda.stream(self.stream):
+            self._open_context()
         self.nwin = 0
         self.seed = req.seed
         self.psi = w.design_field(p, req.seed)  # centre of step 0
@@ -160,15 +165,19 @@ class _Session:
             setattr(self, name, None)
         self._host = host
         self.resident = False
-        torch.cuda.empty_cache()  # the blocks belong to this session's stream: hand them back
 
     def restore(self):
         """Recreate the context and copy the spilled state back (bitwise the same)."""
         torch = self.srv.torch
+        with torch.cuda.stream(self.srv.alloc_stream):
+            for name in self.STATE:
+                h = self._host[name]
+                setattr(self, name, torch.empty(h.shape, dtype=h.dtype, device="cuda"))
+        self.stream.wait_stream(self.srv.alloc_stream)
         with torch.cuda.stream(self.stream):
             self._open_context()
             for name in self.STATE:
-                setattr(self, name, self._host[name].to("cuda", non_blocking=True))
+                getattr(self, name).copy_(self._host[name], non_blocking=True)
         self.stream.synchronize()
         self._host = None
         self.resident = True
@@ -212,6 +221,9 @@ class Server:
         # one solve CTA fills an SM)
         self.ctas = max(1, props.multi_processor_count // slots)
         self.streams = [torch.cuda.Stream() for _ in range(slots)]
+        self.alloc_stream = torch.cuda.Stream()  # allocation stream of every session's tensors
+        self.evict_ms: list[float] = []    # wall time of each spill (copy out, context teardown)
+        self.restore_ms: list[float] = []  # wall time of each restore
         self.lock = threading.Condition()
         self.in_use = 0
         self.free_slots = list(range(slots))
@@ -320,8 +332,10 @@ class Server:
         V = min(idle, key=lambda S: S.last_use)
         V.evicting = True
         self.lock.release()
+        t0 = time.perf_counter()
         try:
             V.evict()
+            self.evict_ms.append(1e3 * (time.perf_counter() - t0))
         finally:
             self.lock.acquire()
             V.evicting = False
@@ -427,9 +441,11 @@ class Server:
                             with self.lock:
                                 self.sessions[sid] = S
                         elif not S.resident:
+                            t_r = time.perf_counter()
                             S.restore()
                             with self.lock:
                                 self.restores += 1
+                                self.restore_ms.append(1e3 * (time.perf_counter() - t_r))
                         out = self._in_session(S, req)
                         results[req.rid] = Result(rid=req.rid, t_arrival=t_arr, t_start=t_start,
                                                   t_done=time.perf_counter() - t0, session=sid, index=req.step,

@@ -29,18 +29,18 @@ def test_batched_solve_matches_singles_and_oracle():
     rhos = [dev(hatfilter.filter_fwd(p, psi)) for p, psi in inst]
     Fs = [cols(p.F) for p, _ in inst]
     Us = [torch.zeros_like(F) for F in Fs]
-    infos = B.topo_batch_solve_hdm(rhos, Fs, Us, rtol=1e-10, maxit=100000)
+    infos = B.topo_batch_solve_hdm(rhos, Fs, Us, rtol=1e-13, maxit=100000)
     for i, (p, psi) in enumerate(inst):
-        assert infos[i]["status"] == 0 and infos[i]["relres"] <= 1e-10, (i, infos[i])
+        assert infos[i]["status"] == 0 and infos[i]["relres"] <= max(1e-13, infos[i]["floor"]), (i, infos[i])
         rho = rhos[i].cpu().numpy()
         Uo = fem.solve(p, rho)
         Ug = host_cols(Us[i])
         for c in range(p.F.shape[1]):
             Jo = fem.compliance(p, Uo[:, c], p.F[:, c])
-            assert abs(fem.compliance(p, Ug[:, c], p.F[:, c]) - Jo) <= 1e-9 * abs(Jo), (i, c)
+            assert abs(fem.compliance(p, Ug[:, c], p.F[:, c]) - Jo) <= 1e-10 * abs(Jo), (i, c)
         T = Topo(p)
         Us1 = torch.zeros_like(Fs[i])
-        T.topo_solve_hdm(rhos[i], Fs[i], Us1, rtol=1e-10, maxit=100000)
+        T.topo_solve_hdm(rhos[i], Fs[i], Us1, rtol=1e-13, maxit=100000)
         assert relerr(Ug, host_cols(Us1)) < 1e-8
     # batched gradient and filter equal the single-instance calls
     J = torch.zeros(len(inst), dtype=torch.float64, device="cuda")
@@ -113,7 +113,7 @@ def test_batched_step_in_cuda_graph():
             B.topo_batch_filter(psis, rhos)
             for U in Us:
                 U.zero_()
-            B.topo_batch_solve_hdm(rhos, Fs, Us, rtol=1e-10, maxit=100000, info=False)
+            B.topo_batch_solve_hdm(rhos, Fs, Us, rtol=1e-13, maxit=100000, info=False)
             B.topo_batch_compliance_grad(rhos, Us, Fs, J, dcs, dps)
 
         body()  # eager: autotunes and stages the launch tables
@@ -140,4 +140,4 @@ def test_batched_step_in_cuda_graph():
     for i, p in enumerate(probs):
         rho = hatfilter.filter_fwd(p, new[i])
         Jo = fem.compliance(p, fem.solve(p, rho))
-        assert abs(Jg[i].item() - Jo) <= 1e-8 * abs(Jo), (i, Jg[i].item(), Jo)
+        assert abs(Jg[i].item() - Jo) <= 1e-10 * abs(Jo), (i, Jg[i].item(), Jo)

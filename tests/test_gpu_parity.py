@@ -2,9 +2,10 @@
 same seeded inputs. Sizes span several tiles plus ragged tails (tiles are 32x8 nodes in 2D,
 8x8x4 in 3D) and the degenerate one-element meshes.
 
-Tolerances: FP64 paths 1e-12 (max-normalised) for single operator applications, 1e-9
-relative on compliance after solves to rtol 1e-10; reduced-precision forms 1e-6 relative
-compliance error (the stated target); FP32 operator applications 2e-6 max-normalised
+Tolerances: FP64 paths 1e-13 (max-normalised) for single operator applications, 1e-10
+relative on compliance after FP64 solves to rtol 1e-13 (or to the FP64 rounding floor the
+solver reports, where that is larger); reduced-precision forms 1e-6 relative compliance error
+(the stated target); FP32 operator applications 2e-6 max-normalised
 (FP32 rounding of K_e, E and the accumulation of 64 (Q4) / 576 (H8) products); BF16 K_e
 applications 8e-3 (BF16 has an 8-bit significand: entry error <= 2^-9)."""
 import numpy as np
@@ -130,16 +131,19 @@ def test_solve_hdm(torch, case, prec):
     Uo = fem.solve(p, rho)
     Jo = fem.compliance(p, Uo)
     U = torch.zeros((1, p.ndof), dtype=torch.float64, device="cuda")
-    info = T.topo_solve_hdm(dev(rho), cols(p.F), U, rtol=1e-10, maxit=200000, prec=prec)
+    # FP64: rtol 1e-13 and compliance within 1e-10 of the oracle's direct solve; the solver may
+    # stop at its reported FP64 rounding floor eps |K||u| / |f| when that is above rtol
+    rtol = 1e-13 if prec == "fp64" else 1e-10
+    info = T.topo_solve_hdm(dev(rho), cols(p.F), U, rtol=rtol, maxit=200000, prec=prec)
     assert info["status"] == 0, info
-    assert info["relres"] <= 1e-10
+    assert info["relres"] <= max(rtol, info["floor"]), info
     Ug = host_cols(U)
     Jg = fem.compliance(p, Ug)
-    tol = 1e-9 if prec == "fp64" else 1e-6
+    tol = 1e-10 if prec == "fp64" else 1e-6
     assert abs(Jg - Jo) <= tol * abs(Jo), (Jg, Jo, info)
     r = p.F[:, 0] - fem.apply_K(p, rho, Ug[:, 0])
     r[fem.fixed_dofs(p)] = 0
-    assert np.linalg.norm(r) <= 1e-9 * np.linalg.norm(p.F)
+    assert np.linalg.norm(r) <= max(1e-10, 4 * info["floor"]) * np.linalg.norm(p.F), info
     if prec != "fp64":
         assert info["outer"] >= 1
 
@@ -249,10 +253,19 @@ def test_rom_build_solve_error(torch, case, m):
         rn = torch.zeros(2, dtype=torch.float64, device="cuda")
         uk = torch.zeros(p.ndof, dtype=torch.float64, device="cuda")
         T.topo_rom_error(dev(rho2), Phi[:k], k, y, dev(f), rn, uk)
-        assert relerr(uk.cpu().numpy(), ref["uk"]) < (1e-9 if prec == "fp64" else 1e-5)
+        ukg = uk.cpu().numpy()
+        # u_k differs from the oracle's by the conditioning of H (different bases, rounding)
+        assert relerr(ukg, ref["uk"]) < (1e-9 if prec == "fp64" else 1e-5)
         if prec == "fp64":
-            assert abs(rn[0].item() - ref["resnorm"]) <= 1e-8 * ref["resnorm"] + 1e-12 * np.linalg.norm(f)
-            assert abs(rn[1].item() - ref["relres"]) <= 1e-8 * ref["relres"] + 1e-12
+            # the residual norm of the GPU's own u_k, recomputed by the oracle, to 1e-10
+            # (Eq. trcon-topopt's ||r||; r = f - K u_k on free DOFs)
+            ro = rom.residual(p, rho2, ukg, f)
+            nro, nf = np.linalg.norm(ro), np.linalg.norm(f)
+            assert abs(rn[0].item() - nro) <= 1e-10 * nro + 1e-14 * nf, (rn[0].item(), nro)
+            assert abs(rn[1].item() - nro / nf) <= 1e-10 * nro / nf + 1e-14, (rn[1].item(), nro / nf)
+            # and the oracle's own residual norm within the propagated state difference
+            dr = np.linalg.norm(rom.residual(p, rho2, ref["uk"], f) - ro)
+            assert abs(rn[0].item() - ref["resnorm"]) <= 1e-10 * ref["resnorm"] + dr + 1e-14 * nf
 
 
 def test_rom_exact_reproduction(torch):
@@ -484,16 +497,16 @@ def test_polynomial_preconditioner_same_solution_fewer_iterations(torch, case):
     for deg in (1, 2, 4, 8, 0):
         T.topo_set_param(TOPO_PARAM_PCG_POLY, deg)
         U = torch.zeros((1, p.ndof), dtype=torch.float64, device="cuda")
-        info = T.topo_solve_hdm(dev(rho), cols(p.F), U, rtol=1e-10, maxit=200000, prec="fp64")
+        info = T.topo_solve_hdm(dev(rho), cols(p.F), U, rtol=1e-13, maxit=200000, prec="fp64")
         T.topo_check()
-        assert info["status"] == 0 and info["relres"] <= 1e-10, (deg, info)
+        assert info["status"] == 0 and info["relres"] <= max(1e-13, info["floor"]), (deg, info)
         assert info["poly"] == (deg if deg else (8 if p.dim == 2 else 4))
         Ug = host_cols(U)
         J = fem.compliance(p, Ug)
-        assert abs(J - Jo) <= 1e-9 * abs(Jo), (deg, J, Jo)
+        assert abs(J - Jo) <= 1e-10 * abs(Jo), (deg, J, Jo)
         r = p.F[:, 0] - fem.apply_K(p, rho, Ug[:, 0])
         r[fem.fixed_dofs(p)] = 0
-        assert np.linalg.norm(r) <= 1e-9 * np.linalg.norm(p.F), deg
+        assert np.linalg.norm(r) <= max(1e-10, 4 * info["floor"]) * np.linalg.norm(p.F), (deg, info)
         iters[deg] = info["iters"]
     assert iters[2] < iters[1] and iters[4] < iters[2] and iters[8] < iters[4], iters
 
@@ -506,3 +519,52 @@ def test_polynomial_degree_parameter_range(torch):
     for v in (9, -1, 2.5):
         with pytest.raises(TopoError):
             T.topo_set_param(TOPO_PARAM_PCG_POLY, v)
+
+
+def _golden_cant96():
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "cant96x48x48_fp64.txt")
+    vals, samples = {}, []
+    with open(path) as fh:
+        for ln in fh:
+            if ln.startswith("#") or not ln.strip():
+                continue
+            parts = ln.split()
+            if parts[0] == "u":
+                samples.append((int(parts[1]), float(parts[2])))
+            else:
+                vals[parts[0]] = float(parts[1])
+    return vals, samples
+
+
+def test_full_size_solve_cant96x48x48_fp64(torch):
+    """The 3D cantilever at full size (698,691 DOFs), FP64 at rtol 1e-13, against the oracle's
+    own CG solution at rtol 1e-13 (tests/golden/cant96x48x48_fp64.txt, written by
+    tests/golden/make_cant96x48x48.py from oracle/ only).
+
+    Both solutions stop at FP64 rounding floors (loads near void: ||u|| ~ 1.6e9), so the
+    compliance comparison allows 1e-10 plus the first-order bound |J_a - J_b| <= ||u|| (||r_a|| +
+    ||r_b||) of the two true residuals; the GPU's true residual is recomputed by the oracle's
+    element-by-element K(rho) and must itself be at the GPU's reported floor."""
+    p = w.cantilever_3d(96, 48, 48, rmin=2.0)
+    T = ctx_for(p)
+    psi = w.design_field(p, 0)
+    rho_d = torch.empty(p.nel, dtype=torch.float64, device="cuda")
+    T.topo_filter(dev(psi), rho_d)
+    rho = hatfilter.filter_fwd(p, psi)
+    assert relerr(rho_d.cpu().numpy(), rho) < 1e-14
+    U = torch.zeros((1, p.ndof), dtype=torch.float64, device="cuda")
+    info = T.topo_solve_hdm(rho_d, cols(p.F), U, rtol=1e-13, maxit=400000, prec="fp64")
+    assert info["status"] == 0 and info["relres"] <= max(1e-13, info["floor"]), info
+    ug = host_cols(U)[:, 0]
+    f = p.F[:, 0]
+    r = f - fem.apply_K_ebe(p, rho, ug)
+    r[fem.fixed_dofs(p)] = 0
+    nf = np.linalg.norm(f)
+    assert np.linalg.norm(r) <= max(1e-10, 4 * info["floor"]) * nf, (np.linalg.norm(r) / nf, info)
+    gold, samples = _golden_cant96()
+    Jg = fem.compliance(p, ug)
+    bound = gold["u_norm"] * (np.linalg.norm(r) + gold["true_relres"] * nf)
+    assert abs(Jg - gold["J"]) <= 1e-10 * abs(gold["J"]) + bound, (Jg, gold["J"], bound)
+    for i, v in samples:
+        assert abs(ug[i] - v) <= 1e-6 * gold["u_norm"], (i, ug[i], v)

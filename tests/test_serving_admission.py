@@ -42,6 +42,8 @@ def _server(budget, slots):
     srv.waiting = []
     srv.evictions = 0
     srv.restores = 0
+    srv.evict_ms = []
+    srv.restore_ms = []
     return srv
 
 
