@@ -234,7 +234,7 @@ def cpu_oracle_timing(p, psi_c, cand, args, rom_samples=2):
     split = {"filter": t_filter, "assembly": t_asm, "solve": max(0.0, st["t_solve"] - t_asm), "gradient": t_grad,
              "H_build": t_hb, "cholesky": t_chol, "residual": t_res}
     hi = host_info()
-    return dict(J=st["J"], t_hdm=st["t_hdm"], t_basis=st["t_basis"], t_rom=st["t_rom"],
+    return dict(J=st["J"], U=st["U"], t_hdm=st["t_hdm"], t_basis=st["t_basis"], t_rom=st["t_rom"],
                 value=(1 + args.rom_evals) / t_step, split_s=split, host=hi,
                 cores=max(1, hi["blas_threads"] or 1),
                 sample=f"1 HDM eval (SuperLU, 1 thread) at the first timed centre + basis update (k={args.k}) + "
@@ -242,7 +242,7 @@ def cpu_oracle_timing(p, psi_c, cand, args, rom_samples=2):
                        f"1 HDM + basis update + {args.rom_evals} ROM evals; wall {st['wall']:.1f} s")
 
 
-def oracle_accuracy(p, probe_in, probe, J_oracle):
+def oracle_accuracy(p, probe_in, probe, J_oracle, U_oracle=None):
     """GPU results of the accuracy probe against the FP64 oracle on the same inputs: the HDM
     compliance at the first timed centre (the oracle's SuperLU solve of the CPU baseline leg),
     and the ROM's J_k and ||r|| at candidate 0 on a basis of the first k_acc snapshot designs,
@@ -251,6 +251,19 @@ def oracle_accuracy(p, probe_in, probe, J_oracle):
     out = {"J_oracle": J_oracle,
            "hdm_J_vs_oracle_rel": abs(probe["J_rtol1e-8"] - J_oracle) / abs(J_oracle),
            "hdm_J_fp64_rtol1e-13_vs_oracle_rel": abs(probe["J_fp64_rtol1e-13"] - J_oracle) / abs(J_oracle)}
+    if U_oracle is not None:
+        # Both FP64 solutions stop at a rounding floor of their residual; to first order
+        # |J_a - J_b| <= ||u|| (||r_a|| + ||r_b||) (J - J_h = u^T r for compliance).
+        rho_c = hatfilter.filter_fwd(p, probe_in["centre"])
+        u_o = U_oracle[:, 0]
+        r_o = rom.residual(p, rho_c, u_o, p.F[:, 0])
+        nf = float(np.linalg.norm(p.F[:, 0]))
+        nu = float(np.linalg.norm(u_o))
+        out["oracle_relres"] = float(np.linalg.norm(r_o)) / nf
+        out["hdm_J_fp64_rtol1e-13_first_order_bound_rel"] = nu * nf * (
+            probe["J_fp64_rtol1e-13_relres"] + out["oracle_relres"]) / abs(J_oracle)
+        out["hdm_J_rtol1e-8_first_order_bound_rel"] = nu * nf * (
+            probe["J_rtol1e-8_relres"] + out["oracle_relres"]) / abs(J_oracle)
     t0 = time.perf_counter()
     S = probe_in["snaps"]
     U = np.stack([fem.solve(p, hatfilter.filter_fwd(p, S[:, i]))[:, 0] for i in range(S.shape[1])], 1)
@@ -843,7 +856,7 @@ def main():
                                    "sample": cpu["sample"], "split_s": cpu["split_s"], "host": cpu["host"],
                                    "part_ms": {"hdm_eval": 1e3 * cpu["t_hdm"], "basis_update": 1e3 * cpu["t_basis"],
                                                "rom_eval": 1e3 * cpu["t_rom"]}}
-            out["accuracy"].update(oracle_accuracy(p, probe_in, out["accuracy"]["probe"], cpu["J"]))
+            out["accuracy"].update(oracle_accuracy(p, probe_in, out["accuracy"]["probe"], cpu["J"], cpu["U"]))
         else:
             out["cpu_baseline"] = None
         print(json.dumps(out), flush=True)
