@@ -324,7 +324,7 @@ def run_ours(args, rank, world):
         stream.synchronize()
 
     ev = lambda: torch.cuda.Event(enable_timing=True)
-    stats = dict(step=[], hdm=[], solve=[], build=[], rom=[], iters=[], outer=[], relres=[], poly=[])
+    stats = dict(step=[], hdm=[], solve=[], build=[], rom=[], iters=[], outer=[], relres=[], poly=[], mg=[], fallback=[])
 
     def step(s, record=True, host_io=None):
         """One trust-region-shaped pass; host_io = (pinned inputs, pinned outputs) for e2e."""
@@ -377,6 +377,8 @@ def run_ours(args, rank, world):
             stats["iters"].append(info["iters"])
             stats["outer"].append(info["outer"])
             stats["poly"].append(info.get("poly", 0))
+            stats["mg"].append(info.get("mg_levels", 0))
+            stats["fallback"].append(info.get("fallback", 0))
             stats["relres"].append(info["relres"])
         return info
 
@@ -412,7 +414,7 @@ def run_ours(args, rank, world):
                     dpr=torch.zeros((R, Ne), dtype=torch.float64).pin_memory())
         e2e_steps = []
         saved = stats["step"]
-        stats_e2e = dict(step=[], hdm=[], solve=[], build=[], rom=[], iters=[], outer=[], relres=[], poly=[])
+        stats_e2e = dict(step=[], hdm=[], solve=[], build=[], rom=[], iters=[], outer=[], relres=[], poly=[], mg=[], fallback=[])
         stats_main = stats
         for s in range(args.warmup, args.warmup + args.steps):
             flush.zero_()
@@ -548,15 +550,24 @@ def run_ours(args, rank, world):
     # FP32: 152 SMs x 128 FMA/clk (256 flop) x 2.07 GHz
     fp32_peak = 152 * 256 * 2.07e9 / 1e12
     poly = int(max(stats["poly"])) if stats.get("poly") else 0
+    mg_levels = int(max(stats["mg"])) if stats.get("mg") else 0
     # FP32 flops of the polynomial preconditioner per DOF and iteration: d - 1 applies of the FP32
     # stencil (36 flop/DOF in 2D, 162 in 3D) with three vector updates (6 flop/DOF) each
     flop32_dof = max(0, poly - 1) * ((36.0 if p.dim == 2 else 162.0) + 6.0)
+    if mg_levels:
+        # FP32 V-cycle (2 Chebyshev steps per side): per level 4 stencil applies (one pre step,
+        # the residual, two post steps) of 2 * 3^d * d flop/DOF plus ~6 flop/DOF of updates each;
+        # coarser levels add 1/4 (2D) or 1/8 (3D) of the DOFs per level
+        per = 4 * ((36.0 if p.dim == 2 else 162.0) + 6.0)
+        flop32_dof = per * (4.0 / 3.0 if p.dim == 2 else 8.0 / 7.0)
     if prec == "fp64":
         # FP64 per iteration: one stencil apply (36 flop/DOF in 2D, 162 in 3D) plus the vector
         # updates and dot products
         flop_dof = 51.0 if p.dim == 2 else 177.0
         peak, peak_source = fp64_peak, "derived: 152 SMs x 4 FP64 flop/clk x 2.07 GHz (measured FMA peak 1.19)"
-        rkernel = "pcg2_kernel (assembled-stencil Chronopoulos-Gear PCG, one launch per HDM solve)"
+        rkernel = ("pcg2_mg_kernel (assembled-stencil Chronopoulos-Gear PCG with the FP32 multigrid V-cycle "
+                   "preconditioner, one launch per HDM solve)" if mg_levels else
+                   "pcg2_kernel (assembled-stencil Chronopoulos-Gear PCG, one launch per HDM solve)")
     else:
         # FP32 inner iterations of the element-form apply (2 ndof_e^2 flop per element: 64 flop/DOF
         # in 2D, 384 in 3D) plus the updates and dots (13); the time also holds the FP64 completion
@@ -599,7 +610,8 @@ def run_ours(args, rank, world):
                      "traffic": pcg_traffic() if (prec == "fp64" and args.config == "mbb600x200") else None,
                      "traffic_unit": "bytes per launch", "launch_ms": solve_ms,
                      "peak_source": peak_source,
-                     "flop_per_dof_iter": flop_dof, "pcg_poly": poly,
+                     "flop_per_dof_iter": flop_dof, "pcg_poly": poly, "mg_levels": mg_levels,
+                     "mg_fallbacks": int(sum(stats["fallback"])) if stats.get("fallback") else 0,
                      "fp32_preconditioner": {"flop_per_dof_iter": flop32_dof, "achieved": achieved32,
                                              "peak": fp32_peak, "unit": "TFLOP/s",
                                              "frac": achieved32 / fp32_peak},
@@ -609,9 +621,10 @@ def run_ours(args, rank, world):
                                   "80 B/DOF)",
                      "achieved_gbs": 96.0 * N * iters / (solve_ms * 1e-3) / 1e9,
                      "frac_hbm": 96.0 * N * iters / (solve_ms * 1e-3) / 1e9 / hbm_peak,
-                     "note": "FP64 CG flops against the FP64 peak; the FP32 polynomial preconditioner's flops are "
-                             "counted separately against the FP32 peak. Neither pipe is saturated: the iteration "
-                             "is bound by its grid barrier and the halo exchanges of the polynomial steps",
+                     "note": "FP64 CG flops against the FP64 peak; the FP32 preconditioner's flops (the "
+                             "multigrid V-cycle, else the polynomial) are counted separately against the FP32 peak. "
+                             "Neither pipe is saturated: each iteration is bound by the latency of its dependent "
+                             "steps (the grid barrier of the CG and the halo exchanges of the preconditioner)",
                      "hbm_peak_gbs": hbm_peak},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "apply_roofline": None if apply_rf is None else {

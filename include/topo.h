@@ -74,7 +74,12 @@ typedef struct {
                      u. The FP64 solves accept relres <= max(rtol, floor): designs that put loads
                      on near-void material cannot go below it (0 when not computed) */
   int poly;       /* degree of the polynomial preconditioner of the FP64 stencil solve (1 =
-                     Jacobi; each iteration then applies K poly times); 0 for the other solvers */
+                     Jacobi; each iteration then applies K poly times); 0 for the other solvers
+                     and for the multigrid preconditioner */
+  int mg_levels;  /* levels of the multigrid preconditioner of the FP64 stencil solve (0 when the
+                     solve used another preconditioner) */
+  int fallback;   /* 1 when the FP32 V-cycle stopped being positive definite (conditioning beyond
+                     FP32) and the solve restarted from its true residual with FP64 Jacobi */
 } topo_solve_info;
 
 /* Tunable parameters (topo_set_param). */
@@ -101,7 +106,7 @@ typedef enum {
                                       halo row and 8 columns) with that many tile-column units in
                                       flight per CTA of a persistent grid; 0 = per-thread cp.async
                                       staging (the form used for other leading dimensions) */
-  TOPO_PARAM_PCG_POLY = 11         /* FP64 solve (TOPO_PARAM_HDM_KERNEL 0): preconditioner
+  TOPO_PARAM_PCG_POLY = 11,        /* FP64 solve (TOPO_PARAM_HDM_KERNEL 0): preconditioner
                                       z = p(D^-1 K) D^-1 r, p from d steps of the Chebyshev
                                       iteration on [lambda_max/100, lambda_max], lambda_max the
                                       Gershgorin bound of D^-1 K, evaluated in FP32 on an FP32 copy
@@ -109,7 +114,22 @@ typedef enum {
                                       stay FP64). d = 1 is Jacobi; 2-8 trade d - 1 more operator
                                       applies (halo exchanges, no grid barrier) per iteration for
                                       fewer iterations and reductions; 0 = automatic (default: 8 in
-                                      2D, 4 in 3D) */
+                                      2D, 4 in 3D). Used when TOPO_PARAM_PCG_MG is 0 */
+  TOPO_PARAM_PCG_MG = 12,          /* FP64 solve (TOPO_PARAM_HDM_KERNEL 0): 1 (default) = geometric
+                                      multigrid V-cycle preconditioner: Galerkin coarse operators
+                                      P^T K P of linear interpolation, formed in FP64 once per
+                                      solve, Chebyshev smoothing on [lambda_max/30, lambda_max]
+                                      per level, the coarsest level (<= 160 DOFs) solved with its
+                                      dense inverse; the V-cycle runs in FP32 and the CG, its
+                                      residuals and stopping test in FP64. 0 = the polynomial /
+                                      Jacobi preconditioner of TOPO_PARAM_PCG_POLY. Meshes too small
+                                      to coarsen use the polynomial */
+  TOPO_PARAM_MG_DEGREE = 13,       /* multigrid: Chebyshev smoothing steps before and after the
+                                      coarse correction, 1 .. 4 (default 2) */
+  TOPO_PARAM_MG_SINGLE_NODES = 14  /* multigrid: coarse levels with at most this many nodes run on
+                                      one CTA with block barriers instead of grid-wide halo
+                                      exchanges (default 0: only the coarsest level; level 0
+                                      always runs on all CTAs) */
 } topo_param;
 
 /* Create a context for one problem; computes K_e (2x2(x2) Gauss quadrature), the filter

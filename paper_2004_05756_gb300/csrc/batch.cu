@@ -239,6 +239,8 @@ static topo_status batch_solve_dim(topo_batch* b, const double* const* rho, cons
       info_host[i].relres = std::sqrt(hr[0]);
       info_host[i].floor = std::sqrt(hr[1]);
       info_host[i].status = hi[2];
+      info_host[i].poly = 1;
+      info_host[i].mg_levels = 0;
       if (hi[2] && worst == TOPO_OK) worst = (topo_status)hi[2];
     }
     int st = 0;

@@ -565,6 +565,9 @@ struct topo_ctx {
   int apply_cols;    // columns per CTA of the 2D node-centric apply (0 = default split)
   int apply_stages;  // 2D FP32 block apply: 0 cp.async staging, 2-4 TMA units in flight per CTA
   int pcg_poly;      // FP64 stencil PCG: degree of the Chebyshev polynomial preconditioner (0 = auto)
+  int pcg_mg;        // FP64 stencil PCG: 1 = multigrid V-cycle preconditioner, 0 = polynomial / Jacobi
+  int mg_deg;        // multigrid: Chebyshev smoothing steps per side (1 .. 4)
+  long long mg_single_nodes;  // multigrid: levels with at most this many nodes run on one CTA
   char err[512];
 };
 

@@ -339,6 +339,9 @@ extern "C" topo_status topo_create(const topo_problem* prob, void* cuda_stream, 
   c->rom_tensor = 1;
   c->apply_stages = 3;
   c->pcg_poly = 0;
+  c->pcg_mg = 1;
+  c->mg_deg = 2;
+  c->mg_single_nodes = 0;
   c->rom_refine = 8;
   c->pcg_blocks_per_sm = 0;
   c->inner_cap = 2000;
@@ -526,6 +529,19 @@ extern "C" topo_status topo_set_param(topo_ctx* c, topo_param which, double v) {
     case TOPO_PARAM_PCG_POLY:
       if (!(v >= 0 && v <= 8 && v == (int)v)) return fail(c, TOPO_ERR_INVALID, "pcg poly must be an integer in [0,8]");
       c->pcg_poly = (int)v;
+      return TOPO_OK;
+    case TOPO_PARAM_PCG_MG:
+      if (!(v == 0 || v == 1)) return fail(c, TOPO_ERR_INVALID, "pcg mg must be 0 or 1");
+      c->pcg_mg = (int)v;
+      return TOPO_OK;
+    case TOPO_PARAM_MG_DEGREE:
+      if (!(v >= 1 && v <= 4 && v == (int)v)) return fail(c, TOPO_ERR_INVALID, "mg degree must be an integer in [1,4]");
+      c->mg_deg = (int)v;
+      return TOPO_OK;
+    case TOPO_PARAM_MG_SINGLE_NODES:
+      if (!(v >= 0 && v <= 1e9 && v == (long long)v))
+        return fail(c, TOPO_ERR_INVALID, "mg single-CTA node count must be an integer in [0,1e9]");
+      c->mg_single_nodes = (long long)v;
       return TOPO_OK;
     case TOPO_PARAM_PCG_BLOCKS_PER_SM:
       if (!(v >= 0 && v <= 8)) return fail(c, TOPO_ERR_INVALID, "blocks per SM must be in [0,8]");

@@ -625,6 +625,9 @@ static topo_status solve_impl(topo_ctx* c, const double* rho, const double* F, d
         info_host->relres = sub.relres;
         info_host->floor = sub.floor;
         info_host->status = sub.status;
+        info_host->poly = sub.poly;
+        info_host->mg_levels = sub.mg_levels;
+        info_host->fallback = sub.fallback;
       }
       if (st2 == TOPO_ERR_NOT_CONVERGED && !info_host) return TOPO_OK;
       return st2;

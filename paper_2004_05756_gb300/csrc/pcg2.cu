@@ -226,9 +226,9 @@ __device__ __forceinline__ void stencil_apply32(const Grid& g, const float* __re
 
 // The solver, run by a group of G co-resident CTAs (this CTA is number `rank` of the group)
 // that share the barrier state gb.
-// POLY: the polynomial preconditioner is compiled in (degree a.poly, 1 = Jacobi); without it
-// the degree is the constant 1 and the Jacobi kernel is unchanged.
-template <int DIM, bool POLY>
+// PK selects the preconditioner compiled in: 0 Jacobi (the batched kernel); 1 Jacobi or the
+// FP32 Chebyshev polynomial of degree a.poly; 2 the FP32 geometric multigrid V-cycle (mg.cuh).
+template <int DIM, int PK>
 __device__ __forceinline__ void pcg2_body(const Pcg2Args<DIM>& a, const unsigned G, const unsigned rank,
                                           GridBar* gb) {
   __shared__ double red[96];
@@ -238,6 +238,11 @@ __device__ __forceinline__ void pcg2_body(const Pcg2Args<DIM>& a, const unsigned
   __shared__ double sh_sum[P2_SLOTS * P2_MAX_COLS];
   __shared__ double sh_floor2[P2_MAX_COLS];
   __shared__ double sh_c1[P2_MAX_POLY], sh_c2[P2_MAX_POLY], sh_itheta;  // Chebyshev coefficients
+  // multigrid: per-level smoother coefficients and the CTA ranges each exchange waits for
+  __shared__ float mg_ith[MG_MAX_LEVELS], mg_c1[MG_MAX_LEVELS][MG_MAX_DEG], mg_c2[MG_MAX_LEVELS][MG_MAX_DEG];
+  __shared__ int mg_halo[MG_MAX_LEVELS][2], mg_rest[MG_MAX_LEVELS][2], mg_prol[MG_MAX_LEVELS][2];
+  __shared__ int mg_okc;
+  __shared__ int sh_fallback;  // multigrid: the FP32 V-cycle lost positive definiteness
   __shared__ int s_okw;
   const Grid& g = a.g;
   const int m = a.m;
@@ -321,19 +326,204 @@ __device__ __forceinline__ void pcg2_body(const Pcg2Args<DIM>& a, const unsigned
     return s_okw != 0;
   };
 
+  // --- multigrid setup (PK == 2), once per solve after the level-0 stencil -------------------
+  // 1. Galerkin levels 1 .. L-1 (all CTAs split each level's units; a grid barrier after each),
+  // 2. the coarsest operator as a dense matrix, factorised by CTA 0 (Cholesky, FP64),
+  // 3. its inverse, one column per CTA, 4. the smoother coefficients of every level and the
+  // ranges of CTAs each exchange of the V-cycle waits for.
+  auto block_max = [&](double v) -> double {
+    for (int o = 16; o; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    __syncthreads();
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    double bm = 0.0;
+    for (int q = 0; q < nwarps; ++q) bm = fmax(bm, red[q]);
+    __syncthreads();
+    return bm;
+  };
+  auto mg_setup = [&]() -> bool {
+    const MgArgs& M = a.mg;
+    for (int l = 0; l + 1 < M.L; ++l) {
+      const MgLevel& F = M.lv[l];
+      const MgLevel& Cc = M.lv[l + 1];
+      const long long c0 = Cc.nunits * rank / G, c1 = Cc.nunits * (rank + 1) / G;
+      const int ux = (Cc.nnx + 31) / 32;
+      double gm = 0.0;
+      for (long long u = c0 + warp; u < c1; u += nwarps) {
+        const int i = (int)(u % ux) * 32 + lane;
+        const long long r = u / ux;
+        const int j = (int)(r % Cc.nny), k = (int)(r / Cc.nny);
+        if (i >= Cc.nnx) continue;
+        const long long n = i + (long long)Cc.nnx * (j + (long long)Cc.nny * k);
+        gm = fmax(gm, mg_galerkin_node<DIM>(g, F, Cc, l == 0, i, j, k, n));
+      }
+      const double bm = block_max(gm);
+      if (threadIdx.x == 0) M.lmax[(size_t)(l + 1) * G + rank] = bm;
+      if (!sync_reduce(0)) return false;
+    }
+    // coarsest level: dense rows of the owned nodes
+    const int nc = M.nc;
+    {
+      const MgLevel& Cc = M.lv[M.L - 1];
+      constexpr int NB = StencilGeom<DIM>::NB;
+      const long long c0 = Cc.nunits * rank / G, c1 = Cc.nunits * (rank + 1) / G;
+      const int ux = (Cc.nnx + 31) / 32;
+      for (long long u = c0 + warp; u < c1; u += nwarps) {
+        const int i = (int)(u % ux) * 32 + lane;
+        const long long r = u / ux;
+        const int j = (int)(r % Cc.nny), k = (int)(r / Cc.nny);
+        if (i >= Cc.nnx) continue;
+        const long long n = i + (long long)Cc.nnx * (j + (long long)Cc.nny * k);
+        for (int ar = 0; ar < DIM; ++ar) {
+          double* row = M.A + (size_t)(DIM * n + ar) * nc;
+          for (int q = 0; q < nc; ++q) row[q] = 0.0;
+          for (int nb = 0; nb < NB; ++nb) {
+            const int ii = i + nb % 3 - 1, jj = j + (nb / 3) % 3 - 1, kk = DIM == 3 ? k + nb / 9 - 1 : 0;
+            if (ii < 0 || ii >= Cc.nnx || jj < 0 || jj >= Cc.nny || kk < 0 || kk >= Cc.nnz) continue;
+            const long long mm = ii + (long long)Cc.nnx * (jj + (long long)Cc.nny * kk);
+            for (int b = 0; b < DIM; ++b) row[DIM * mm + b] = __ldcg(Cc.C + (long long)((nb * DIM + ar) * DIM + b) * Cc.nnodes + n);
+          }
+        }
+      }
+    }
+    if (!sync_reduce(0)) return false;
+    // Cholesky A = L L^T on CTA 0 (lower triangle, in place); a non-positive pivot disables the
+    // coarse correction instead of failing the solve
+    if (rank == 0) {
+      if (threadIdx.x == 0) mg_okc = 1;
+      __syncthreads();
+      for (int k = 0; k < nc; ++k) {
+        if (threadIdx.x == 0) {
+          const double d = M.A[(size_t)k * nc + k];
+          if (!(d > 0.0) || !isfinite(d)) mg_okc = 0;
+          M.A[(size_t)k * nc + k] = mg_okc ? sqrt(d) : 1.0;
+        }
+        __syncthreads();
+        if (!mg_okc) break;
+        const double lkk = M.A[(size_t)k * nc + k];
+        for (int i = k + 1 + threadIdx.x; i < nc; i += blockDim.x) M.A[(size_t)i * nc + k] /= lkk;
+        __syncthreads();
+        const int mrem = nc - k - 1;
+        for (int t = threadIdx.x; t < mrem * mrem; t += blockDim.x) {
+          const int i = k + 1 + t / mrem, j = k + 1 + t % mrem;
+          if (j <= i) M.A[(size_t)i * nc + j] -= M.A[(size_t)i * nc + k] * M.A[(size_t)j * nc + k];
+        }
+        __syncthreads();
+      }
+      if (threadIdx.x == 0) *M.coarse_ok = mg_okc;
+    }
+    if (!sync_reduce(0)) return false;
+    // inverse: column q of A^-1 (= row q, A symmetric) by CTA q mod G, warp 0; y in shared memory
+    {
+      __shared__ double ycol[MG_COARSE_MAX];
+      const int ok = __ldcg(M.coarse_ok);
+      for (int q = rank; q < nc; q += G) {
+        if (warp == 0) {
+          for (int i = 0; i < nc; ++i) {  // L y = e_q
+            double t = 0.0;
+            if (ok && i >= q)
+              for (int p = q + lane; p < i; p += 32) t = fma(__ldcg(M.A + (size_t)i * nc + p), ycol[p], t);
+            t = warp_sum(t);
+            if (lane == 0) ycol[i] = (ok && i >= q) ? ((i == q ? 1.0 : 0.0) - t) / __ldcg(M.A + (size_t)i * nc + i) : 0.0;
+            __syncwarp();
+          }
+          for (int i = nc - 1; i >= 0; --i) {  // L^T x = y
+            double t = 0.0;
+            if (ok)
+              for (int p = i + 1 + lane; p < nc; p += 32) t = fma(__ldcg(M.A + (size_t)p * nc + i), ycol[p], t);
+            t = warp_sum(t);
+            if (lane == 0) ycol[i] = ok ? (ycol[i] - t) / __ldcg(M.A + (size_t)i * nc + i) : 0.0;
+            __syncwarp();
+          }
+          for (int i = lane; i < nc; i += 32) M.Ainv[(size_t)q * nc + i] = (float)ycol[i];
+          __syncwarp();
+        }
+      }
+    }
+    if (!sync_reduce(0)) return false;
+    // Chebyshev coefficients of every level (as in the polynomial preconditioner above)
+    if (warp < M.L) {
+      double lm = 0.0;
+      for (unsigned q = lane; q < G; q += 32) lm = fmax(lm, __ldcg(M.lmax + (size_t)warp * G + q));
+      for (int o = 16; o; o >>= 1) lm = fmax(lm, __shfl_xor_sync(0xffffffffu, lm, o));
+      if (lane == 0) {
+        if (!(lm > 0.0) || !isfinite(lm)) lm = 1.0;
+        lm *= 1.001;
+        const double lmin = lm / MG_RATIO;
+        const double th = 0.5 * (lm + lmin), de = 0.5 * (lm - lmin), sigma = th / de;
+        mg_ith[warp] = (float)(1.0 / th);
+        double ro = 1.0 / sigma;
+        for (int j = 1; j < M.deg; ++j) {
+          const double rn = 1.0 / (2.0 * sigma - ro);
+          mg_c1[warp][j] = (float)(rn * ro);
+          mg_c2[warp][j] = (float)(2.0 * rn / de);
+          ro = rn;
+        }
+      }
+    }
+    // exchange ranges of the levels run by all CTAs (0 .. ls - 1)
+    if (threadIdx.x < M.ls) {
+      const int l = threadIdx.x;
+      const MgLevel& Lv = M.lv[l];
+      const long long u0 = Lv.nunits * rank / G, u1 = Lv.nunits * (rank + 1) / G;
+      const long long ux = (Lv.nnx + 31) / 32;
+      if (u1 > u0) {
+        const long long sp = DIM == 2 ? ux + 1 : ux * Lv.nny + ux + 1;
+        mg_halo[l][0] = (int)mg_owner(max(0LL, u0 - sp), Lv.nunits, G);
+        mg_halo[l][1] = (int)mg_owner(min(Lv.nunits - 1, u1 - 1 + sp), Lv.nunits, G);
+        // first and last owned node positions
+        const int i0 = (int)(u0 % ux) * 32, j0 = (int)((u0 / ux) % Lv.nny), k0 = (int)(u0 / ux / Lv.nny);
+        const long long ul = u1 - 1;
+        const int i1 = min((int)(ul % ux) * 32 + 31, Lv.nnx - 1), j1 = (int)((ul / ux) % Lv.nny),
+                  k1 = (int)(ul / ux / Lv.nny);
+        if (l >= 1) {  // restriction from level l - 1: its owners of the fine support
+          const MgLevel& F = M.lv[l - 1];
+          const long long fmin = mg_unit(F, max(0, 2 * i0 - 2), max(0, 2 * j0 - 2), DIM == 3 ? max(0, 2 * k0 - 2) : 0);
+          const long long fmaxu = mg_unit(F, min(F.nnx - 1, 2 * i1 + 1), min(F.nny - 1, 2 * j1 + 1),
+                                          DIM == 3 ? min(F.nnz - 1, 2 * k1 + 1) : 0);
+          mg_rest[l][0] = (int)mg_owner(fmin, F.nunits, G);
+          mg_rest[l][1] = (int)mg_owner(fmaxu, F.nunits, G);
+        }
+        if (l + 1 < M.ls) {  // prolongation from level l + 1: its owners of the coarse parents
+          // parents of fine node i lie in [i / 2, i / 2 + 1]; a range of owned nodes that spans
+          // more than one row (plane) reaches whole coarse rows (planes), so the bounds take
+          // x from 0 to the row end (and y likewise when planes are spanned)
+          const MgLevel& Cc = M.lv[l + 1];
+          const bool planes = DIM == 3 && k1 > k0;
+          const long long cmin = mg_unit(Cc, 0, planes ? 0 : j0 / 2, DIM == 3 ? k0 / 2 : 0);
+          const long long cmaxu = mg_unit(Cc, Cc.nnx - 1, planes ? Cc.nny - 1 : min(Cc.nny - 1, j1 / 2 + 1),
+                                          DIM == 3 ? min(Cc.nnz - 1, k1 / 2 + 1) : 0);
+          mg_prol[l][0] = (int)mg_owner(cmin, Cc.nunits, G);
+          mg_prol[l][1] = (int)mg_owner(cmaxu, Cc.nunits, G);
+        } else {  // level ls is run by CTA 0
+          mg_prol[l][0] = mg_prol[l][1] = 0;
+        }
+      } else {
+        mg_halo[l][0] = mg_halo[l][1] = mg_rest[l][0] = mg_rest[l][1] = mg_prol[l][0] = mg_prol[l][1] = (int)rank;
+      }
+    }
+    __syncthreads();
+    return true;
+  };
+
   // --- stencil assembly and Jacobi diagonal ----------------------------------------------
   // With a polynomial preconditioner, also the Gershgorin bound max_i sum_j |K_ij| / K_ii of the
   // spectrum of D^-1 K (an upper bound, so the polynomial stays positive on the spectrum).
-  const int poly = POLY ? a.poly : 1;
+  const int poly = PK == 1 ? a.poly : 1;
+  // an FP32 preconditioner on an FP32 copy of the stencil; the multigrid solve drops to FP64
+  // Jacobi if its FP32 V-cycle stops being positive definite (r.z <= 0 or p.K p <= 0: only on
+  // designs whose conditioning is beyond FP32, e.g. near-void parts carrying load)
+  bool f32pre = PK == 2 || poly > 1;
+  if (threadIdx.x == 0) sh_fallback = 0;
   double gmax = 0.0;
   for_owned([&](int i, int j, int k, long long n) {
-    assemble_node<DIM>(g, a.ke, a.rho, i, j, k, n, a.C, poly > 1 ? a.C32 : nullptr);
+    assemble_node<DIM>(g, a.ke, a.rho, i, j, k, n, a.C, f32pre ? a.C32 : nullptr);
     const int centre = DIM == 2 ? 4 : 13;
 #pragma unroll
     for (int r = 0; r < DIM; ++r) {
       const double d = a.C[(long long)((centre * DIM + r) * DIM + r) * g.nnodes + n];
       a.dinv[DIM * n + r] = 1.0 / d;
-      if (poly > 1) {
+      if (f32pre) {
         a.dinv32[DIM * n + r] = (float)(1.0 / d);
         double rs = 0.0;
         for (int q = 0; q < StencilGeom<DIM>::NB * DIM; ++q) rs += fabs(a.C[(long long)(r * DIM + (q / DIM) * DIM * DIM + q % DIM) * g.nnodes + n]);
@@ -341,17 +531,23 @@ __device__ __forceinline__ void pcg2_body(const Pcg2Args<DIM>& a, const unsigned
       }
     }
   });
-  if (poly > 1) {
+  if (f32pre) {
     for (int o = 16; o; o >>= 1) gmax = fmax(gmax, __shfl_xor_sync(0xffffffffu, gmax, o));
     if (lane == 0) red[warp] = gmax;
     __syncthreads();
     if (threadIdx.x == 0) {
       double bm = 0.0;
       for (int q = 0; q < nwarps; ++q) bm = fmax(bm, red[q]);
-      *P(0, 0) = bm;
+      if (PK == 2)
+        a.mg.lmax[rank] = bm;  // level 0
+      else
+        *P(0, 0) = bm;
     }
   }
   if (!sync_reduce(0)) return;
+  if constexpr (PK == 2) {
+    if (!mg_setup()) return;
+  }
   if (poly > 1) {
     // Chebyshev iteration for D^-1 K z = D^-1 r on [lmax / ratio, lmax], from z = 0, poly steps:
     // z_0 = b / theta, then d_j = c1_j d_{j-1} + c2_j res_{j-1}, z_j = z_{j-1} + d_j, with
@@ -446,6 +642,317 @@ __device__ __forceinline__ void pcg2_body(const Pcg2Args<DIM>& a, const unsigned
     return true;
   };
 
+  // --- multigrid V-cycle z = M r (PK == 2) ---------------------------------------------------
+  // Levels 0 .. ls - 1 are split over all G CTAs like level 0 (units of 32 nodes of an x-row);
+  // every step that reads neighbouring nodes first waits for the CTAs that own them to publish
+  // the previous step (per-CTA release flags, as the z halo of phase W). Levels ls .. L - 1
+  // (small) run on CTA 0 alone with block barriers. Every vector slot is written once per
+  // V-cycle, and V-cycles are separated by the CG's grid barrier, so no step overwrites data a
+  // slower neighbour still reads.
+  auto wait_seq = [&](long long lo, long long hi, unsigned long long seq) -> bool {
+    if (threadIdx.x == 0) s_okw = 1;
+    __syncthreads();
+    for (long long q = lo + threadIdx.x; q <= hi; q += blockDim.x) {
+      if (q == (long long)rank) continue;
+      cuda::atomic_ref<unsigned long long, cuda::thread_scope_device> f(a.zflag[q]);
+      const long long t0 = clock64();
+      while (f.load(cuda::memory_order_acquire) < seq) {
+        if (*(volatile int*)&gb->abort) {
+          s_okw = 0;
+          break;
+        }
+        if (clock64() - t0 > a.wait_cycles) {
+          atomicCAS(&gs->status, 0, (int)TOPO_ERR_TIMEOUT);
+          atomicExch(&gb->abort, 1);
+          s_okw = 0;
+          break;
+        }
+      }
+    }
+    __syncthreads();
+    return s_okw != 0;
+  };
+  auto for_lv = [&](int l, bool single, auto fn) {
+    const MgLevel& Lv = a.mg.lv[l];
+    long long lo = 0, hi = Lv.nunits;
+    if (single) {
+      if (rank != 0) return;
+    } else {
+      lo = Lv.nunits * rank / G;
+      hi = Lv.nunits * (rank + 1) / G;
+    }
+    const int ux = (Lv.nnx + 31) / 32;
+    for (long long u = lo + warp; u < hi; u += nwarps) {
+      const int i = (int)(u % ux) * 32 + lane;
+      const long long r = u / ux;
+      const int j = (int)(r % Lv.nny), k = (int)(r / Lv.nny);
+      if (i >= Lv.nnx) continue;
+      fn(i, j, k, i + (long long)Lv.nnx * (j + (long long)Lv.nny * k));
+    }
+  };
+  auto mgv = [&](int l, int slot, int c) -> float* {
+    const MgLevel& Lv = a.mg.lv[l];
+    return Lv.v + ((size_t)slot * m + c) * Lv.ndof;
+  };
+  auto colskip = [&](bool all_cols, int c) -> bool { return !all_cols && sh_done[c]; };
+  // b at coarse node (I, J, K) of level l = P^T r of level l - 1 (its residual slot)
+  auto restrict_node = [&](int l, const float* src, int I, int J, int K, float* out) {
+    const MgLevel& F = a.mg.lv[l - 1];
+#pragma unroll
+    for (int q = 0; q < DIM; ++q) out[q] = 0.f;
+    const int px = mg_pos(I, F.nnx), py = mg_pos(J, F.nny), pz = DIM == 3 ? mg_pos(K, F.nnz) : 0;
+    for (int iz = (DIM == 3 ? max(pz - 1, 0) : 0); iz <= (DIM == 3 ? min(pz + 1, F.nnz - 1) : 0); ++iz) {
+      const float wz = DIM == 3 ? mg_w1(iz, K, F.nnz) : 1.f;
+      if (wz == 0.f) continue;
+      for (int iy = max(py - 1, 0); iy <= min(py + 1, F.nny - 1); ++iy) {
+        const float wy = mg_w1(iy, J, F.nny) * wz;
+        if (wy == 0.f) continue;
+        for (int ix = max(px - 1, 0); ix <= min(px + 1, F.nnx - 1); ++ix) {
+          const float w = mg_w1(ix, I, F.nnx) * wy;
+          if (w == 0.f) continue;
+          const long long ni = ix + (long long)F.nnx * (iy + (long long)F.nny * iz);
+#pragma unroll
+          for (int q = 0; q < DIM; ++q) out[q] = fmaf(w, __ldcg(src + DIM * ni + q), out[q]);
+        }
+      }
+    }
+  };
+  // (P x_c) at fine node (i, j, k) of level l from level l + 1
+  auto prolong_node = [&](int l, const float* src, int i, int j, int k, float* out) {
+    const MgLevel& F = a.mg.lv[l];
+    const MgLevel& Cc = a.mg.lv[l + 1];
+#pragma unroll
+    for (int q = 0; q < DIM; ++q) out[q] = 0.f;
+    for (int Kz = (DIM == 3 ? k / 2 : 0); Kz <= (DIM == 3 ? min(k / 2 + 1, Cc.nnz - 1) : 0); ++Kz) {
+      const float wz = DIM == 3 ? mg_w1(k, Kz, F.nnz) : 1.f;
+      if (wz == 0.f) continue;
+      for (int Jy = j / 2; Jy <= min(j / 2 + 1, Cc.nny - 1); ++Jy) {
+        const float wy = mg_w1(j, Jy, F.nny) * wz;
+        if (wy == 0.f) continue;
+        for (int Ix = i / 2; Ix <= min(i / 2 + 1, Cc.nnx - 1); ++Ix) {
+          const float w = mg_w1(i, Ix, F.nnx) * wy;
+          if (w == 0.f) continue;
+          const long long mc = Ix + (long long)Cc.nnx * (Jy + (long long)Cc.nny * Kz);
+#pragma unroll
+          for (int q = 0; q < DIM; ++q) out[q] = fmaf(w, __ldcg(src + DIM * mc + q), out[q]);
+        }
+      }
+    }
+  };
+  auto fixed_lv = [&](int l, long long dof) -> bool {
+    return l == 0 ? is_fixed(g, dof) : __ldcg(a.mg.lv[l].fix + dof) != 0;
+  };
+  // right-hand side of level l at a DOF: the CG residual (level 0) or the restricted residual
+  auto rhs = [&](int l, int c, long long dof) -> float {
+    return l == 0 ? (float)a.r[(size_t)c * N + dof] : __ldcg(mgv(l, mg_slot_b(a.mg.deg), c) + dof);
+  };
+  // pre-smoothing step 0 (from zero): x_0 = D^-1 b / theta; for l >= 1 b is restricted first
+  auto mg_pre0 = [&](int l, bool single, bool all_cols) {
+    const MgLevel& Lv = a.mg.lv[l];
+    const float ith = mg_ith[l];
+    for (int c = 0; c < m; ++c) {
+      if (colskip(all_cols, c)) continue;
+      float* x0 = mgv(l, 0, c);
+      float* bb = mgv(l, mg_slot_b(a.mg.deg), c);
+      const float* r2f = l ? mgv(l - 1, mg_slot_res(a.mg.deg), c) : nullptr;
+      for_lv(l, single, [&](int i, int j, int k, long long n) {
+        float b[DIM];
+        if (l == 0) {
+#pragma unroll
+          for (int q = 0; q < DIM; ++q) b[q] = (float)a.r[(size_t)c * N + DIM * n + q];
+        } else {
+          restrict_node(l, r2f, i, j, k, b);
+#pragma unroll
+          for (int q = 0; q < DIM; ++q) bb[DIM * n + q] = b[q];
+        }
+#pragma unroll
+        for (int q = 0; q < DIM; ++q) x0[DIM * n + q] = __ldcg(Lv.dinv + DIM * n + q) * b[q] * ith;
+      });
+    }
+  };
+  // pre-smoothing step jj >= 1: x_jj = x_{jj-1} + c1 (x_{jj-1} - x_{jj-2}) + c2 D^-1 (b - K x_{jj-1})
+  auto mg_pre = [&](int l, int jj, bool single, bool all_cols) {
+    const MgLevel& Lv = a.mg.lv[l];
+    const Grid gl = mg_grid(g, Lv);
+    const float c1 = mg_c1[l][jj], c2 = mg_c2[l][jj];
+    for (int c = 0; c < m; ++c) {
+      if (colskip(all_cols, c)) continue;
+      const float* xin = mgv(l, jj - 1, c);
+      const float* xpp = jj >= 2 ? mgv(l, jj - 2, c) : nullptr;
+      float* xout = mgv(l, jj, c);
+      for_lv(l, single, [&](int i, int j, int k, long long n) {
+        float y[DIM], own[DIM];
+        stencil_apply32<DIM>(gl, Lv.C32, xin, i, j, k, n, y, own);
+#pragma unroll
+        for (int q = 0; q < DIM; ++q) {
+          const long long dof = DIM * n + q;
+          const float prev = xpp ? __ldcg(xpp + dof) : 0.f;
+          const float d = fmaf(c1, own[q] - prev, c2 * __ldcg(Lv.dinv + dof) * (rhs(l, c, dof) - y[q]));
+          xout[dof] = own[q] + d;
+        }
+      });
+    }
+  };
+  // residual after pre-smoothing: r = b - K x_{deg-1}
+  auto mg_res = [&](int l, bool single, bool all_cols) {
+    const MgLevel& Lv = a.mg.lv[l];
+    const Grid gl = mg_grid(g, Lv);
+    for (int c = 0; c < m; ++c) {
+      if (colskip(all_cols, c)) continue;
+      const float* xin = mgv(l, a.mg.deg - 1, c);
+      float* res = mgv(l, mg_slot_res(a.mg.deg), c);
+      for_lv(l, single, [&](int i, int j, int k, long long n) {
+        float y[DIM], own[DIM];
+        stencil_apply32<DIM>(gl, Lv.C32, xin, i, j, k, n, y, own);
+#pragma unroll
+        for (int q = 0; q < DIM; ++q) res[DIM * n + q] = rhs(l, c, DIM * n + q) - y[q];
+      });
+    }
+  };
+  // coarse correction: y_0 = x_{deg-1} + P x_coarse (no correction on identity rows)
+  auto mg_post0 = [&](int l, bool single, bool all_cols) {
+    const int deg = a.mg.deg;
+    for (int c = 0; c < m; ++c) {
+      if (colskip(all_cols, c)) continue;
+      const float* xc = (l + 1 == a.mg.L - 1) ? mgv(l + 1, 0, c) : mgv(l + 1, mg_slot_post(deg, deg), c);
+      const float* xin = mgv(l, deg - 1, c);
+      float* y0 = mgv(l, mg_slot_post(deg, 0), c);
+      for_lv(l, single, [&](int i, int j, int k, long long n) {
+        float p[DIM];
+        prolong_node(l, xc, i, j, k, p);
+#pragma unroll
+        for (int q = 0; q < DIM; ++q) {
+          const long long dof = DIM * n + q;
+          y0[dof] = __ldcg(xin + dof) + (fixed_lv(l, dof) ? 0.f : p[q]);
+        }
+      });
+    }
+  };
+  // post-smoothing step jj (0 .. deg-1): y_{jj+1} from y_jj (and y_{jj-1}); the last step of
+  // level 0 writes z (FP64) and accumulates r.z per thread
+  auto mg_post = [&](int l, int jj, bool single, bool all_cols) {
+    const MgLevel& Lv = a.mg.lv[l];
+    const Grid gl = mg_grid(g, Lv);
+    const int deg = a.mg.deg;
+    const float ith = mg_ith[l];
+    const float c1 = jj ? mg_c1[l][jj] : 0.f, c2 = jj ? mg_c2[l][jj] : 0.f;
+    const bool last0 = l == 0 && jj == deg - 1;
+    for (int c = 0; c < m; ++c) {
+      if (colskip(all_cols, c)) continue;
+      const float* yin = mgv(l, mg_slot_post(deg, jj), c);
+      const float* yprev = jj ? mgv(l, mg_slot_post(deg, jj - 1), c) : nullptr;
+      float* yout = last0 ? nullptr : mgv(l, mg_slot_post(deg, jj + 1), c);
+      double ag = 0.0;
+      for_lv(l, single, [&](int i, int j, int k, long long n) {
+        float y[DIM], own[DIM];
+        stencil_apply32<DIM>(gl, Lv.C32, yin, i, j, k, n, y, own);
+#pragma unroll
+        for (int q = 0; q < DIM; ++q) {
+          const long long dof = DIM * n + q;
+          const float dr = __ldcg(Lv.dinv + dof) * (rhs(l, c, dof) - y[q]);
+          const float d = jj ? fmaf(c1, own[q] - __ldcg(yprev + dof), c2 * dr) : dr * ith;
+          const float out = own[q] + d;
+          if (last0) {
+            const double zd = (double)out;
+            const size_t o = (size_t)c * N + dof;
+            a.z[o] = zd;
+            ag = fma(a.r[o], zd, ag);
+          } else {
+            yout[dof] = out;
+          }
+        }
+      });
+      if (last0) accg[c] = ag;
+    }
+  };
+  // coarsest level on CTA 0: b = P^T r (restricted), x = A^-1 b (dense, one warp per row)
+  auto mg_coarsest = [&](bool all_cols) {
+    const int l = a.mg.L - 1, nc = a.mg.nc, deg = a.mg.deg;
+    for (int c = 0; c < m; ++c) {
+      if (colskip(all_cols, c)) continue;
+      float* bc = mgv(l, mg_slot_b(deg), c);
+      const float* r2f = mgv(l - 1, mg_slot_res(deg), c);
+      for_lv(l, true, [&](int i, int j, int k, long long n) {
+        float b[DIM];
+        restrict_node(l, r2f, i, j, k, b);
+#pragma unroll
+        for (int q = 0; q < DIM; ++q) bc[DIM * n + q] = b[q];
+      });
+    }
+    __syncthreads();
+    for (int c = 0; c < m; ++c) {
+      if (colskip(all_cols, c)) continue;
+      const float* bc = mgv(l, mg_slot_b(deg), c);
+      float* xs = mgv(l, 0, c);
+      for (int row = warp; row < nc; row += nwarps) {
+        float t = 0.f;
+        for (int q = lane; q < nc; q += 32) t = fmaf(__ldcg(a.mg.Ainv + (size_t)row * nc + q), __ldcg(bc + q), t);
+        for (int o = 16; o; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0) xs[row] = t;
+      }
+    }
+    __syncthreads();
+  };
+  auto mg_vcycle = [&](bool all_cols) -> bool {
+    const int deg = a.mg.deg, L = a.mg.L, ls = a.mg.ls;
+    unsigned long long seq_res[MG_MAX_LEVELS], seq_out[MG_MAX_LEVELS];
+    for (int c = 0; c < m; ++c) accg[c] = 0.0;
+    for (int l = 0; l < ls; ++l) {  // descend (all CTAs)
+      if (l >= 1 && !wait_seq(mg_rest[l][0], mg_rest[l][1], seq_res[l - 1])) return false;
+      mg_pre0(l, false, all_cols);
+      publish_z();
+      for (int jj = 1; jj < deg; ++jj) {
+        if (!wait_seq(mg_halo[l][0], mg_halo[l][1], zseq)) return false;
+        mg_pre(l, jj, false, all_cols);
+        publish_z();
+      }
+      if (!wait_seq(mg_halo[l][0], mg_halo[l][1], zseq)) return false;
+      mg_res(l, false, all_cols);
+      publish_z();
+      seq_res[l] = zseq;
+    }
+    bool ok = true;
+    if (rank == 0) {  // levels ls .. L - 1 on CTA 0
+      ok = wait_seq(0, (long long)G - 1, seq_res[ls - 1]);
+      if (ok) {
+        for (int l = ls; l < L - 1; ++l) {
+          mg_pre0(l, true, all_cols);
+          __syncthreads();
+          for (int jj = 1; jj < deg; ++jj) {
+            mg_pre(l, jj, true, all_cols);
+            __syncthreads();
+          }
+          mg_res(l, true, all_cols);
+          __syncthreads();
+        }
+        mg_coarsest(all_cols);
+        for (int l = L - 2; l >= ls; --l) {
+          mg_post0(l, true, all_cols);
+          __syncthreads();
+          for (int jj = 0; jj < deg; ++jj) {
+            mg_post(l, jj, true, all_cols);
+            __syncthreads();
+          }
+        }
+      }
+    }
+    if (!ok) return false;
+    publish_z();
+    const unsigned long long seq_tail = zseq;
+    for (int l = ls - 1; l >= 0; --l) {  // ascend (all CTAs)
+      if (!wait_seq(mg_prol[l][0], mg_prol[l][1], l + 1 == ls ? seq_tail : seq_out[l + 1])) return false;
+      mg_post0(l, false, all_cols);
+      publish_z();
+      for (int jj = 0; jj < deg; ++jj) {
+        if (!wait_seq(mg_halo[l][0], mg_halo[l][1], zseq)) return false;
+        mg_post(l, jj, false, all_cols);
+        publish_z();
+      }
+      seq_out[l] = zseq;
+    }
+    return true;
+  };
+
   // --- true residual r = f - K x, z = D^-1 r -----------------------------------------------
   // r, z for owned nodes (x = caller's U, Dirichlet entries zeroed), partial gamma, r.r, f.f,
   // (|K||x|)^2; one barrier (it also publishes z to every CTA).
@@ -473,7 +980,7 @@ __device__ __forceinline__ void pcg2_body(const Pcg2Args<DIM>& a, const unsigned
             x[dof] = 0.0;  // Dirichlet entries of the solution are zero (their columns are zero)
           }
           a.r[c * N + dof] = rv;
-          if (poly == 1) {
+          if (!f32pre) {
             const double zv = __ldcg(a.dinv + dof) * rv;
             a.z[c * N + dof] = zv;
             t0 = fma(rv, zv, t0);
@@ -485,8 +992,8 @@ __device__ __forceinline__ void pcg2_body(const Pcg2Args<DIM>& a, const unsigned
       acc[2][c] = t2;
       acc[3][c] = t3;
     }
-    if (poly > 1) {  // z = p(D^-1 K) D^-1 r: needs every CTA's r complete, and so its own halo steps
-      if (!precond(true)) return false;
+    if (f32pre) {  // z = p(D^-1 K) D^-1 r or the V-cycle: their halo steps need every CTA's r
+      if (!(PK == 2 ? mg_vcycle(true) : precond(true))) return false;
       for (int c = 0; c < m; ++c) acc[0][c] = accg[c];
     }
     for (int c = 0; c < m; ++c)
@@ -529,7 +1036,7 @@ __device__ __forceinline__ void pcg2_body(const Pcg2Args<DIM>& a, const unsigned
   // 1,658 with the flexible choice -alpha_old e / gamma_old).
   auto phase_w = [&](bool restart) -> bool {
     if (!restart && !wait_z()) return false;
-    const bool flex = poly > 1;
+    const bool flex = f32pre;
     double acc[P2_MAX_COLS], acce[P2_MAX_COLS], accf[P2_MAX_COLS];  // per column
     for (int c = 0; c < m; ++c) acc[c] = acce[c] = accf[c] = 0.0;
     for (int c = 0; c < m; ++c) {
@@ -594,8 +1101,12 @@ __device__ __forceinline__ void pcg2_body(const Pcg2Args<DIM>& a, const unsigned
           }
           sh_alpha[c] = sh_gamma[c] / sh_den[c];
           if (!(sh_alpha[c] > 0.0) || !isfinite(sh_alpha[c])) {
-            set_status(&gs->status, TOPO_ERR_NOT_SPD);
-            sh_done[c] = 1;
+            if (PK == 2 && !sh_fallback) {
+              sh_fallback = 1;  // restart from the true residual with Jacobi
+            } else {
+              set_status(&gs->status, TOPO_ERR_NOT_SPD);
+              sh_done[c] = 1;
+            }
           }
           continue;
         }
@@ -631,7 +1142,7 @@ __device__ __forceinline__ void pcg2_body(const Pcg2Args<DIM>& a, const unsigned
   // the polynomial preconditioner; per-thread gamma = r.z and r.r (reduced by the next phase W);
   // then z is published to the neighbours.
   auto phase_u = [&](bool restart) -> bool {
-    const bool jac = poly == 1;
+    const bool jac = !f32pre;
     for (int c = 0; c < m; ++c) accg[c] = accr[c] = 0.0;
     for (int c = 0; c < m; ++c) {
       if (sh_done[c]) continue;
@@ -695,9 +1206,15 @@ __device__ __forceinline__ void pcg2_body(const Pcg2Args<DIM>& a, const unsigned
       accg[c] = ag;
       accr[c] = ar;
     }
-    if (!jac && !precond(false)) return false;
-    publish_z();
-    return true;
+    if constexpr (PK == 2) {
+      if (f32pre) return mg_vcycle(false);  // publishes z as its last step
+      publish_z();
+      return true;
+    } else {
+      if (!jac && !precond(false)) return false;
+      publish_z();
+      return true;
+    }
   };
 
   int iters = 0;
@@ -709,6 +1226,10 @@ __device__ __forceinline__ void pcg2_body(const Pcg2Args<DIM>& a, const unsigned
     bool restart = true;
     while (true) {
       if (!phase_w(restart)) return;
+      if (PK == 2 && f32pre && sh_fallback) {
+        f32pre = false;  // every CTA reduced the same values: all switch here
+        break;
+      }
       bool any = false;
       for (int c = 0; c < m; ++c) any = any || !sh_done[c];
       if (!any || iters >= a.maxit) break;
@@ -732,14 +1253,20 @@ __device__ __forceinline__ void pcg2_body(const Pcg2Args<DIM>& a, const unsigned
     a.info[0] = iters;
     a.info[1] = 0;
     a.info[2] = conv ? 0 : TOPO_ERR_NOT_CONVERGED;
-    a.info[3] = 0;
+    a.info[3] = (PK == 2 && !f32pre) ? 1 : 0;  // multigrid fell back to Jacobi
     a.info_rr[0] = worst;
   }
 }
 
 template <int DIM>
 __global__ void __launch_bounds__(P2_THREADS_SOLO, 1) pcg2_kernel(const __grid_constant__ Pcg2Args<DIM> a) {
-  pcg2_body<DIM, true>(a, gridDim.x, blockIdx.x, a.gb);
+  pcg2_body<DIM, 1>(a, gridDim.x, blockIdx.x, a.gb);
+}
+
+// The same solver with the multigrid V-cycle as its preconditioner.
+template <int DIM>
+__global__ void __launch_bounds__(P2_THREADS_SOLO, 1) pcg2_mg_kernel(const __grid_constant__ Pcg2Args<DIM> a) {
+  pcg2_body<DIM, 2>(a, gridDim.x, blockIdx.x, a.gb);
 }
 
 // Batched form: CTA b works on instance cta_inst[b] as number cta_rank[b] of that instance's
@@ -751,14 +1278,14 @@ __global__ void __launch_bounds__(P2_THREADS, 4) pcg2_batch_kernel(const Pcg2Arg
                                                                 const int* __restrict__ cta_rank,
                                                                 const int* __restrict__ grp_size) {
   const int inst = cta_inst[blockIdx.x];
-  pcg2_body<DIM, false>(args[inst], (unsigned)grp_size[inst], (unsigned)cta_rank[blockIdx.x], args[inst].gb);
+  pcg2_body<DIM, 0>(args[inst], (unsigned)grp_size[inst], (unsigned)cta_rank[blockIdx.x], args[inst].gb);
 }
 template __global__ void pcg2_batch_kernel<2>(const Pcg2Args<2>*, const int*, const int*, const int*);
 
 
 template <int DIM>
 topo_status build_pcg2_args(topo_ctx* c, const double* rho, const double* F, double* U, int m, int ld, double rtol,
-                            int maxit, int G, Pcg2Args<DIM>* out, GridSync* status, int poly) {
+                            int maxit, int G, Pcg2Args<DIM>* out, GridSync* status, int poly, bool mg) {
   const Grid& g = c->g;
   const long long N = g.ndof;
   size_t off = 0;
@@ -771,11 +1298,69 @@ topo_status build_pcg2_args(topo_ctx* c, const double* rho, const double* F, dou
   size_t ov[5];
   for (int t = 0; t < 5; ++t) ov[t] = take(N * m * 8);
   size_t oC32 = 0, oD32 = 0, of[4] = {0, 0, 0, 0};
-  if (poly > 1) {  // FP32 stencil, D^-1 and the four vectors of the polynomial preconditioner
+  if (poly > 1 || mg) {  // FP32 stencil and D^-1 (the FP32 preconditioners)
     oC32 = take((size_t)StencilGeom<DIM>::NC * g.nnodes * 4);
     oD32 = take(N * 4);
-    for (int t = 0; t < 4; ++t) of[t] = take(N * m * 4);
   }
+  if (poly > 1)  // the four vectors of the polynomial preconditioner
+    for (int t = 0; t < 4; ++t) of[t] = take(N * m * 4);
+  // multigrid levels: sizes, then FP64/FP32 stencils, D^-1, identity-row flags and V-cycle
+  // vectors of every level, the dense coarsest operator and its inverse
+  MgArgs mga = {};
+  size_t omg[MG_MAX_LEVELS][5] = {};
+  size_t oA = 0, oAi = 0, olm = 0, ook = 0;
+  if (mg) {
+    const int deg = c->mg_deg;
+    int nn[3] = {g.nnx, g.nny, g.nnz};
+    int L = 0;
+    while (true) {
+      MgLevel& Lv = mga.lv[L];
+      Lv.nnx = nn[0];
+      Lv.nny = nn[1];
+      Lv.nnz = nn[2];
+      Lv.nnodes = (long long)nn[0] * nn[1] * nn[2];
+      Lv.ndof = DIM * Lv.nnodes;
+      Lv.nunits = (long long)((nn[0] + 31) / 32) * nn[1] * nn[2];
+      ++L;
+      const int nx2 = mg_coarse_n(nn[0]), ny2 = mg_coarse_n(nn[1]), nz2 = DIM == 3 ? mg_coarse_n(nn[2]) : 1;
+      const bool shrinks = nx2 < nn[0] || ny2 < nn[1] || nz2 < nn[2];
+      if (Lv.ndof <= MG_COARSE_MAX || !shrinks || L == MG_MAX_LEVELS) break;
+      nn[0] = nx2;
+      nn[1] = ny2;
+      nn[2] = nz2;
+    }
+    mga.L = L;
+    mga.deg = deg;
+    mga.nc = (int)mga.lv[L - 1].ndof;
+    if (L >= 2 && mga.nc <= MG_COARSE_MAX) {
+      // levels from the first with at most mg_single_nodes nodes run on CTA 0 (level 0 never)
+      int ls = L - 1;
+      for (int l = 1; l < L; ++l)
+        if (mga.lv[l].nnodes <= c->mg_single_nodes) {
+          ls = l;
+          break;
+        }
+      mga.ls = ls;
+      for (int l = 0; l < L; ++l) {
+        const MgLevel& Lv = mga.lv[l];
+        if (l > 0) {
+          omg[l][0] = take((size_t)StencilGeom<DIM>::NC * Lv.nnodes * 8);
+          omg[l][1] = take((size_t)StencilGeom<DIM>::NC * Lv.nnodes * 4);
+          omg[l][2] = take((size_t)Lv.ndof * 4);
+          omg[l][3] = take((size_t)Lv.ndof);
+        }
+        omg[l][4] = take((size_t)mg_slots(deg) * m * Lv.ndof * 4);
+      }
+      oA = take((size_t)mga.nc * mga.nc * 8);
+      oAi = take((size_t)mga.nc * mga.nc * 4);
+      olm = take((size_t)MG_MAX_LEVELS * G * 8);
+      ook = take(16);
+    } else {
+      mg = false;  // a mesh too small to coarsen: the polynomial / Jacobi path
+      mga.L = 0;
+    }
+  }
+
   const size_t opart = take(sizeof(double) * 2 * P2_SLOTS * m * G), oflag = take(sizeof(unsigned long long) * G),
                oinfo = take(64);
   topo_status st = ensure_scratch(c, off);
@@ -800,9 +1385,31 @@ topo_status build_pcg2_args(topo_ctx* c, const double* rho, const double* F, dou
   for (int t = 0; t < 5; ++t) *vecs[t] = (double*)(base + ov[t]);
   float** fvecs[4] = {&a.t0, &a.t1, &a.res, &a.z32};
   for (int t = 0; t < 4; ++t) *fvecs[t] = poly > 1 ? (float*)(base + of[t]) : nullptr;
-  a.C32 = poly > 1 ? (float*)(base + oC32) : nullptr;
-  a.dinv32 = poly > 1 ? (float*)(base + oD32) : nullptr;
+  a.C32 = (poly > 1 || mg) ? (float*)(base + oC32) : nullptr;
+  a.dinv32 = (poly > 1 || mg) ? (float*)(base + oD32) : nullptr;
   a.poly = poly > 1 ? poly : 1;
+  a.mg = mga;
+  if (mg) {
+    for (int l = 0; l < mga.L; ++l) {
+      MgLevel& Lv = a.mg.lv[l];
+      if (l == 0) {
+        Lv.C = a.C;
+        Lv.C32 = a.C32;
+        Lv.dinv = a.dinv32;
+        Lv.fix = nullptr;
+      } else {
+        Lv.C = (double*)(base + omg[l][0]);
+        Lv.C32 = (float*)(base + omg[l][1]);
+        Lv.dinv = (float*)(base + omg[l][2]);
+        Lv.fix = (unsigned char*)(base + omg[l][3]);
+      }
+      Lv.v = (float*)(base + omg[l][4]);
+    }
+    a.mg.A = (double*)(base + oA);
+    a.mg.Ainv = (float*)(base + oAi);
+    a.mg.lmax = (double*)(base + olm);
+    a.mg.coarse_ok = (int*)(base + ook);
+  }
   a.cheb_ratio = 100.0;  // interval [lambda_max / 100, lambda_max]
   a.partial = (double*)(base + opart);
   a.zflag = (unsigned long long*)(base + oflag);
@@ -844,8 +1451,12 @@ topo_status solve_stencil_fp64(topo_ctx* c, const double* rho, const double* F, 
                                int maxit, topo_solve_info* info_host) {
   const Grid& g = c->g;
   const long long nunits = (long long)((g.nnx + 31) / 32) * g.nny * g.nnz;
+  const bool want_mg = c->pcg_mg != 0;
   int occ = 0;
-  TOPO_CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pcg2_kernel<DIM>, P2_THREADS_SOLO, 0));
+  if (want_mg)
+    TOPO_CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pcg2_mg_kernel<DIM>, P2_THREADS_SOLO, 0));
+  else
+    TOPO_CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pcg2_kernel<DIM>, P2_THREADS_SOLO, 0));
   if (occ < 1) return fail(c, TOPO_ERR_CUDA, "pcg2 kernel cannot be resident");
   const int per_sm = c->pcg_blocks_per_sm > 0 ? std::min(c->pcg_blocks_per_sm, occ) : std::min(occ, 2);
   long long G = (long long)per_sm * c->num_sms;
@@ -854,8 +1465,13 @@ topo_status solve_stencil_fp64(topo_ctx* c, const double* rho, const double* F, 
   if (G > maxG) G = std::max(1LL, maxG);
   Pcg2Args<DIM> a;
   const int poly = c->pcg_poly > 0 ? c->pcg_poly : pcg_poly_auto(DIM);
-  topo_status st = build_pcg2_args<DIM>(c, rho, F, U, m, ld, rtol, maxit, (int)G, &a, c->d_sync, poly);
+  topo_status st = build_pcg2_args<DIM>(c, rho, F, U, m, ld, rtol, maxit, (int)G, &a, c->d_sync, poly, want_mg);
   if (st) return st;
+  const bool use_mg = want_mg && a.mg.L >= 2;  // a mesh too small to coarsen keeps the polynomial
+  if (want_mg && !use_mg) {
+    st = build_pcg2_args<DIM>(c, rho, F, U, m, ld, rtol, maxit, (int)G, &a, c->d_sync, poly, false);
+    if (st) return st;
+  }
   TOPO_CUDA_TRY(c, cudaMemsetAsync(c->d_bar, 0, sizeof(GridBar), c->stream));  // counter, generation, abort
   TOPO_CUDA_TRY(c, cudaMemsetAsync(a.zflag, 0, sizeof(unsigned long long) * G, c->stream));
   TOPO_CUDA_TRY(c, cudaMemsetAsync(a.info, 0, 32, c->stream));
@@ -868,7 +1484,10 @@ topo_status solve_stencil_fp64(topo_ctx* c, const double* rho, const double* F, 
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  TOPO_CUDA_TRY(c, cudaLaunchKernelEx(&cfg, pcg2_kernel<DIM>, a));
+  if (use_mg)
+    TOPO_CUDA_TRY(c, cudaLaunchKernelEx(&cfg, pcg2_mg_kernel<DIM>, a));
+  else
+    TOPO_CUDA_TRY(c, cudaLaunchKernelEx(&cfg, pcg2_kernel<DIM>, a));
   note_launch();
   if (info_host) {
     int hinfo[4];
@@ -882,7 +1501,9 @@ topo_status solve_stencil_fp64(topo_ctx* c, const double* rho, const double* F, 
     info_host->outer = 0;
     info_host->relres = sqrt(hrr[0]);
     info_host->floor = sqrt(hrr[1]);
-    info_host->poly = a.poly;
+    info_host->poly = use_mg ? (hinfo[3] ? 1 : 0) : a.poly;
+    info_host->mg_levels = use_mg ? a.mg.L : 0;
+    info_host->fallback = use_mg ? hinfo[3] : 0;
     info_host->status = dev_status ? dev_status : hinfo[2];
     if (dev_status) {
       int zero = 0;
@@ -904,4 +1525,4 @@ template topo_status solve_stencil_fp64<3>(topo_ctx*, const double*, const doubl
 }  // namespace topo
 
 template topo_status topo::build_pcg2_args<2>(topo_ctx*, const double*, const double*, double*, int, int, double, int,
-                                              int, topo::Pcg2Args<2>*, topo::GridSync*, int);
+                                              int, topo::Pcg2Args<2>*, topo::GridSync*, int, bool);

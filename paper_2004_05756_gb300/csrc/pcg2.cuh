@@ -2,6 +2,7 @@
 #pragma once
 
 #include "common.cuh"
+#include "mg.cuh"
 
 namespace topo {
 
@@ -38,6 +39,7 @@ struct Pcg2Args {
   float* z32;        //   the accumulated result; N x m
   int poly;          // degree of the preconditioner polynomial in D^-1 K (1 = Jacobi)
   double cheb_ratio; // its Chebyshev interval: [lambda_max / cheb_ratio, lambda_max]
+  MgArgs mg;         // multigrid preconditioner (the multigrid kernel only)
   double* partial;   // [2 barrier parities][P2_SLOTS slots][m][G]
   unsigned long long* zflag;  // [G]: phase-U completions of each CTA (z published), reset per launch
   GridSync* gs;      // sticky status
@@ -65,7 +67,7 @@ cudaError_t launch_pcg2_batch2(unsigned ctas, cudaStream_t stream, const Pcg2Arg
 // vectors); the batched solve uses 1.
 template <int DIM>
 topo_status build_pcg2_args(topo_ctx* c, const double* rho, const double* F, double* U, int m, int ld, double rtol,
-                            int maxit, int G, Pcg2Args<DIM>* out, GridSync* status, int poly = 1);
+                            int maxit, int G, Pcg2Args<DIM>* out, GridSync* status, int poly = 1, bool mg = false);
 
 // Resident CTAs per SM of the batched kernel.
 int pcg2_occupancy();

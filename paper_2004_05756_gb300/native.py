@@ -21,7 +21,8 @@ TOPO_FP64, TOPO_FP32_REFINED, TOPO_FP32_BF16KE_REFINED = 0, 1, 2
 PREC = {"fp64": TOPO_FP64, "fp32": TOPO_FP32_REFINED, "fp32_bf16ke": TOPO_FP32_BF16KE_REFINED}
 (TOPO_PARAM_INNER_RTOL, TOPO_PARAM_MAX_OUTER, TOPO_PARAM_WAIT_CYCLES, TOPO_PARAM_ROM_REFINE,
  TOPO_PARAM_TILE_X, TOPO_PARAM_PCG_BLOCKS_PER_SM, TOPO_PARAM_INNER_CAP, TOPO_PARAM_HDM_KERNEL,
- TOPO_PARAM_PCG_MAX_CTAS, TOPO_PARAM_ROM_TENSOR, TOPO_PARAM_APPLY_STAGES, TOPO_PARAM_PCG_POLY) = range(12)
+ TOPO_PARAM_PCG_MAX_CTAS, TOPO_PARAM_ROM_TENSOR, TOPO_PARAM_APPLY_STAGES, TOPO_PARAM_PCG_POLY,
+ TOPO_PARAM_PCG_MG, TOPO_PARAM_MG_DEGREE, TOPO_PARAM_MG_SINGLE_NODES) = range(15)
 
 # Every entry point declared in include/topo.h (checked by the tests).
 EXPORTS = ["topo_create", "topo_destroy", "topo_last_error", "topo_set_param", "topo_check", "topo_sizes",
@@ -47,7 +48,8 @@ class topo_problem(ctypes.Structure):
 
 class topo_solve_info(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("outer", ctypes.c_int), ("relres", ctypes.c_double),
-                ("status", ctypes.c_int), ("floor", ctypes.c_double), ("poly", ctypes.c_int)]
+                ("status", ctypes.c_int), ("floor", ctypes.c_double), ("poly", ctypes.c_int),
+                ("mg_levels", ctypes.c_int), ("fallback", ctypes.c_int)]
 
 
 _lib = None
@@ -182,7 +184,7 @@ class Topo:
         if st not in (TOPO_OK, TOPO_ERR_NOT_CONVERGED):
             self._chk(st, "topo_solve_hdm")
         return dict(iters=inf.iters, outer=inf.outer, relres=inf.relres, status=inf.status, poly=inf.poly,
-                    floor=inf.floor) if info else None
+                    floor=inf.floor, mg_levels=inf.mg_levels, fallback=inf.fallback) if info else None
 
     def topo_rom_build(self, rho, Usnap, Phi, H, b, f):
         m, ld = _cols(Usnap, self.N)

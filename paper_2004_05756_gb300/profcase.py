@@ -40,6 +40,9 @@ def main(argv=None):
     ap.add_argument("--ld-pad", type=int, default=1, help="round the leading dimension of V, Y up to a multiple")
     ap.add_argument("--poly", type=int, default=0, help="FP64 solve: polynomial preconditioner degree (0 = auto)")
     ap.add_argument("--rtol", type=float, default=1e-30, help="pcg/hdm: relative residual target")
+    ap.add_argument("--mg", type=int, default=1, help="FP64 solve: 1 multigrid preconditioner, 0 polynomial")
+    ap.add_argument("--mg-deg", type=int, default=2, help="multigrid: Chebyshev smoothing steps per side")
+    ap.add_argument("--mg-single", type=int, default=0, help="multigrid: nodes of levels run on one CTA")
     a = ap.parse_args(argv)
     import torch
 
@@ -56,6 +59,9 @@ def main(argv=None):
     T.topo_set_param(native.TOPO_PARAM_TILE_X, a.apply_cols)
     T.topo_set_param(native.TOPO_PARAM_APPLY_STAGES, a.apply_stages)
     T.topo_set_param(native.TOPO_PARAM_PCG_POLY, a.poly)
+    T.topo_set_param(native.TOPO_PARAM_PCG_MG, a.mg)
+    T.topo_set_param(native.TOPO_PARAM_MG_DEGREE, a.mg_deg)
+    T.topo_set_param(native.TOPO_PARAM_MG_SINGLE_NODES, a.mg_single)
     f64 = dict(dtype=torch.float64, device="cuda")
     psi = torch.as_tensor(w.design_field(p, 0)).to(**f64)
     rho = torch.empty(p.nel, **f64)
@@ -119,7 +125,8 @@ def main(argv=None):
     e1.synchronize()
     print(f"{a.call} {a.prec} shape={a.shape} m={a.m} k={k} hdm_kernel={a.hdm_kernel} bps={a.blocks_per_sm} "
           f"rom_tensor={a.rom_tensor} apply_cols={a.apply_cols} apply_stages={a.apply_stages} ld={ldp}: "
-          f"{e0.elapsed_time(e1) / a.reps * 1e3:.1f} us/call" + (f" poly={a.poly} {last_info}" if last_info else ""))
+          f"{e0.elapsed_time(e1) / a.reps * 1e3:.1f} us/call" +
+          (f" poly={a.poly} mg={a.mg} deg={a.mg_deg} single={a.mg_single} {last_info}" if last_info else ""))
     T.topo_check()
 
 

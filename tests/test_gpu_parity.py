@@ -487,9 +487,10 @@ def test_polynomial_preconditioner_same_solution_fewer_iterations(torch, case):
     """The FP64 stencil solve with the FP32 Chebyshev polynomial preconditioner (degrees 2, 4, 8
     and the automatic choice) reaches the oracle's direct solution like Jacobi (degree 1), to
     rtol 1e-10, in fewer iterations; topo_solve_info reports the degree used."""
-    from paper_2004_05756_gb300.native import TOPO_PARAM_PCG_POLY
+    from paper_2004_05756_gb300.native import TOPO_PARAM_PCG_MG, TOPO_PARAM_PCG_POLY
     p = CASES[case]()
     T = ctx_for(p)
+    T.topo_set_param(TOPO_PARAM_PCG_MG, 0)  # the polynomial path (multigrid is the default)
     psi, rho = _design(p)
     Uo = fem.solve(p, rho)
     Jo = fem.compliance(p, Uo)
