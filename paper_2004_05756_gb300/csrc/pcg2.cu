@@ -509,11 +509,13 @@ __device__ __forceinline__ void pcg2_body(const Pcg2Args<DIM>& a, const unsigned
   // --- stencil assembly and Jacobi diagonal ----------------------------------------------
   // With a polynomial preconditioner, also the Gershgorin bound max_i sum_j |K_ij| / K_ii of the
   // spectrum of D^-1 K (an upper bound, so the polynomial stays positive on the spectrum).
-  const int poly = PK == 1 ? a.poly : 1;
-  // an FP32 preconditioner on an FP32 copy of the stencil; the multigrid solve drops to FP64
-  // Jacobi if its FP32 V-cycle stops being positive definite (r.z <= 0 or p.K p <= 0: only on
-  // designs whose conditioning is beyond FP32, e.g. near-void parts carrying load)
-  bool f32pre = PK == 2 || poly > 1;
+  // poly: degree of the polynomial preconditioner (the multigrid solve's fallback for PK == 2)
+  const int poly = PK >= 1 ? a.poly : 1;
+  // the preconditioner in use: 2 multigrid, 1 polynomial, 0 Jacobi. The multigrid solve drops
+  // to the polynomial if its FP32 V-cycle stops being positive definite (r.z <= 0 or p.K p <= 0:
+  // designs whose conditioning is beyond the V-cycle's FP32 arithmetic, e.g. loads on void)
+  int mode = PK == 2 ? 2 : (poly > 1 ? 1 : 0);
+  const bool f32pre = mode != 0;  // an FP32 preconditioner on an FP32 copy of the stencil
   if (threadIdx.x == 0) sh_fallback = 0;
   double gmax = 0.0;
   for_owned([&](int i, int j, int k, long long n) {
@@ -549,12 +551,13 @@ __device__ __forceinline__ void pcg2_body(const Pcg2Args<DIM>& a, const unsigned
     if (!mg_setup()) return;
   }
   if (poly > 1) {
+    // (the multigrid solve keeps these for its fallback; its level-0 bound is in mg.lmax)
     // Chebyshev iteration for D^-1 K z = D^-1 r on [lmax / ratio, lmax], from z = 0, poly steps:
     // z_0 = b / theta, then d_j = c1_j d_{j-1} + c2_j res_{j-1}, z_j = z_{j-1} + d_j, with
     // rho_0 = 1 / sigma, rho_j = 1 / (2 sigma - rho_{j-1}), c1_j = rho_j rho_{j-1},
     // c2_j = 2 rho_j / delta (theta, delta: centre and half-width of the interval).
     if (threadIdx.x == 0) {
-      const double* bpart = part + (size_t)((bar & 1) * P2_SLOTS * m) * G;
+      const double* bpart = PK == 2 ? a.mg.lmax : part + (size_t)((bar & 1) * P2_SLOTS * m) * G;
       double lmax = 0.0;
       for (unsigned q = 0; q < G; ++q) lmax = fmax(lmax, bpart[q]);
       if (!(lmax > 0.0) || !isfinite(lmax)) lmax = 1.0;
@@ -980,7 +983,7 @@ __device__ __forceinline__ void pcg2_body(const Pcg2Args<DIM>& a, const unsigned
             x[dof] = 0.0;  // Dirichlet entries of the solution are zero (their columns are zero)
           }
           a.r[c * N + dof] = rv;
-          if (!f32pre) {
+          if (mode == 0) {
             const double zv = __ldcg(a.dinv + dof) * rv;
             a.z[c * N + dof] = zv;
             t0 = fma(rv, zv, t0);
@@ -992,8 +995,8 @@ __device__ __forceinline__ void pcg2_body(const Pcg2Args<DIM>& a, const unsigned
       acc[2][c] = t2;
       acc[3][c] = t3;
     }
-    if (f32pre) {  // z = p(D^-1 K) D^-1 r or the V-cycle: their halo steps need every CTA's r
-      if (!(PK == 2 ? mg_vcycle(true) : precond(true))) return false;
+    if (mode != 0) {  // z = p(D^-1 K) D^-1 r or the V-cycle: their halo steps need every CTA's r
+      if (!(mode == 2 ? mg_vcycle(true) : precond(true))) return false;
       for (int c = 0; c < m; ++c) acc[0][c] = accg[c];
     }
     for (int c = 0; c < m; ++c)
@@ -1101,8 +1104,8 @@ __device__ __forceinline__ void pcg2_body(const Pcg2Args<DIM>& a, const unsigned
           }
           sh_alpha[c] = sh_gamma[c] / sh_den[c];
           if (!(sh_alpha[c] > 0.0) || !isfinite(sh_alpha[c])) {
-            if (PK == 2 && !sh_fallback) {
-              sh_fallback = 1;  // restart from the true residual with Jacobi
+            if (PK == 2 && mode == 2) {
+              sh_fallback = 1;  // restart from the true residual with the polynomial
             } else {
               set_status(&gs->status, TOPO_ERR_NOT_SPD);
               sh_done[c] = 1;
@@ -1142,7 +1145,7 @@ __device__ __forceinline__ void pcg2_body(const Pcg2Args<DIM>& a, const unsigned
   // the polynomial preconditioner; per-thread gamma = r.z and r.r (reduced by the next phase W);
   // then z is published to the neighbours.
   auto phase_u = [&](bool restart) -> bool {
-    const bool jac = !f32pre;
+    const bool jac = mode == 0;
     for (int c = 0; c < m; ++c) accg[c] = accr[c] = 0.0;
     for (int c = 0; c < m; ++c) {
       if (sh_done[c]) continue;
@@ -1207,7 +1210,8 @@ __device__ __forceinline__ void pcg2_body(const Pcg2Args<DIM>& a, const unsigned
       accr[c] = ar;
     }
     if constexpr (PK == 2) {
-      if (f32pre) return mg_vcycle(false);  // publishes z as its last step
+      if (mode == 2) return mg_vcycle(false);  // publishes z as its last step
+      if (!precond(false)) return false;
       publish_z();
       return true;
     } else {
@@ -1226,8 +1230,8 @@ __device__ __forceinline__ void pcg2_body(const Pcg2Args<DIM>& a, const unsigned
     bool restart = true;
     while (true) {
       if (!phase_w(restart)) return;
-      if (PK == 2 && f32pre && sh_fallback) {
-        f32pre = false;  // every CTA reduced the same values: all switch here
+      if (PK == 2 && mode == 2 && sh_fallback) {
+        mode = 1;  // every CTA reduced the same values: all switch here
         break;
       }
       bool any = false;
@@ -1253,7 +1257,7 @@ __device__ __forceinline__ void pcg2_body(const Pcg2Args<DIM>& a, const unsigned
     a.info[0] = iters;
     a.info[1] = 0;
     a.info[2] = conv ? 0 : TOPO_ERR_NOT_CONVERGED;
-    a.info[3] = (PK == 2 && !f32pre) ? 1 : 0;  // multigrid fell back to Jacobi
+    a.info[3] = (PK == 2 && mode != 2) ? 1 : 0;  // multigrid fell back to the polynomial
     a.info_rr[0] = worst;
   }
 }
@@ -1302,7 +1306,7 @@ topo_status build_pcg2_args(topo_ctx* c, const double* rho, const double* F, dou
     oC32 = take((size_t)StencilGeom<DIM>::NC * g.nnodes * 4);
     oD32 = take(N * 4);
   }
-  if (poly > 1)  // the four vectors of the polynomial preconditioner
+  if (poly > 1 || mg)  // the four vectors of the polynomial preconditioner (multigrid: its fallback)
     for (int t = 0; t < 4; ++t) of[t] = take(N * m * 4);
   // multigrid levels: sizes, then FP64/FP32 stencils, D^-1, identity-row flags and V-cycle
   // vectors of every level, the dense coarsest operator and its inverse
@@ -1384,10 +1388,11 @@ topo_status build_pcg2_args(topo_ctx* c, const double* rho, const double* F, dou
   double** vecs[5] = {&a.r, &a.z, &a.w, &a.p, &a.s};
   for (int t = 0; t < 5; ++t) *vecs[t] = (double*)(base + ov[t]);
   float** fvecs[4] = {&a.t0, &a.t1, &a.res, &a.z32};
-  for (int t = 0; t < 4; ++t) *fvecs[t] = poly > 1 ? (float*)(base + of[t]) : nullptr;
+  for (int t = 0; t < 4; ++t) *fvecs[t] = (poly > 1 || mg) ? (float*)(base + of[t]) : nullptr;
   a.C32 = (poly > 1 || mg) ? (float*)(base + oC32) : nullptr;
   a.dinv32 = (poly > 1 || mg) ? (float*)(base + oD32) : nullptr;
   a.poly = poly > 1 ? poly : 1;
+  if (mg && a.poly < 2) a.poly = 2;  // the multigrid solve's fallback is a real polynomial
   a.mg = mga;
   if (mg) {
     for (int l = 0; l < mga.L; ++l) {
@@ -1501,7 +1506,7 @@ topo_status solve_stencil_fp64(topo_ctx* c, const double* rho, const double* F, 
     info_host->outer = 0;
     info_host->relres = sqrt(hrr[0]);
     info_host->floor = sqrt(hrr[1]);
-    info_host->poly = use_mg ? (hinfo[3] ? 1 : 0) : a.poly;
+    info_host->poly = use_mg ? (hinfo[3] ? a.poly : 0) : a.poly;
     info_host->mg_levels = use_mg ? a.mg.L : 0;
     info_host->fallback = use_mg ? hinfo[3] : 0;
     info_host->status = dev_status ? dev_status : hinfo[2];
