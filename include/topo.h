@@ -228,6 +228,28 @@ topo_status topo_rom_solve_elem(topo_ctx* ctx, const double* rho, const double* 
 topo_status topo_rom_solve_elem_noalloc(topo_ctx* ctx, const double* rho, const double* Hel, int k,
                                         const double* b, double* H_work, double* yhat, double* Jk);
 
+/* ROM design evaluations of R candidate designs on one resident basis, in one call (the
+ * candidates of a trust-region step, Algorithm 2; each evaluation as Section 3.1 Eq. rom_soln,
+ * Section 3.3 and Remark topopt_compl):
+ *   rho_r = filter(psi_r) (filtered != 0; else psi_r is the density),
+ *   H_r = sum_e E(rho_r,e) Hel[e] + Hel[N_e] (element reduced matrices of topo_rom_elem),
+ *   y_r = H_r^-1 b by FP64 Cholesky, Jk[r] = b^T y_r,
+ *   u_r = Phi y_r, resnorm[2r] = ||f - K(rho_r) u_r||_2 and resnorm[2r+1] = that / ||f||_2
+ *   (free DOFs, FP64),
+ *   dpsi_r = filter^T(-E'(rho_r) u_r,e^T K_e u_r,e) (or the unfiltered gradient when filtered
+ *   is 0), when dpsi is not NULL.
+ * psi: R fields of N_e doubles at stride ldp >= N_e; Phi: N x k at leading dimension ld;
+ * Hel: (N_e + 1) x k(k+1)/2 from topo_rom_elem for this Phi; b = Phi^T f (FP64[k]); f FP64[N].
+ * Outputs (device): Jk[R], resnorm[2R], yhat[R*k] (may be NULL), dpsi (R fields at stride ldp,
+ * may be NULL; must not alias psi). 1 <= k <= 128. Every candidate's results equal those of the
+ * one-candidate calls (topo_filter, topo_rom_solve_elem, topo_rom_error,
+ * topo_compliance_grad) up to the rounding order of their sums, and do not depend on the other
+ * candidates of the batch. A non-positive pivot sets TOPO_ERR_NOT_SPD in the device status and
+ * NaN for that candidate. Asynchronous on the context's stream. */
+topo_status topo_rom_eval_batch(topo_ctx* ctx, int R, const double* psi, int ldp, int filtered,
+                                const double* Hel, const double* Phi, int k, int ld, const double* b,
+                                const double* f, double* Jk, double* resnorm, double* yhat, double* dpsi);
+
 /* A posteriori residual (Section 3.3; the trust-region constraint of Eq. trcon-topopt):
  * u_k = Phi yhat, r = f - K(rho) u_k on the free DOFs, resnorm[0] = ||r||_2,
  * resnorm[1] = ||r||_2 / ||f||_2 (device FP64[2]). uk_opt (FP64[N], may be NULL) receives

@@ -510,7 +510,8 @@ struct ResArgs {
   const double* u;
   const double* f;
   double* r;        // may be null
-  double* partial;  // [2 * G]
+  double* partial;  // [2 * G] per design
+  long long ldr, ldu;  // strides of rho and u between the designs of blockIdx.y (several per launch)
 };
 
 template <int DIM>
@@ -519,8 +520,10 @@ __global__ void __launch_bounds__(TileShape<DIM>::NT) residual_kernel(const __gr
   __shared__ double red[32];
   const Grid& g = a.g;
   const TileCoord tc = tile_coord<DIM>(g, blockIdx.x);
-  stage_E<DIM, double>(s, g, tc, [&](long long e) { return young<double>(a.rho[e], g.E0, g.Emin, g.ipenal); });
-  stage_V<DIM, double>(s, g, tc, [&](long long dof) { return a.u[dof]; });
+  const double* rho = a.rho + blockIdx.y * a.ldr;
+  const double* u = a.u + blockIdx.y * a.ldu;
+  stage_E<DIM, double>(s, g, tc, [&](long long e) { return young<double>(rho[e], g.E0, g.Emin, g.ipenal); });
+  stage_V<DIM, double>(s, g, tc, [&](long long dof) { return u[dof]; });
   __syncthreads();
   int tx, ty, tz;
   long long n = 0;
@@ -544,13 +547,16 @@ __global__ void __launch_bounds__(TileShape<DIM>::NT) residual_kernel(const __gr
   double t1 = block_sum(rr, red);
   double t2 = block_sum(ff, red);
   if (threadIdx.x == 0) {
-    a.partial[blockIdx.x] = t1;
-    a.partial[gridDim.x + blockIdx.x] = t2;
+    double* part = a.partial + (size_t)blockIdx.y * 2 * gridDim.x;
+    part[blockIdx.x] = t1;
+    part[gridDim.x + blockIdx.x] = t2;
   }
 }
 
 __global__ void residual_final_kernel(const double* partial, int G, double* out2) {
   __shared__ double red[32];
+  partial += (size_t)blockIdx.x * 2 * G;  // one CTA per design
+  out2 += 2 * blockIdx.x;
   double a = 0.0, b = 0.0;
   for (int i = threadIdx.x; i < G; i += blockDim.x) {
     a += partial[i];
@@ -578,12 +584,46 @@ static topo_status residual_impl(topo_ctx* c, const double* rho, const double* u
   a.f = f;
   a.r = r;
   a.partial = c->d_red;
+  a.ldr = a.ldu = 0;
   residual_kernel<DIM><<<(unsigned)tiles, TileShape<DIM>::NT, 0, c->stream>>>(a);
   note_launch();
   residual_final_kernel<<<1, 256, 0, c->stream>>>(c->d_red, (int)tiles, out2);
   note_launch();
   TOPO_CUDA_TRY(c, cudaGetLastError());
   return TOPO_OK;
+}
+
+long long residual_tiles(topo_ctx* c) {
+  return c->g.dim == 2 ? num_tiles<2>(c->g) : num_tiles<3>(c->g);
+}
+
+template <int DIM>
+static topo_status residual_batch_impl(topo_ctx* c, const double* rho, long long ldr, const double* U, long long ldu,
+                                       const double* f, double* out2, int R, double* partial,
+                                       const typename KeOf<DIM, double>::type& ke) {
+  const long long tiles = num_tiles<DIM>(c->g);
+  ResArgs<DIM> a;
+  a.g = c->g;
+  a.ke = ke;
+  a.rho = rho;
+  a.u = U;
+  a.f = f;
+  a.r = nullptr;
+  a.partial = partial;
+  a.ldr = ldr;
+  a.ldu = ldu;
+  residual_kernel<DIM><<<dim3((unsigned)tiles, (unsigned)R), TileShape<DIM>::NT, 0, c->stream>>>(a);
+  note_launch();
+  residual_final_kernel<<<R, 256, 0, c->stream>>>(partial, (int)tiles, out2);
+  note_launch();
+  TOPO_CUDA_TRY(c, cudaGetLastError());
+  return TOPO_OK;
+}
+
+topo_status launch_residual64_batch(topo_ctx* c, const double* rho, long long ldr, const double* U, long long ldu,
+                                    const double* f, double* out2, int R, double* partial) {
+  if (c->g.dim == 2) return residual_batch_impl<2>(c, rho, ldr, U, ldu, f, out2, R, partial, c->q4_64);
+  return residual_batch_impl<3>(c, rho, ldr, U, ldu, f, out2, R, partial, c->h8_64);
 }
 
 topo_status launch_residual64(topo_ctx* c, const double* rho, const double* u, const double* f, double* r,

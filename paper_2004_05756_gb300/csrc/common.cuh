@@ -583,6 +583,17 @@ bool dev_ptr_ok(const void* p);
 // Launch helpers implemented in apply.cu (used by the ROM code as well).
 topo_status launch_apply(topo_ctx* c, const double* rho, const void* V, void* Y, int m, int ld, topo_prec prec,
                          const int* gate = nullptr);
+// The filter of R fields (forward, or adjoint when adjoint != 0) in one launch (ctx.cu).
+topo_status launch_filter_batch(topo_ctx* c, const double* in, long long ldin, double* out, long long ldout, int R,
+                                int adjoint);
+// Compliance gradients of R designs with one state each (ctx.cu).
+topo_status launch_grad_batch(topo_ctx* c, const double* rho, long long ldr, const double* U, long long ldu,
+                              double* dc, long long ldd, int R);
+// Residual norms ||f - K(rho_r) u_r|| (and / ||f||) of R designs in one launch (apply.cu): out2 +
+// 2 r receives them; partial holds 2 x tiles x R doubles.
+topo_status launch_residual64_batch(topo_ctx* c, const double* rho, long long ldr, const double* U, long long ldu,
+                                    const double* f, double* out2, int R, double* partial);
+long long residual_tiles(topo_ctx* c);
 // Residual r = f - K(rho) u on free DOFs (0 on Dirichlet DOFs), FP64, with ||r||^2 and ||f||^2
 // partials reduced to out2[0..1] (device). r may be NULL (norms only).
 topo_status launch_residual64(topo_ctx* c, const double* rho, const double* u, const double* f, double* r,

@@ -151,6 +151,7 @@ struct FilterArgs {
   const double* in;
   double* out;
   int mode;  // 0 = 1 / Hs, 1 = forward, 2 = adjoint
+  long long ldin, ldout;  // strides between the fields of blockIdx.y (several fields per launch)
 };
 
 __global__ void filter_kernel(const __grid_constant__ FilterArgs a) {
@@ -161,6 +162,8 @@ __global__ void filter_kernel(const __grid_constant__ FilterArgs a) {
   for (int i = threadIdx.x; i < a.ns; i += blockDim.x) sw[i] = a.w[i];
   __syncthreads();
   const Grid& g = a.g;
+  const double* in = a.in + blockIdx.y * a.ldin;
+  double* out = a.out + blockIdx.y * a.ldout;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < g.nel; e += (long long)gridDim.x * blockDim.x) {
     int i = (int)(e % g.nx);
     long long r = e / g.nx;
@@ -175,14 +178,14 @@ __global__ void filter_kernel(const __grid_constant__ FilterArgs a) {
       if (a.mode == 0)
         v = 1.0;
       else if (a.mode == 1)
-        v = a.in[en];
+        v = in[en];
       else
-        v = a.in[en] * a.Hsinv[en];  // FP64 division is slow here: multiply by 1 / Hs
+        v = in[en] * a.Hsinv[en];  // FP64 division is slow here: multiply by 1 / Hs
       acc = fma(sw[s], v, acc);
     }
     if (a.mode == 0) acc = 1.0 / acc;  // once per context
     if (a.mode == 1) acc *= a.Hsinv[e];
-    a.out[e] = acc;
+    out[e] = acc;
   }
 }
 
@@ -196,12 +199,16 @@ struct GradArgs {
   long long ld;
   int m;
   double* dc;
+  long long ldr, ldu, ldd;  // strides of rho, U and dc between the designs of blockIdx.y
 };
 
 template <int DIM>
 __global__ void grad_kernel(const __grid_constant__ GradArgs<DIM> a) {
   constexpr int NN = DIM == 2 ? 4 : 8, ND = DIM * NN;
   const Grid& g = a.g;
+  const double* rho = a.rho + blockIdx.y * a.ldr;
+  const double* U = a.U + blockIdx.y * a.ldu;
+  double* dc = a.dc + blockIdx.y * a.ldd;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < g.nel; e += (long long)gridDim.x * blockDim.x) {
     int i = (int)(e % g.nx);
     long long r = e / g.nx;
@@ -217,7 +224,7 @@ __global__ void grad_kernel(const __grid_constant__ GradArgs<DIM> a) {
     }
     double ce = 0.0;
     for (int col = 0; col < a.m; ++col) {
-      const double* u = a.U + (long long)col * a.ld;
+      const double* u = U + (long long)col * a.ld;
       double ue[ND];
 #pragma unroll
       for (int d = 0; d < ND; ++d) ue[d] = is_fixed(g, dofs[d]) ? 0.0 : u[dofs[d]];
@@ -229,7 +236,7 @@ __global__ void grad_kernel(const __grid_constant__ GradArgs<DIM> a) {
         ce = fma(ue[r2], t, ce);
       }
     }
-    a.dc[e] = -dyoung<double>(a.rho[e], g.E0, g.Emin, g.ipenal) * ce;
+    dc[e] = -dyoung<double>(rho[e], g.E0, g.Emin, g.ipenal) * ce;
   }
 }
 
@@ -285,8 +292,11 @@ __global__ void dot_cols_partial_kernel(const double* F, const double* U, long l
   if (threadIdx.x == 0) partial[(long long)blockIdx.y * gridDim.x + blockIdx.x] = t;
 }
 
-static topo_status filter_launch(topo_ctx* c, const double* in, double* out, int mode) {
+static topo_status filter_launch(topo_ctx* c, const double* in, double* out, int mode, int R = 1,
+                                 long long ldin = 0, long long ldout = 0) {
   FilterArgs a;
+  a.ldin = ldin;
+  a.ldout = ldout;
   a.g = c->g;
   a.off = c->d_stencil_off;
   a.w = c->d_stencil_w;
@@ -298,7 +308,54 @@ static topo_status filter_launch(topo_ctx* c, const double* in, double* out, int
   size_t sm = ((a.ns * 3 * sizeof(int) + 15) & ~(size_t)15) + a.ns * sizeof(double);
   long long blocks = (c->g.nel + 255) / 256;
   if (blocks > 8LL * c->num_sms) blocks = 8LL * c->num_sms;
-  filter_kernel<<<(int)blocks, 256, sm, c->stream>>>(a);
+  if (R > 1) blocks = std::max(1LL, std::min(blocks, (8LL * c->num_sms + R - 1) / R));
+  filter_kernel<<<dim3((unsigned)blocks, (unsigned)R), 256, sm, c->stream>>>(a);
+  note_launch();
+  TOPO_CUDA_TRY(c, cudaGetLastError());
+  return TOPO_OK;
+}
+
+// The filter (forward or adjoint) of R fields in one launch: field r at in + r ldin -> out + r ldout.
+topo_status launch_filter_batch(topo_ctx* c, const double* in, long long ldin, double* out, long long ldout, int R,
+                                int adjoint) {
+  return filter_launch(c, in, out, adjoint ? 2 : 1, R, ldin, ldout);
+}
+
+// dc_r = -E'(rho_r) u_r,e^T K_e u_r,e for R designs with one state each, in one launch.
+topo_status launch_grad_batch(topo_ctx* c, const double* rho, long long ldr, const double* U, long long ldu,
+                              double* dc, long long ldd, int R) {
+  const Grid& g = c->g;
+  long long blocks = (g.nel + 127) / 128;
+  const long long cap = std::max(1LL, (16LL * c->num_sms + R - 1) / R);
+  if (blocks > cap) blocks = cap;
+  const dim3 grid((unsigned)blocks, (unsigned)R);
+  if (g.dim == 2) {
+    GradArgs<2> a;
+    a.g = g;
+    a.ke = c->q4_64;
+    a.rho = rho;
+    a.U = U;
+    a.ld = ldu;
+    a.m = 1;
+    a.dc = dc;
+    a.ldr = ldr;
+    a.ldu = ldu;
+    a.ldd = ldd;
+    grad_kernel<2><<<grid, 128, 0, c->stream>>>(a);
+  } else {
+    GradArgs<3> a;
+    a.g = g;
+    a.ke = c->h8_64;
+    a.rho = rho;
+    a.U = U;
+    a.ld = ldu;
+    a.m = 1;
+    a.dc = dc;
+    a.ldr = ldr;
+    a.ldu = ldu;
+    a.ldd = ldd;
+    grad_kernel<3><<<grid, 128, 0, c->stream>>>(a);
+  }
   note_launch();
   TOPO_CUDA_TRY(c, cudaGetLastError());
   return TOPO_OK;
@@ -608,6 +665,7 @@ extern "C" topo_status topo_compliance_grad(topo_ctx* c, const double* rho, cons
     a.ld = ld;
     a.m = m;
     a.dc = dc_rho;
+    a.ldr = a.ldu = a.ldd = 0;
     grad_kernel<2><<<(int)blocks, 128, 0, c->stream>>>(a);
     note_launch();
   } else {
@@ -619,6 +677,7 @@ extern "C" topo_status topo_compliance_grad(topo_ctx* c, const double* rho, cons
     a.ld = ld;
     a.m = m;
     a.dc = dc_rho;
+    a.ldr = a.ldu = a.ldd = 0;
     grad_kernel<3><<<(int)blocks, 128, 0, c->stream>>>(a);
     note_launch();
   }

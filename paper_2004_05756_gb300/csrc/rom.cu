@@ -246,8 +246,8 @@ __global__ void cholesky_kernel(double* H, int k, int* status, int* ok_flag, con
 // so the solve takes k square roots and k divisions (each a long FP64 dependency chain here).
 // A pivot <= 0 (or NaN) sets TOPO_ERR_NOT_SPD and writes NaN to y and J.
 template <int KMAX>
-__global__ void __launch_bounds__(32) chol_small_kernel(double* H, int k, const double* b, double* y, double* J,
-                                                        int* status, int* ok_flag) {
+__device__ __forceinline__ void chol_small_body(double* H, int k, const double* b, double* y, double* J, int* status,
+                                                int* ok_flag) {
   __shared__ double Ls[KMAX][KMAX + 1];
   const unsigned FULL = 0xffffffffu;
   const int lane = threadIdx.x;
@@ -321,6 +321,20 @@ __global__ void __launch_bounds__(32) chol_small_kernel(double* H, int k, const 
     *J = t;
     *ok_flag = 1;
   }
+}
+
+template <int KMAX>
+__global__ void __launch_bounds__(32) chol_small_kernel(double* H, int k, const double* b, double* y, double* J,
+                                                        int* status, int* ok_flag) {
+  chol_small_body<KMAX>(H, k, b, y, J, status, ok_flag);
+}
+
+// R reduced solves, one warp each: H + r k^2, y + r k, J + r, ok + r (one right-hand side b).
+template <int KMAX>
+__global__ void __launch_bounds__(32) chol_small_batch_kernel(double* H, int k, const double* b, double* y, double* J,
+                                                              int* status, int* ok) {
+  const int r = blockIdx.x;
+  chol_small_body<KMAX>(H + (size_t)r * k * k, k, b, y + (size_t)r * k, J + r, status, ok + r);
 }
 
 // Solve L L^T x = rhs (L lower, row-major). mode 0: y = x; mode 1: y += x. Skipped (y left
@@ -545,6 +559,25 @@ topo_status launch_reduced_solve(topo_ctx* c, int k, const double* b, double* H_
   note_launch();
   dot_small_kernel<<<1, 128, 0, c->stream>>>(b, yhat, k, Jk);
   note_launch();
+  TOPO_CUDA_TRY(c, cudaGetLastError());
+  return TOPO_OK;
+}
+
+// R reduced solves with one right-hand side b: H, y, J and ok hold R consecutive instances.
+topo_status launch_reduced_solve_batch(topo_ctx* c, int k, int R, const double* b, double* H, double* y, double* J,
+                                       int* ok) {
+  if (k <= 16) {
+    chol_small_batch_kernel<16><<<R, 32, 0, c->stream>>>(H, k, b, y, J, &c->d_sync->status, ok);
+    note_launch();
+  } else if (k <= 32) {
+    chol_small_batch_kernel<32><<<R, 32, 0, c->stream>>>(H, k, b, y, J, &c->d_sync->status, ok);
+    note_launch();
+  } else {
+    for (int r = 0; r < R; ++r) {
+      topo_status s = launch_reduced_solve(c, k, b, H + (size_t)r * k * k, y + (size_t)r * k, J + r, ok + r);
+      if (s) return s;
+    }
+  }
   TOPO_CUDA_TRY(c, cudaGetLastError());
   return TOPO_OK;
 }

@@ -28,7 +28,8 @@ PREC = {"fp64": TOPO_FP64, "fp32": TOPO_FP32_REFINED, "fp32_bf16ke": TOPO_FP32_B
 EXPORTS = ["topo_create", "topo_destroy", "topo_last_error", "topo_set_param", "topo_check", "topo_sizes",
            "topo_filter", "topo_apply_K", "topo_solve_hdm", "topo_rom_build", "topo_rom_solve",
            "topo_rom_error", "topo_compliance_grad", "topo_launch_count", "topo_rom_elem",
-           "topo_rom_solve_elem", "topo_rom_solve_elem_noalloc", "topo_batch_create", "topo_batch_destroy",
+           "topo_rom_solve_elem", "topo_rom_solve_elem_noalloc", "topo_rom_eval_batch", "topo_batch_create",
+           "topo_batch_destroy",
            "topo_batch_last_error", "topo_batch_context", "topo_batch_solve_hdm", "topo_batch_filter",
            "topo_batch_compliance_grad", "topo_batch_rom_solve_elem"]
 
@@ -82,6 +83,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "topo_rom_elem": ([P, P, I, I, P], I),
         "topo_rom_solve_elem": ([P, P, P, I, P, P, P, P], I),
         "topo_rom_solve_elem_noalloc": ([P, P, P, I, P, P, P, P], I),
+        "topo_rom_eval_batch": ([P, I, P, I, I, P, P, I, I, P, P, P, P, P, P], I),
         "topo_batch_create": ([ctypes.POINTER(topo_problem), I, P, ctypes.POINTER(P)], I),
         "topo_batch_destroy": ([P], I),
         "topo_batch_last_error": ([P], ctypes.c_char_p),
@@ -210,6 +212,19 @@ class Topo:
     def topo_rom_solve_elem_noalloc(self, rho, Hel, k: int, b, H_work, yhat, Jk):
         self._chk(self.lib.topo_rom_solve_elem_noalloc(self.h, _ptr(rho), _ptr(Hel), int(k), _ptr(b), _ptr(H_work),
                                                        _ptr(yhat), _ptr(Jk)), "topo_rom_solve_elem_noalloc")
+
+    def topo_rom_eval_batch(self, psi, Hel, Phi, k: int, b, f, Jk, resnorm, yhat=None, dpsi=None,
+                            filtered: bool = True):
+        """psi: (R, ldp) tensor of designs (rows = candidates); Jk (R,), resnorm (R, 2), yhat (R, k),
+        dpsi (R, ldp) like psi."""
+        R = int(psi.shape[0]) if psi.dim() == 2 else 1
+        ldp = int(psi.stride(0)) if psi.dim() == 2 and R > 1 else int(self.Ne)
+        if dpsi is not None and dpsi.dim() == 2 and R > 1 and int(dpsi.stride(0)) != ldp:
+            raise ValueError("dpsi must have the stride of psi")
+        ld = _ld(Phi, self.N)
+        self._chk(self.lib.topo_rom_eval_batch(self.h, R, _ptr(psi), ldp, 1 if filtered else 0, _ptr(Hel), _ptr(Phi),
+                                               int(k), ld, _ptr(b), _ptr(f), _ptr(Jk), _ptr(resnorm), _ptr(yhat),
+                                               _ptr(dpsi)), "topo_rom_eval_batch")
 
     def topo_rom_error(self, rho, Phi, k: int, yhat, f, resnorm, uk=None):
         ld = _ld(Phi, self.N)
