@@ -46,8 +46,7 @@ struct MgArgs {
   int ls;         // levels ls .. L - 1 run on CTA 0 alone (1 <= ls <= L - 1)
   int deg;        // Chebyshev smoothing steps per side (1 .. MG_MAX_DEG)
   int nc;         // DOFs of the coarsest level
-  double* A;      // coarsest operator, dense nc x nc FP64 (row-major), Cholesky factor in place
-  float* Ainv;    // its inverse, nc x nc FP32
+  float* Ainv;    // inverse of the coarsest operator, nc x nc FP32 (factorised in FP64 per solve)
   double* lmax;   // per-level Gershgorin partials [MG_MAX_LEVELS][G]
   int* coarse_ok; // 1 when the coarsest factorisation succeeded (else no coarse correction)
   MgLevel lv[MG_MAX_LEVELS];
@@ -101,108 +100,108 @@ __device__ __forceinline__ long long mg_owner(long long u, long long n, long lon
   return b;
 }
 
-// Galerkin row block of coarse node (I, J, K) of level Lc from fine level Lf: for every coarse
-// neighbour offset (3^d blocks), sum over fine nodes i in the support of the coarse node and
-// fine neighbours j of i in the support of the coarse neighbour of
-// w(i, coarse) (1 - fixed(i, a)) K_f[(i, a), (j, b)] w(j, neighbour).
-// Writes the FP64 block row (identity rows where the row is all zero) and its FP32 copy, the
-// identity-row flags, D^-1 (FP32), and returns the Gershgorin ratio max_a sum_b |K_ab| / K_aa.
+// Galerkin product K_c = P^T K_f P, one row of one block: entries (oc, a, b), b < DIM, of coarse
+// node (I, J, K) of level Cl from fine level F, i.e. the sum over fine nodes i in the support of
+// the coarse node and fine neighbours j of i in the support of coarse neighbour oc of
+// w(i, coarse) (1 - fixed(i, a)) K_f[(i, a), (j, b)] w(j, neighbour). (A fixed fine column b of
+// K_f is already zero, apart from the identity entry, which the row factor removes.) Written to
+// the FP64 stencil and its FP32 copy; identity rows are patched afterwards (mg_galerkin_finish).
 template <int DIM>
-__device__ double mg_galerkin_node(const Grid& g0, const MgLevel& F, const MgLevel& Cl, bool fine0, int I, int J,
-                                   int K, long long n) {
-  constexpr int NB = DIM == 2 ? 9 : 27, DD = DIM * DIM;
-  const int nfx = F.nnx, nfy = F.nny, nfz = F.nnz;
-  const int px = mg_pos(I, nfx), py = mg_pos(J, nfy), pz = DIM == 3 ? mg_pos(K, nfz) : 0;
-  double rowabs[DIM], diag[DIM];
+__device__ void mg_galerkin_row(const Grid& g0, const MgLevel& F, const MgLevel& Cl, bool fine0, int I, int J, int K,
+                                long long n, int oc, int a) {
+  const int nf[3] = {F.nnx, F.nny, F.nnz};
+  const int cidx[3] = {I, J, K};
+  const int off[3] = {oc % 3 - 1, (oc / 3) % 3 - 1, DIM == 3 ? oc / 9 - 1 : 0};
+  const int ncd[3] = {Cl.nnx, Cl.nny, Cl.nnz};
+  double acc[DIM];
 #pragma unroll
-  for (int a = 0; a < DIM; ++a) rowabs[a] = diag[a] = 0.0;
-  const int centre = DIM == 2 ? 4 : 13;
-  // first pass computes the blocks; identity rows are decided from the diagonal, so the
-  // blocks are written, then patched in a second pass if a row is all zero
-#pragma unroll 1
-  for (int oc = 0; oc < NB; ++oc) {
-    const int ox = oc % 3 - 1, oy = (oc / 3) % 3 - 1, oz = DIM == 3 ? oc / 9 - 1 : 0;
-    const int I2 = I + ox, J2 = J + oy, K2 = K + oz;
-    double acc[DD];
+  for (int b = 0; b < DIM; ++b) acc[b] = 0.0;
+  bool cin = true;
 #pragma unroll
-    for (int q = 0; q < DD; ++q) acc[q] = 0.0;
-    const bool cin = I2 >= 0 && I2 < Cl.nnx && J2 >= 0 && J2 < Cl.nny && (DIM == 2 || (K2 >= 0 && K2 < Cl.nnz));
-    if (cin) {
-      const int qx = mg_pos(I2, nfx), qy = mg_pos(J2, nfy), qz = DIM == 3 ? mg_pos(K2, nfz) : 0;
-      for (int iz = (DIM == 3 ? max(pz - 1, 0) : 0); iz <= (DIM == 3 ? min(pz + 1, nfz - 1) : 0); ++iz) {
-        const float wz = DIM == 3 ? mg_w1(iz, K, nfz) : 1.f;
-        if (wz == 0.f) continue;
-        for (int iy = max(py - 1, 0); iy <= min(py + 1, nfy - 1); ++iy) {
-          const float wy = mg_w1(iy, J, nfy);
-          if (wy == 0.f) continue;
-          for (int ix = max(px - 1, 0); ix <= min(px + 1, nfx - 1); ++ix) {
-            const float wx = mg_w1(ix, I, nfx);
-            if (wx == 0.f) continue;
-            const double wi = (double)wx * wy * wz;
-            const long long ni = ix + (long long)nfx * (iy + (long long)nfy * iz);
-            bool rowfree[DIM];
+  for (int d = 0; d < DIM; ++d) cin = cin && cidx[d] + off[d] >= 0 && cidx[d] + off[d] < ncd[d];
+  if (cin) {
+    // per direction, the fine pairs (i, j) with j - i in {-1, 0, 1}, i in the support of the
+    // coarse node and j in the support of its neighbour, and the weight w(i) w(j) of the pair
+    short pi[3][7], pj[3][7];
+    float pw[3][7];
+    int np[3] = {1, 1, 1};
+    pi[2][0] = pj[2][0] = 0;
+    pw[2][0] = 1.f;
 #pragma unroll
-            for (int a = 0; a < DIM; ++a)
-              rowfree[a] = fine0 ? !is_fixed(g0, DIM * ni + a) : (__ldcg(F.fix + DIM * ni + a) == 0);
-            // fine neighbours j of i inside the support of the coarse neighbour
-            for (int jz = (DIM == 3 ? max(iz - 1, max(qz - 1, 0)) : 0);
-                 jz <= (DIM == 3 ? min(iz + 1, min(qz + 1, nfz - 1)) : 0); ++jz) {
-              const float vz = DIM == 3 ? mg_w1(jz, K2, nfz) : 1.f;
-              if (vz == 0.f) continue;
-              for (int jy = max(iy - 1, max(qy - 1, 0)); jy <= min(iy + 1, min(qy + 1, nfy - 1)); ++jy) {
-                const float vy = mg_w1(jy, J2, nfy);
-                if (vy == 0.f) continue;
-                for (int jx = max(ix - 1, max(qx - 1, 0)); jx <= min(ix + 1, min(qx + 1, nfx - 1)); ++jx) {
-                  const float vx = mg_w1(jx, I2, nfx);
-                  if (vx == 0.f) continue;
-                  const double wij = wi * ((double)vx * vy * vz);
-                  const int nb = (jx - ix + 1) + 3 * (jy - iy + 1) + (DIM == 3 ? 9 * (jz - iz + 1) : 0);
+    for (int d = 0; d < DIM; ++d) {
+      const int p = mg_pos(cidx[d], nf[d]), c2 = cidx[d] + off[d];
+      int cnt = 0;
 #pragma unroll
-                  for (int a = 0; a < DIM; ++a) {
-                    if (!rowfree[a]) continue;
+      for (int di = -1; di <= 1; ++di) {
+        const int i = p + di;
+        const float wi = (i >= 0 && i < nf[d]) ? mg_w1(i, cidx[d], nf[d]) : 0.f;
 #pragma unroll
-                    for (int b = 0; b < DIM; ++b)
-                      acc[a * DIM + b] =
-                          fma(wij, __ldcg(F.C + (long long)((nb * DIM + a) * DIM + b) * F.nnodes + ni), acc[a * DIM + b]);
-                  }
-                }
-              }
-            }
+        for (int e = -1; e <= 1; ++e) {
+          const int j = i + e;
+          const float wj = (wi != 0.f && j >= 0 && j < nf[d]) ? mg_w1(j, c2, nf[d]) : 0.f;
+          if (wj != 0.f && cnt < 7) {
+            pi[d][cnt] = (short)i;
+            pj[d][cnt] = (short)j;
+            pw[d][cnt] = wi * wj;
+            ++cnt;
           }
         }
       }
+      np[d] = cnt;
     }
+    for (int qz = 0; qz < np[2]; ++qz) {
+      for (int qy = 0; qy < np[1]; ++qy) {
+        for (int qx = 0; qx < np[0]; ++qx) {
+          const int ix = pi[0][qx], iy = pi[1][qy], iz = pi[2][qz];
+          const long long ni = ix + (long long)F.nnx * (iy + (long long)F.nny * iz);
+          const bool rowfree = fine0 ? !is_fixed(g0, DIM * ni + a) : (__ldcg(F.fix + DIM * ni + a) == 0);
+          if (!rowfree) continue;
+          const double w = (double)pw[0][qx] * pw[1][qy] * pw[2][qz];
+          const int nb = (pj[0][qx] - ix + 1) + 3 * (pj[1][qy] - iy + 1) + (DIM == 3 ? 9 * (pj[2][qz] - iz + 1) : 0);
 #pragma unroll
-    for (int a = 0; a < DIM; ++a)
-#pragma unroll
-      for (int b = 0; b < DIM; ++b) {
-        const double v = acc[a * DIM + b];
-        Cl.C[(long long)((oc * DIM + a) * DIM + b) * Cl.nnodes + n] = v;
-        rowabs[a] += fabs(v);
-        if (oc == centre && a == b) diag[a] = v;
+          for (int b = 0; b < DIM; ++b)
+            acc[b] = fma(w, __ldcg(F.C + (long long)((nb * DIM + a) * DIM + b) * F.nnodes + ni), acc[b]);
+        }
       }
-  }
-  double gmax = 0.0;
-#pragma unroll
-  for (int a = 0; a < DIM; ++a) {
-    const bool ident = !(diag[a] != 0.0);
-    Cl.fix[DIM * n + a] = ident ? 1 : 0;
-    if (ident) {
-      for (int oc = 0; oc < NB; ++oc)
-#pragma unroll
-        for (int b = 0; b < DIM; ++b)
-          Cl.C[(long long)((oc * DIM + a) * DIM + b) * Cl.nnodes + n] = (oc == centre && a == b) ? 1.0 : 0.0;
-      diag[a] = 1.0;
-      rowabs[a] = 1.0;
     }
-    Cl.dinv[DIM * n + a] = (float)(1.0 / diag[a]);
-    gmax = fmax(gmax, rowabs[a] / diag[a]);
   }
-  for (int q = 0; q < NB * DD; ++q) {
-    const long long o = (long long)q * Cl.nnodes + n;
-    Cl.C32[o] = (float)Cl.C[o];
+#pragma unroll
+  for (int b = 0; b < DIM; ++b) {
+    const long long o = (long long)((oc * DIM + a) * DIM + b) * Cl.nnodes + n;
+    Cl.C[o] = acc[b];
+    Cl.C32[o] = (float)acc[b];
   }
-  return gmax;
+}
+
+// After every block of coarse node n is written (by threads of the same CTA): row a becomes an
+// identity row when its diagonal is zero (its whole fine support is fixed); writes the flag and
+// D^-1 and returns the Gershgorin ratio sum_b |K_ab| / K_aa of the row.
+template <int DIM>
+__device__ double mg_galerkin_finish(const MgLevel& Cl, long long n, int a) {
+  constexpr int NB = DIM == 2 ? 9 : 27;
+  const int centre = DIM == 2 ? 4 : 13;
+  double diag = Cl.C[(long long)((centre * DIM + a) * DIM + a) * Cl.nnodes + n];
+  const bool ident = !(diag != 0.0);
+  double rowabs = 0.0;
+  for (int oc = 0; oc < NB; ++oc)
+#pragma unroll
+    for (int b = 0; b < DIM; ++b) {
+      const long long o = (long long)((oc * DIM + a) * DIM + b) * Cl.nnodes + n;
+      if (ident) {
+        const double v = (oc == centre && a == b) ? 1.0 : 0.0;
+        Cl.C[o] = v;
+        Cl.C32[o] = (float)v;
+      } else {
+        rowabs += fabs(Cl.C[o]);
+      }
+    }
+  if (ident) {
+    diag = 1.0;
+    rowabs = 1.0;
+  }
+  Cl.fix[DIM * n + a] = ident ? 1 : 0;
+  Cl.dinv[DIM * n + a] = (float)(1.0 / diag);
+  return rowabs / diag;
 }
 
 }  // namespace topo

@@ -173,7 +173,10 @@ __device__ __forceinline__ void stencil_apply(const Grid& g, const double* __res
   for (int d = 0; d < DIM; ++d) vown[d] = __ldcg(v + DIM * n + d);
 }
 
-// y = C32 v in FP32 for node (i, j, k) (the polynomial preconditioner); vown: v at the node.
+// y = C32 v in FP32 for node (i, j, k) (the FP32 preconditioners); vown: v at the node. In 2D
+// the coefficients (read-only after the setup, written by the reading thread or before a grid
+// barrier for levels run by one CTA) stay in L1: a CTA's share of a level fits there. In 3D
+// (243 per node) they do not, and come from L2 like v, which other CTAs write during the solve.
 template <int DIM>
 __device__ __forceinline__ void stencil_apply32(const Grid& g, const float* __restrict__ C, const float* v, int i,
                                                 int j, int k, long long n, float* y, float* vown) {
@@ -195,7 +198,7 @@ __device__ __forceinline__ void stencil_apply32(const Grid& g, const float* __re
     for (int nb = 0; nb < NB; ++nb) {
       float cc[4];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) cc[q] = __ldcg(gp + (long long)(nb * 4 + q) * g.nnodes);
+      for (int q = 0; q < 4; ++q) cc[q] = __ldca(gp + (long long)(nb * 4 + q) * g.nnodes);
       y[0] = fmaf(cc[0], vv[nb].x, y[0]);
       y[0] = fmaf(cc[1], vv[nb].y, y[0]);
       y[1] = fmaf(cc[2], vv[nb].x, y[1]);
@@ -348,94 +351,112 @@ __device__ __forceinline__ void pcg2_body(const Pcg2Args<DIM>& a, const unsigned
       const MgLevel& Cc = M.lv[l + 1];
       const long long c0 = Cc.nunits * rank / G, c1 = Cc.nunits * (rank + 1) / G;
       const int ux = (Cc.nnx + 31) / 32;
-      double gm = 0.0;
-      for (long long u = c0 + warp; u < c1; u += nwarps) {
-        const int i = (int)(u % ux) * 32 + lane;
+      constexpr int NB = StencilGeom<DIM>::NB;
+      // one thread per (node, neighbour block, row); nodes fastest, so stores coalesce
+      const long long items = (c1 - c0) * 32 * NB * DIM;
+      for (long long t = threadIdx.x; t < items; t += blockDim.x) {
+        const int ln = (int)(t % 32);
+        const long long rest = t / 32;
+        const int ar = (int)(rest % DIM);
+        const int oc = (int)((rest / DIM) % NB);
+        const long long u = c0 + rest / (DIM * NB);
+        const int i = (int)(u % ux) * 32 + ln;
         const long long r = u / ux;
         const int j = (int)(r % Cc.nny), k = (int)(r / Cc.nny);
         if (i >= Cc.nnx) continue;
         const long long n = i + (long long)Cc.nnx * (j + (long long)Cc.nny * k);
-        gm = fmax(gm, mg_galerkin_node<DIM>(g, F, Cc, l == 0, i, j, k, n));
+        mg_galerkin_row<DIM>(g, F, Cc, l == 0, i, j, k, n, oc, ar);
+      }
+      __syncthreads();
+      double gm = 0.0;
+      for (long long t = threadIdx.x; t < (c1 - c0) * 32 * DIM; t += blockDim.x) {
+        const int ln = (int)(t % 32);
+        const int ar = (int)((t / 32) % DIM);
+        const long long u = c0 + t / (32 * DIM);
+        const int i = (int)(u % ux) * 32 + ln;
+        const long long r = u / ux;
+        const int j = (int)(r % Cc.nny), k = (int)(r / Cc.nny);
+        if (i >= Cc.nnx) continue;
+        const long long n = i + (long long)Cc.nnx * (j + (long long)Cc.nny * k);
+        gm = fmax(gm, mg_galerkin_finish<DIM>(Cc, n, ar));
       }
       const double bm = block_max(gm);
       if (threadIdx.x == 0) M.lmax[(size_t)(l + 1) * G + rank] = bm;
       if (!sync_reduce(0)) return false;
     }
-    // coarsest level: dense rows of the owned nodes
+    // Coarsest level: every CTA that owns a column of the inverse (q = rank, rank + G, ...)
+    // builds the dense operator itself from the coarsest stencil, as a packed lower triangle in
+    // shared memory, factorises it (Cholesky, FP64; a non-positive pivot disables the coarse
+    // correction instead of failing the solve) and solves L L^T x = e_q column-wise: no grid
+    // barrier and no global round trip between the steps, and the same factor on every CTA.
     const int nc = M.nc;
-    {
+    if ((int)rank < nc) {
+      extern __shared__ __align__(16) unsigned char mg_dyn[];
+      double* Ap = reinterpret_cast<double*>(mg_dyn);      // packed lower triangle, nc (nc + 1) / 2
+      double* yv = Ap + (size_t)nc * (nc + 1) / 2;          // [nc]: the column being solved
+      auto pk = [&](int i, int j) -> double& { return Ap[(size_t)i * (i + 1) / 2 + j]; };
       const MgLevel& Cc = M.lv[M.L - 1];
       constexpr int NB = StencilGeom<DIM>::NB;
-      const long long c0 = Cc.nunits * rank / G, c1 = Cc.nunits * (rank + 1) / G;
-      const int ux = (Cc.nnx + 31) / 32;
-      for (long long u = c0 + warp; u < c1; u += nwarps) {
-        const int i = (int)(u % ux) * 32 + lane;
-        const long long r = u / ux;
-        const int j = (int)(r % Cc.nny), k = (int)(r / Cc.nny);
-        if (i >= Cc.nnx) continue;
-        const long long n = i + (long long)Cc.nnx * (j + (long long)Cc.nny * k);
-        for (int ar = 0; ar < DIM; ++ar) {
-          double* row = M.A + (size_t)(DIM * n + ar) * nc;
-          for (int q = 0; q < nc; ++q) row[q] = 0.0;
-          for (int nb = 0; nb < NB; ++nb) {
-            const int ii = i + nb % 3 - 1, jj = j + (nb / 3) % 3 - 1, kk = DIM == 3 ? k + nb / 9 - 1 : 0;
-            if (ii < 0 || ii >= Cc.nnx || jj < 0 || jj >= Cc.nny || kk < 0 || kk >= Cc.nnz) continue;
-            const long long mm = ii + (long long)Cc.nnx * (jj + (long long)Cc.nny * kk);
-            for (int b = 0; b < DIM; ++b) row[DIM * mm + b] = __ldcg(Cc.C + (long long)((nb * DIM + ar) * DIM + b) * Cc.nnodes + n);
+      for (int t = threadIdx.x; t < nc * (nc + 1) / 2; t += blockDim.x) Ap[t] = 0.0;
+      __syncthreads();
+      for (int row = threadIdx.x; row < nc; row += blockDim.x) {
+        const long long n = row / DIM;
+        const int ar = row % DIM;
+        const int i = (int)(n % Cc.nnx), j = (int)((n / Cc.nnx) % Cc.nny), k = (int)(n / ((long long)Cc.nnx * Cc.nny));
+        for (int nb = 0; nb < NB; ++nb) {
+          const int ii = i + nb % 3 - 1, jj = j + (nb / 3) % 3 - 1, kk = DIM == 3 ? k + nb / 9 - 1 : 0;
+          if (ii < 0 || ii >= Cc.nnx || jj < 0 || jj >= Cc.nny || kk < 0 || kk >= Cc.nnz) continue;
+          const long long mm = ii + (long long)Cc.nnx * (jj + (long long)Cc.nny * kk);
+          for (int b = 0; b < DIM; ++b) {
+            const int col = (int)(DIM * mm + b);
+            if (col <= row) pk(row, col) = __ldcg(Cc.C + (long long)((nb * DIM + ar) * DIM + b) * Cc.nnodes + n);
           }
         }
       }
-    }
-    if (!sync_reduce(0)) return false;
-    // Cholesky A = L L^T on CTA 0 (lower triangle, in place); a non-positive pivot disables the
-    // coarse correction instead of failing the solve
-    if (rank == 0) {
       if (threadIdx.x == 0) mg_okc = 1;
       __syncthreads();
-      for (int k = 0; k < nc; ++k) {
+      for (int kq = 0; kq < nc; ++kq) {  // right-looking Cholesky, a warp per trailing row
         if (threadIdx.x == 0) {
-          const double d = M.A[(size_t)k * nc + k];
+          const double d = pk(kq, kq);
           if (!(d > 0.0) || !isfinite(d)) mg_okc = 0;
-          M.A[(size_t)k * nc + k] = mg_okc ? sqrt(d) : 1.0;
+          pk(kq, kq) = mg_okc ? sqrt(d) : 1.0;
         }
         __syncthreads();
         if (!mg_okc) break;
-        const double lkk = M.A[(size_t)k * nc + k];
-        for (int i = k + 1 + threadIdx.x; i < nc; i += blockDim.x) M.A[(size_t)i * nc + k] /= lkk;
+        const double inv = 1.0 / pk(kq, kq);
+        for (int i = kq + 1 + threadIdx.x; i < nc; i += blockDim.x) pk(i, kq) *= inv;
         __syncthreads();
-        const int mrem = nc - k - 1;
-        for (int t = threadIdx.x; t < mrem * mrem; t += blockDim.x) {
-          const int i = k + 1 + t / mrem, j = k + 1 + t % mrem;
-          if (j <= i) M.A[(size_t)i * nc + j] -= M.A[(size_t)i * nc + k] * M.A[(size_t)j * nc + k];
+        for (int i = kq + 1 + warp; i < nc; i += nwarps) {
+          const double lik = pk(i, kq);
+          for (int j = kq + 1 + lane; j <= i; j += 32) pk(i, j) = fma(-lik, pk(j, kq), pk(i, j));
         }
         __syncthreads();
       }
-      if (threadIdx.x == 0) *M.coarse_ok = mg_okc;
-    }
-    if (!sync_reduce(0)) return false;
-    // inverse: column q of A^-1 (= row q, A symmetric) by CTA q mod G, warp 0; y in shared memory
-    {
-      __shared__ double ycol[MG_COARSE_MAX];
-      const int ok = __ldcg(M.coarse_ok);
-      for (int q = rank; q < nc; q += G) {
+      if (rank == 0 && threadIdx.x == 0) *M.coarse_ok = mg_okc;
+      for (int q = rank; q < nc; q += G) {  // L y = e_q, then L^T x = y (column-oriented)
         if (warp == 0) {
-          for (int i = 0; i < nc; ++i) {  // L y = e_q
-            double t = 0.0;
-            if (ok && i >= q)
-              for (int p = q + lane; p < i; p += 32) t = fma(__ldcg(M.A + (size_t)i * nc + p), ycol[p], t);
-            t = warp_sum(t);
-            if (lane == 0) ycol[i] = (ok && i >= q) ? ((i == q ? 1.0 : 0.0) - t) / __ldcg(M.A + (size_t)i * nc + i) : 0.0;
+          for (int i = lane; i < nc; i += 32) yv[i] = (i == q) ? 1.0 : 0.0;
+          __syncwarp();
+          if (mg_okc) {
+            for (int jc = q; jc < nc; ++jc) {
+              const double yj = yv[jc] / pk(jc, jc);
+              __syncwarp();
+              for (int i = jc + 1 + lane; i < nc; i += 32) yv[i] = fma(-pk(i, jc), yj, yv[i]);
+              if (lane == 0) yv[jc] = yj;
+              __syncwarp();
+            }
+            for (int jc = nc - 1; jc >= 0; --jc) {
+              const double xj = yv[jc] / pk(jc, jc);
+              __syncwarp();
+              for (int i = lane; i < jc; i += 32) yv[i] = fma(-pk(jc, i), xj, yv[i]);
+              if (lane == 0) yv[jc] = xj;
+              __syncwarp();
+            }
+          } else {
+            for (int i = lane; i < nc; i += 32) yv[i] = 0.0;
             __syncwarp();
           }
-          for (int i = nc - 1; i >= 0; --i) {  // L^T x = y
-            double t = 0.0;
-            if (ok)
-              for (int p = i + 1 + lane; p < nc; p += 32) t = fma(__ldcg(M.A + (size_t)p * nc + i), ycol[p], t);
-            t = warp_sum(t);
-            if (lane == 0) ycol[i] = ok ? (ycol[i] - t) / __ldcg(M.A + (size_t)i * nc + i) : 0.0;
-            __syncwarp();
-          }
-          for (int i = lane; i < nc; i += 32) M.Ainv[(size_t)q * nc + i] = (float)ycol[i];
+          for (int i = lane; i < nc; i += 32) M.Ainv[(size_t)q * nc + i] = (float)yv[i];
           __syncwarp();
         }
       }
@@ -598,7 +619,7 @@ __device__ __forceinline__ void pcg2_body(const Pcg2Args<DIM>& a, const unsigned
 #pragma unroll
         for (int d = 0; d < DIM; ++d) {
           const long long dof = DIM * n + d, o = o0 + dof;
-          const float b = __ldcg(a.dinv32 + dof) * (float)a.r[o];
+          const float b = __ldca(a.dinv32 + dof) * (float)a.r[o];
           const float zv = b * it;
           a.res[o] = b;
           a.t0[o] = zv;
@@ -624,7 +645,7 @@ __device__ __forceinline__ void pcg2_body(const Pcg2Args<DIM>& a, const unsigned
 #pragma unroll
           for (int d = 0; d < DIM; ++d) {
             const long long dof = DIM * n + d, o = o0 + dof;
-            const float rs = fmaf(-__ldcg(a.dinv32 + dof), y[d], a.res[o]);
+            const float rs = fmaf(-__ldca(a.dinv32 + dof), y[d], a.res[o]);
             const float dv = fmaf(c1, tn[d], c2 * rs);
             const float zv = a.z32[o] + dv;
             if (last) {
@@ -698,48 +719,74 @@ __device__ __forceinline__ void pcg2_body(const Pcg2Args<DIM>& a, const unsigned
     return Lv.v + ((size_t)slot * m + c) * Lv.ndof;
   };
   auto colskip = [&](bool all_cols, int c) -> bool { return !all_cols && sh_done[c]; };
-  // b at coarse node (I, J, K) of level l = P^T r of level l - 1 (its residual slot)
+  // b at coarse node (I, J, K) of level l = P^T r of level l - 1 (its residual slot). The 3^d
+  // fine support positions are unrolled with predicates, so all loads are issued at once.
   auto restrict_node = [&](int l, const float* src, int I, int J, int K, float* out) {
     const MgLevel& F = a.mg.lv[l - 1];
+    constexpr int NZ = DIM == 3 ? 3 : 1;
+    const int px = mg_pos(I, F.nnx), py = mg_pos(J, F.nny), pz = DIM == 3 ? mg_pos(K, F.nnz) : 0;
 #pragma unroll
     for (int q = 0; q < DIM; ++q) out[q] = 0.f;
-    const int px = mg_pos(I, F.nnx), py = mg_pos(J, F.nny), pz = DIM == 3 ? mg_pos(K, F.nnz) : 0;
-    for (int iz = (DIM == 3 ? max(pz - 1, 0) : 0); iz <= (DIM == 3 ? min(pz + 1, F.nnz - 1) : 0); ++iz) {
-      const float wz = DIM == 3 ? mg_w1(iz, K, F.nnz) : 1.f;
+#pragma unroll 1
+    for (int dz = 0; dz < NZ; ++dz) {  // one plane of the support at a time (register budget)
+      const int iz = DIM == 3 ? pz + dz - 1 : 0;
+      const float wz = DIM == 3 ? ((iz >= 0 && iz < F.nnz) ? mg_w1(iz, K, F.nnz) : 0.f) : 1.f;
       if (wz == 0.f) continue;
-      for (int iy = max(py - 1, 0); iy <= min(py + 1, F.nny - 1); ++iy) {
-        const float wy = mg_w1(iy, J, F.nny) * wz;
-        if (wy == 0.f) continue;
-        for (int ix = max(px - 1, 0); ix <= min(px + 1, F.nnx - 1); ++ix) {
-          const float w = mg_w1(ix, I, F.nnx) * wy;
-          if (w == 0.f) continue;
-          const long long ni = ix + (long long)F.nnx * (iy + (long long)F.nny * iz);
+      float v[3][3][DIM], wt[3][3];
 #pragma unroll
-          for (int q = 0; q < DIM; ++q) out[q] = fmaf(w, __ldcg(src + DIM * ni + q), out[q]);
+      for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+        for (int dx = 0; dx < 3; ++dx) {
+          const int ix = px + dx - 1, iy = py + dy - 1;
+          const bool in = ix >= 0 && ix < F.nnx && iy >= 0 && iy < F.nny;
+          const float w = in ? mg_w1(ix, I, F.nnx) * mg_w1(iy, J, F.nny) * wz : 0.f;
+          wt[dy][dx] = w;
+          const long long ni = w != 0.f ? ix + (long long)F.nnx * (iy + (long long)F.nny * iz) : 0;
+#pragma unroll
+          for (int q = 0; q < DIM; ++q) v[dy][dx][q] = w != 0.f ? __ldcg(src + DIM * ni + q) : 0.f;
         }
+#pragma unroll
+      for (int q = 0; q < DIM; ++q) {
+        float t = out[q];
+#pragma unroll
+        for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+          for (int dx = 0; dx < 3; ++dx) t = fmaf(wt[dy][dx], v[dy][dx][q], t);
+        out[q] = t;
       }
     }
   };
-  // (P x_c) at fine node (i, j, k) of level l from level l + 1
+  // (P x_c) at fine node (i, j, k) of level l from level l + 1: parents in [i/2, i/2 + 1] per
+  // direction, unrolled the same way
   auto prolong_node = [&](int l, const float* src, int i, int j, int k, float* out) {
     const MgLevel& F = a.mg.lv[l];
     const MgLevel& Cc = a.mg.lv[l + 1];
+    constexpr int NZ = DIM == 3 ? 2 : 1;
+    float v[NZ][2][2][DIM], wt[NZ][2][2];
 #pragma unroll
-    for (int q = 0; q < DIM; ++q) out[q] = 0.f;
-    for (int Kz = (DIM == 3 ? k / 2 : 0); Kz <= (DIM == 3 ? min(k / 2 + 1, Cc.nnz - 1) : 0); ++Kz) {
-      const float wz = DIM == 3 ? mg_w1(k, Kz, F.nnz) : 1.f;
-      if (wz == 0.f) continue;
-      for (int Jy = j / 2; Jy <= min(j / 2 + 1, Cc.nny - 1); ++Jy) {
-        const float wy = mg_w1(j, Jy, F.nny) * wz;
-        if (wy == 0.f) continue;
-        for (int Ix = i / 2; Ix <= min(i / 2 + 1, Cc.nnx - 1); ++Ix) {
-          const float w = mg_w1(i, Ix, F.nnx) * wy;
-          if (w == 0.f) continue;
-          const long long mc = Ix + (long long)Cc.nnx * (Jy + (long long)Cc.nny * Kz);
+    for (int dz = 0; dz < NZ; ++dz)
 #pragma unroll
-          for (int q = 0; q < DIM; ++q) out[q] = fmaf(w, __ldcg(src + DIM * mc + q), out[q]);
+      for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+        for (int dx = 0; dx < 2; ++dx) {
+          const int Ix = i / 2 + dx, Jy = j / 2 + dy, Kz = DIM == 3 ? k / 2 + dz : 0;
+          const bool in = Ix < Cc.nnx && Jy < Cc.nny && Kz < Cc.nnz;
+          const float w = in ? mg_w1(i, Ix, F.nnx) * mg_w1(j, Jy, F.nny) * (DIM == 3 ? mg_w1(k, Kz, F.nnz) : 1.f) : 0.f;
+          wt[dz][dy][dx] = w;
+          const long long mc = w != 0.f ? Ix + (long long)Cc.nnx * (Jy + (long long)Cc.nny * Kz) : 0;
+#pragma unroll
+          for (int q = 0; q < DIM; ++q) v[dz][dy][dx][q] = w != 0.f ? __ldcg(src + DIM * mc + q) : 0.f;
         }
-      }
+#pragma unroll
+    for (int q = 0; q < DIM; ++q) {
+      float t = 0.f;
+#pragma unroll
+      for (int dz = 0; dz < NZ; ++dz)
+#pragma unroll
+        for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+          for (int dx = 0; dx < 2; ++dx) t = fmaf(wt[dz][dy][dx], v[dz][dy][dx][q], t);
+      out[q] = t;
     }
   };
   auto fixed_lv = [&](int l, long long dof) -> bool {
@@ -769,7 +816,7 @@ __device__ __forceinline__ void pcg2_body(const Pcg2Args<DIM>& a, const unsigned
           for (int q = 0; q < DIM; ++q) bb[DIM * n + q] = b[q];
         }
 #pragma unroll
-        for (int q = 0; q < DIM; ++q) x0[DIM * n + q] = __ldcg(Lv.dinv + DIM * n + q) * b[q] * ith;
+        for (int q = 0; q < DIM; ++q) x0[DIM * n + q] = __ldca(Lv.dinv + DIM * n + q) * b[q] * ith;
       });
     }
   };
@@ -790,7 +837,7 @@ __device__ __forceinline__ void pcg2_body(const Pcg2Args<DIM>& a, const unsigned
         for (int q = 0; q < DIM; ++q) {
           const long long dof = DIM * n + q;
           const float prev = xpp ? __ldcg(xpp + dof) : 0.f;
-          const float d = fmaf(c1, own[q] - prev, c2 * __ldcg(Lv.dinv + dof) * (rhs(l, c, dof) - y[q]));
+          const float d = fmaf(c1, own[q] - prev, c2 * __ldca(Lv.dinv + dof) * (rhs(l, c, dof) - y[q]));
           xout[dof] = own[q] + d;
         }
       });
@@ -852,7 +899,7 @@ __device__ __forceinline__ void pcg2_body(const Pcg2Args<DIM>& a, const unsigned
 #pragma unroll
         for (int q = 0; q < DIM; ++q) {
           const long long dof = DIM * n + q;
-          const float dr = __ldcg(Lv.dinv + dof) * (rhs(l, c, dof) - y[q]);
+          const float dr = __ldca(Lv.dinv + dof) * (rhs(l, c, dof) - y[q]);
           const float d = jj ? fmaf(c1, own[q] - __ldcg(yprev + dof), c2 * dr) : dr * ith;
           const float out = own[q] + d;
           if (last0) {
@@ -1312,7 +1359,7 @@ topo_status build_pcg2_args(topo_ctx* c, const double* rho, const double* F, dou
   // vectors of every level, the dense coarsest operator and its inverse
   MgArgs mga = {};
   size_t omg[MG_MAX_LEVELS][5] = {};
-  size_t oA = 0, oAi = 0, olm = 0, ook = 0;
+  size_t oAi = 0, olm = 0, ook = 0;
   if (mg) {
     const int deg = c->mg_deg;
     int nn[3] = {g.nnx, g.nny, g.nnz};
@@ -1355,7 +1402,6 @@ topo_status build_pcg2_args(topo_ctx* c, const double* rho, const double* F, dou
         }
         omg[l][4] = take((size_t)mg_slots(deg) * m * Lv.ndof * 4);
       }
-      oA = take((size_t)mga.nc * mga.nc * 8);
       oAi = take((size_t)mga.nc * mga.nc * 4);
       olm = take((size_t)MG_MAX_LEVELS * G * 8);
       ook = take(16);
@@ -1410,7 +1456,6 @@ topo_status build_pcg2_args(topo_ctx* c, const double* rho, const double* F, dou
       }
       Lv.v = (float*)(base + omg[l][4]);
     }
-    a.mg.A = (double*)(base + oA);
     a.mg.Ainv = (float*)(base + oAi);
     a.mg.lmax = (double*)(base + olm);
     a.mg.coarse_ok = (int*)(base + ook);
@@ -1489,9 +1534,13 @@ topo_status solve_stencil_fp64(topo_ctx* c, const double* rho, const double* F, 
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  if (use_mg)
+  if (use_mg) {
+    // the coarsest operator's packed factor and one column, in shared memory (setup only)
+    const size_t dyn = ((size_t)a.mg.nc * (a.mg.nc + 1) / 2 + a.mg.nc) * sizeof(double);
+    TOPO_CUDA_TRY(c, cudaFuncSetAttribute(pcg2_mg_kernel<DIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+    cfg.dynamicSmemBytes = dyn;
     TOPO_CUDA_TRY(c, cudaLaunchKernelEx(&cfg, pcg2_mg_kernel<DIM>, a));
-  else
+  } else
     TOPO_CUDA_TRY(c, cudaLaunchKernelEx(&cfg, pcg2_kernel<DIM>, a));
   note_launch();
   if (info_host) {

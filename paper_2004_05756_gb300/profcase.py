@@ -24,7 +24,8 @@ if ROOT not in sys.path:
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--call", required=True, choices=["pcg", "hdm", "apply", "rom_elem", "rom_solve_elem", "rom_solve",
-                                                      "rom_error", "grad", "filter"])
+                                                      "rom_error", "grad", "filter", "rom_eval_batch"])
+    ap.add_argument("--R", type=int, default=100, help="rom_eval_batch: candidates per call")
     ap.add_argument("--shape", default="600x200")
     ap.add_argument("--prec", default="fp64")
     ap.add_argument("--m", type=int, default=1)
@@ -82,6 +83,12 @@ def main(argv=None):
         rn = torch.zeros(2, **f64)
         if a.call != "rom_elem":
             T.topo_rom_elem(Phi, k, Hel)
+        if a.call == "rom_eval_batch":
+            cands = torch.as_tensor(w.perturbed_designs(p, w.design_field(p, 0), a.R, amplitude=0.02,
+                                                        first_seed=2000).T.copy()).to(**f64)
+            JkR = torch.zeros(a.R, **f64)
+            rnR = torch.zeros((a.R, 2), **f64)
+            dpR = torch.zeros((a.R, p.nel), **f64)
     dt = torch.float64 if a.prec == "fp64" else torch.float32
     ldp = -(-p.ndof // a.ld_pad) * a.ld_pad
     V = torch.randn((a.m, ldp), dtype=dt, device="cuda")[:, :p.ndof]
@@ -108,6 +115,8 @@ def main(argv=None):
             T.topo_rom_solve_elem(rho, Hel, k, b, Hw, y, Jk)
         elif a.call == "rom_solve":
             T.topo_rom_solve(rho, Phi, k, b, Hw, y, Jk, a.prec)
+        elif a.call == "rom_eval_batch":
+            T.topo_rom_eval_batch(cands, Hel, Phi, k, b, F[0], JkR, rnR, None, dpR)
         elif a.call == "rom_error":
             T.topo_rom_error(rho, Phi, k, y, F[0], rn)
         elif a.call == "grad":
