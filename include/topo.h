@@ -127,9 +127,12 @@ typedef enum {
   TOPO_PARAM_MG_DEGREE = 13,       /* multigrid: Chebyshev smoothing steps before and after the
                                       coarse correction, 1 .. 4 (default 2) */
   TOPO_PARAM_MG_SINGLE_NODES = 14  /* multigrid: coarse levels with at most this many nodes run on
-                                      one CTA with block barriers instead of grid-wide halo
-                                      exchanges (default 0: only the coarsest level; level 0
-                                      always runs on all CTAs) */
+                                      one CTA, their vectors in its shared memory, with block
+                                      barriers instead of halo exchanges between CTAs (default
+                                      -1: 1024 in 2D, 0 in 3D; levels whose vectors do not fit
+                                      96 KB with those of
+                                      the coarser levels stay on all CTAs; the coarsest level
+                                      always runs on one CTA and level 0 never does) */
 } topo_param;
 
 /* Create a context for one problem; computes K_e (2x2(x2) Gauss quadrature), the filter

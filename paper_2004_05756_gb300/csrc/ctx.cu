@@ -398,7 +398,7 @@ extern "C" topo_status topo_create(const topo_problem* prob, void* cuda_stream, 
   c->pcg_poly = 0;
   c->pcg_mg = 1;
   c->mg_deg = 2;
-  c->mg_single_nodes = 0;
+  c->mg_single_nodes = -1;
   c->rom_refine = 8;
   c->pcg_blocks_per_sm = 0;
   c->inner_cap = 2000;
@@ -596,8 +596,8 @@ extern "C" topo_status topo_set_param(topo_ctx* c, topo_param which, double v) {
       c->mg_deg = (int)v;
       return TOPO_OK;
     case TOPO_PARAM_MG_SINGLE_NODES:
-      if (!(v >= 0 && v <= 1e9 && v == (long long)v))
-        return fail(c, TOPO_ERR_INVALID, "mg single-CTA node count must be an integer in [0,1e9]");
+      if (!(v >= -1 && v <= 1e9 && v == (long long)v))
+        return fail(c, TOPO_ERR_INVALID, "mg single-CTA node count must be an integer in [-1,1e9]");
       c->mg_single_nodes = (long long)v;
       return TOPO_OK;
     case TOPO_PARAM_PCG_BLOCKS_PER_SM:

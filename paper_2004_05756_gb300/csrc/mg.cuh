@@ -30,6 +30,7 @@ constexpr int MG_MAX_LEVELS = 12;
 constexpr int MG_MAX_DEG = 4;          // Chebyshev smoothing steps per side
 constexpr int MG_COARSE_MAX = 160;     // DOFs of the coarsest level (dense inverse)
 constexpr double MG_RATIO = 30.0;      // Chebyshev interval [lambda_max / 30, lambda_max]
+constexpr size_t MG_TAIL_BYTES = 96 * 1024;  // shared memory for the vectors of the levels on CTA 0
 
 struct MgLevel {
   int nnx, nny, nnz;
@@ -49,6 +50,8 @@ struct MgArgs {
   float* Ainv;    // inverse of the coarsest operator, nc x nc FP32 (factorised in FP64 per solve)
   double* lmax;   // per-level Gershgorin partials [MG_MAX_LEVELS][G]
   int* coarse_ok; // 1 when the coarsest factorisation succeeded (else no coarse correction)
+  int tail_off[MG_MAX_LEVELS];  // levels ls .. L - 1: float offset of their vectors in shared memory
+  int tail_floats;              // floats of shared memory those vectors take
   MgLevel lv[MG_MAX_LEVELS];
 };
 

@@ -177,7 +177,7 @@ __device__ __forceinline__ void stencil_apply(const Grid& g, const double* __res
 // the coefficients (read-only after the setup, written by the reading thread or before a grid
 // barrier for levels run by one CTA) stay in L1: a CTA's share of a level fits there. In 3D
 // (243 per node) they do not, and come from L2 like v, which other CTAs write during the solve.
-template <int DIM>
+template <int DIM, bool SMEMV = false>
 __device__ __forceinline__ void stencil_apply32(const Grid& g, const float* __restrict__ C, const float* v, int i,
                                                 int j, int k, long long n, float* y, float* vown) {
   constexpr int NB = StencilGeom<DIM>::NB;
@@ -191,7 +191,7 @@ __device__ __forceinline__ void stencil_apply32(const Grid& g, const float* __re
       const int ii = i + nb % 3 - 1, jj = j + nb / 3 - 1;
       const bool nin = ii >= 0 && ii < g.nnx && jj >= 0 && jj < g.nny;
       const long long m = nin ? ii + (long long)g.nnx * jj : n;
-      vv[nb] = __ldcg(reinterpret_cast<const float2*>(v) + m);
+      vv[nb] = SMEMV ? reinterpret_cast<const float2*>(v)[m] : __ldcg(reinterpret_cast<const float2*>(v) + m);
     }
     const float* gp = C + n;
 #pragma unroll
@@ -217,14 +217,14 @@ __device__ __forceinline__ void stencil_apply32(const Grid& g, const float* __re
     const long long m = ii + (long long)g.nnx * (jj + (long long)g.nny * kk);
     float vv[DIM];
 #pragma unroll
-    for (int d = 0; d < DIM; ++d) vv[d] = __ldcg(v + DIM * m + d);
+    for (int d = 0; d < DIM; ++d) vv[d] = SMEMV ? v[DIM * m + d] : __ldcg(v + DIM * m + d);
 #pragma unroll
     for (int r = 0; r < DIM; ++r)
 #pragma unroll
       for (int d = 0; d < DIM; ++d) y[r] = fmaf(__ldcg(C + (long long)((nb * DIM + r) * DIM + d) * g.nnodes + n), vv[d], y[r]);
   }
 #pragma unroll
-  for (int d = 0; d < DIM; ++d) vown[d] = __ldcg(v + DIM * n + d);
+  for (int d = 0; d < DIM; ++d) vown[d] = SMEMV ? v[DIM * n + d] : __ldcg(v + DIM * n + d);
 }
 
 // The solver, run by a group of G co-resident CTAs (this CTA is number `rank` of the group)
@@ -714,9 +714,26 @@ __device__ __forceinline__ void pcg2_body(const Pcg2Args<DIM>& a, const unsigned
       fn(i, j, k, i + (long long)Lv.nnx * (j + (long long)Lv.nny * k));
     }
   };
-  auto mgv = [&](int l, int slot, int c) -> float* {
+  // vectors of the levels run by CTA 0 (ls and coarser) live in its dynamic shared memory
+  extern __shared__ __align__(16) unsigned char mg_tail_dyn[];
+  float* const tail_s = reinterpret_cast<float*>(mg_tail_dyn);
+  auto in_tail = [&](int l) -> bool { return PK == 2 && l >= a.mg.ls; };
+  auto mgv_g = [&](int l, int slot, int c) -> float* {  // the global copy
     const MgLevel& Lv = a.mg.lv[l];
     return Lv.v + ((size_t)slot * m + c) * Lv.ndof;
+  };
+  auto mgv = [&](int l, int slot, int c) -> float* {
+    const MgLevel& Lv = a.mg.lv[l];
+    if (in_tail(l) && rank == 0) return tail_s + a.mg.tail_off[l] + ((size_t)slot * m + c) * Lv.ndof;
+    return mgv_g(l, slot, c);
+  };
+  auto ldv = [&](int l, const float* p) -> float { return in_tail(l) ? *p : __ldcg(p); };
+  auto apply_lv = [&](int l, const Grid& gl, const float* C32, const float* v, int i, int j, int k, long long n,
+                      float* y, float* own) {
+    if (in_tail(l))
+      stencil_apply32<DIM, true>(gl, C32, v, i, j, k, n, y, own);
+    else
+      stencil_apply32<DIM, false>(gl, C32, v, i, j, k, n, y, own);
   };
   auto colskip = [&](bool all_cols, int c) -> bool { return !all_cols && sh_done[c]; };
   // b at coarse node (I, J, K) of level l = P^T r of level l - 1 (its residual slot). The 3^d
@@ -743,7 +760,7 @@ __device__ __forceinline__ void pcg2_body(const Pcg2Args<DIM>& a, const unsigned
           wt[dy][dx] = w;
           const long long ni = w != 0.f ? ix + (long long)F.nnx * (iy + (long long)F.nny * iz) : 0;
 #pragma unroll
-          for (int q = 0; q < DIM; ++q) v[dy][dx][q] = w != 0.f ? __ldcg(src + DIM * ni + q) : 0.f;
+          for (int q = 0; q < DIM; ++q) v[dy][dx][q] = w != 0.f ? ldv(l - 1, src + DIM * ni + q) : 0.f;
         }
 #pragma unroll
       for (int q = 0; q < DIM; ++q) {
@@ -775,7 +792,7 @@ __device__ __forceinline__ void pcg2_body(const Pcg2Args<DIM>& a, const unsigned
           wt[dz][dy][dx] = w;
           const long long mc = w != 0.f ? Ix + (long long)Cc.nnx * (Jy + (long long)Cc.nny * Kz) : 0;
 #pragma unroll
-          for (int q = 0; q < DIM; ++q) v[dz][dy][dx][q] = w != 0.f ? __ldcg(src + DIM * mc + q) : 0.f;
+          for (int q = 0; q < DIM; ++q) v[dz][dy][dx][q] = w != 0.f ? ldv(l, src + DIM * mc + q) : 0.f;
         }
 #pragma unroll
     for (int q = 0; q < DIM; ++q) {
@@ -794,7 +811,7 @@ __device__ __forceinline__ void pcg2_body(const Pcg2Args<DIM>& a, const unsigned
   };
   // right-hand side of level l at a DOF: the CG residual (level 0) or the restricted residual
   auto rhs = [&](int l, int c, long long dof) -> float {
-    return l == 0 ? (float)a.r[(size_t)c * N + dof] : __ldcg(mgv(l, mg_slot_b(a.mg.deg), c) + dof);
+    return l == 0 ? (float)a.r[(size_t)c * N + dof] : ldv(l, mgv(l, mg_slot_b(a.mg.deg), c) + dof);
   };
   // pre-smoothing step 0 (from zero): x_0 = D^-1 b / theta; for l >= 1 b is restricted first
   auto mg_pre0 = [&](int l, bool single, bool all_cols) {
@@ -832,11 +849,11 @@ __device__ __forceinline__ void pcg2_body(const Pcg2Args<DIM>& a, const unsigned
       float* xout = mgv(l, jj, c);
       for_lv(l, single, [&](int i, int j, int k, long long n) {
         float y[DIM], own[DIM];
-        stencil_apply32<DIM>(gl, Lv.C32, xin, i, j, k, n, y, own);
+        apply_lv(l, gl, Lv.C32, xin, i, j, k, n, y, own);
 #pragma unroll
         for (int q = 0; q < DIM; ++q) {
           const long long dof = DIM * n + q;
-          const float prev = xpp ? __ldcg(xpp + dof) : 0.f;
+          const float prev = xpp ? ldv(l, xpp + dof) : 0.f;
           const float d = fmaf(c1, own[q] - prev, c2 * __ldca(Lv.dinv + dof) * (rhs(l, c, dof) - y[q]));
           xout[dof] = own[q] + d;
         }
@@ -853,7 +870,7 @@ __device__ __forceinline__ void pcg2_body(const Pcg2Args<DIM>& a, const unsigned
       float* res = mgv(l, mg_slot_res(a.mg.deg), c);
       for_lv(l, single, [&](int i, int j, int k, long long n) {
         float y[DIM], own[DIM];
-        stencil_apply32<DIM>(gl, Lv.C32, xin, i, j, k, n, y, own);
+        apply_lv(l, gl, Lv.C32, xin, i, j, k, n, y, own);
 #pragma unroll
         for (int q = 0; q < DIM; ++q) res[DIM * n + q] = rhs(l, c, DIM * n + q) - y[q];
       });
@@ -864,7 +881,9 @@ __device__ __forceinline__ void pcg2_body(const Pcg2Args<DIM>& a, const unsigned
     const int deg = a.mg.deg;
     for (int c = 0; c < m; ++c) {
       if (colskip(all_cols, c)) continue;
-      const float* xc = (l + 1 == a.mg.L - 1) ? mgv(l + 1, 0, c) : mgv(l + 1, mg_slot_post(deg, deg), c);
+      // level l + 1's result: for l + 1 == ls the global copy CTA 0 leaves for the other CTAs
+      const int so = (l + 1 == a.mg.L - 1) ? 0 : mg_slot_post(deg, deg);
+      const float* xc = (l + 1 == a.mg.ls) ? mgv_g(l + 1, so, c) : mgv(l + 1, so, c);
       const float* xin = mgv(l, deg - 1, c);
       float* y0 = mgv(l, mg_slot_post(deg, 0), c);
       for_lv(l, single, [&](int i, int j, int k, long long n) {
@@ -873,7 +892,7 @@ __device__ __forceinline__ void pcg2_body(const Pcg2Args<DIM>& a, const unsigned
 #pragma unroll
         for (int q = 0; q < DIM; ++q) {
           const long long dof = DIM * n + q;
-          y0[dof] = __ldcg(xin + dof) + (fixed_lv(l, dof) ? 0.f : p[q]);
+          y0[dof] = ldv(l, xin + dof) + (fixed_lv(l, dof) ? 0.f : p[q]);
         }
       });
     }
@@ -895,12 +914,12 @@ __device__ __forceinline__ void pcg2_body(const Pcg2Args<DIM>& a, const unsigned
       double ag = 0.0;
       for_lv(l, single, [&](int i, int j, int k, long long n) {
         float y[DIM], own[DIM];
-        stencil_apply32<DIM>(gl, Lv.C32, yin, i, j, k, n, y, own);
+        apply_lv(l, gl, Lv.C32, yin, i, j, k, n, y, own);
 #pragma unroll
         for (int q = 0; q < DIM; ++q) {
           const long long dof = DIM * n + q;
           const float dr = __ldca(Lv.dinv + dof) * (rhs(l, c, dof) - y[q]);
-          const float d = jj ? fmaf(c1, own[q] - __ldcg(yprev + dof), c2 * dr) : dr * ith;
+          const float d = jj ? fmaf(c1, own[q] - ldv(l, yprev + dof), c2 * dr) : dr * ith;
           const float out = own[q] + d;
           if (last0) {
             const double zd = (double)out;
@@ -936,7 +955,8 @@ __device__ __forceinline__ void pcg2_body(const Pcg2Args<DIM>& a, const unsigned
       float* xs = mgv(l, 0, c);
       for (int row = warp; row < nc; row += nwarps) {
         float t = 0.f;
-        for (int q = lane; q < nc; q += 32) t = fmaf(__ldcg(a.mg.Ainv + (size_t)row * nc + q), __ldcg(bc + q), t);
+#pragma unroll 5
+        for (int q = lane; q < nc; q += 32) t = fmaf(__ldca(a.mg.Ainv + (size_t)row * nc + q), bc[q], t);
         for (int o = 16; o; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
         if (lane == 0) xs[row] = t;
       }
@@ -983,6 +1003,14 @@ __device__ __forceinline__ void pcg2_body(const Pcg2Args<DIM>& a, const unsigned
             mg_post(l, jj, true, all_cols);
             __syncthreads();
           }
+        }
+        // level ls's result, from shared memory to its global copy, for level ls - 1
+        const int so = (ls == L - 1) ? 0 : mg_slot_post(deg, deg);
+        for (int c = 0; c < m; ++c) {
+          if (colskip(all_cols, c)) continue;
+          const float* src = mgv(ls, so, c);
+          float* dst = mgv_g(ls, so, c);
+          for (long long t = threadIdx.x; t < a.mg.lv[ls].ndof; t += blockDim.x) dst[t] = src[t];
         }
       }
     }
@@ -1384,14 +1412,31 @@ topo_status build_pcg2_args(topo_ctx* c, const double* rho, const double* F, dou
     mga.deg = deg;
     mga.nc = (int)mga.lv[L - 1].ndof;
     if (L >= 2 && mga.nc <= MG_COARSE_MAX) {
-      // levels from the first with at most mg_single_nodes nodes run on CTA 0 (level 0 never)
+      // Levels ls .. L - 1 run on CTA 0 with their vectors in its shared memory: the first level
+      // (never level 0) with at most mg_single_nodes nodes whose vectors, with those of all
+      // coarser levels, fit MG_TAIL_BYTES; at least the coarsest level.
+      auto tail_floats = [&](int l0) {
+        size_t t = 0;
+        for (int l = l0; l < L; ++l) t += (((size_t)mg_slots(deg) * m * mga.lv[l].ndof + 3) & ~(size_t)3);
+        return t;
+      };
+      // -1: 1024 nodes in 2D (measured best at 600x200); in 3D only the coarsest level, whose
+      // 243-coefficient stencils do not stay in one SM's L1 at coarse sizes
+      const long long single = c->mg_single_nodes >= 0 ? c->mg_single_nodes : (DIM == 2 ? 1024 : 0);
       int ls = L - 1;
       for (int l = 1; l < L; ++l)
-        if (mga.lv[l].nnodes <= c->mg_single_nodes) {
+        if (mga.lv[l].nnodes <= single && tail_floats(l) * 4 <= MG_TAIL_BYTES) {
           ls = l;
           break;
         }
       mga.ls = ls;
+      size_t toff = 0;
+      for (int l = 0; l < MG_MAX_LEVELS; ++l) mga.tail_off[l] = 0;
+      for (int l = ls; l < L; ++l) {
+        mga.tail_off[l] = (int)toff;
+        toff += ((size_t)mg_slots(deg) * m * mga.lv[l].ndof + 3) & ~(size_t)3;
+      }
+      mga.tail_floats = (int)toff;
       for (int l = 0; l < L; ++l) {
         const MgLevel& Lv = mga.lv[l];
         if (l > 0) {
@@ -1535,8 +1580,10 @@ topo_status solve_stencil_fp64(topo_ctx* c, const double* rho, const double* F, 
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   if (use_mg) {
-    // the coarsest operator's packed factor and one column, in shared memory (setup only)
-    const size_t dyn = ((size_t)a.mg.nc * (a.mg.nc + 1) / 2 + a.mg.nc) * sizeof(double);
+    // shared memory: the coarsest operator's packed factor and one column (setup), then the
+    // vectors of the levels CTA 0 runs alone (the V-cycle)
+    const size_t dyn = std::max(((size_t)a.mg.nc * (a.mg.nc + 1) / 2 + a.mg.nc) * sizeof(double),
+                                (size_t)a.mg.tail_floats * sizeof(float));
     TOPO_CUDA_TRY(c, cudaFuncSetAttribute(pcg2_mg_kernel<DIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
     cfg.dynamicSmemBytes = dyn;
     TOPO_CUDA_TRY(c, cudaLaunchKernelEx(&cfg, pcg2_mg_kernel<DIM>, a));

@@ -43,7 +43,8 @@ def main(argv=None):
     ap.add_argument("--rtol", type=float, default=1e-30, help="pcg/hdm: relative residual target")
     ap.add_argument("--mg", type=int, default=1, help="FP64 solve: 1 multigrid preconditioner, 0 polynomial")
     ap.add_argument("--mg-deg", type=int, default=2, help="multigrid: Chebyshev smoothing steps per side")
-    ap.add_argument("--mg-single", type=int, default=0, help="multigrid: nodes of levels run on one CTA")
+    ap.add_argument("--mg-single", type=int, default=-1,
+                    help="multigrid: nodes of levels run on one CTA (-1: the library's default)")
     a = ap.parse_args(argv)
     import torch
 

@@ -82,7 +82,7 @@ def test_mg_solve_matches_oracle(torch, case):
 
 
 @pytest.mark.parametrize("deg", [1, 2, 3, 4])
-@pytest.mark.parametrize("single", [0, 2048, 10 ** 9])
+@pytest.mark.parametrize("single", [-1, 0, 2048, 10 ** 9])
 def test_mg_degree_and_single_cta_levels(torch, deg, single):
     from paper_2004_05756_gb300.native import Topo, TOPO_PARAM_MG_DEGREE, TOPO_PARAM_MG_SINGLE_NODES
     p = CASES["q4_130x41"]()
@@ -139,10 +139,10 @@ def test_mg_parameter_ranges(torch):
         T.topo_set_param(TOPO_PARAM_PCG_MG, v)
     for v in (1, 2, 3, 4):
         T.topo_set_param(TOPO_PARAM_MG_DEGREE, v)
-    for v in (0, 1, 2048, 10 ** 9):
+    for v in (-1, 0, 1, 2048, 10 ** 9):
         T.topo_set_param(TOPO_PARAM_MG_SINGLE_NODES, v)
     for which, bad in ((TOPO_PARAM_PCG_MG, 2), (TOPO_PARAM_MG_DEGREE, 0), (TOPO_PARAM_MG_DEGREE, 5),
-                       (TOPO_PARAM_MG_DEGREE, 1.5), (TOPO_PARAM_MG_SINGLE_NODES, -1)):
+                       (TOPO_PARAM_MG_DEGREE, 1.5), (TOPO_PARAM_MG_SINGLE_NODES, -2)):
         with pytest.raises(TopoError):
             T.topo_set_param(which, bad)
 
