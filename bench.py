@@ -32,17 +32,17 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-# DRAM bytes (read + write) of one pcg2_kernel launch of the default step, from a one-pass ncu
-# capture (dram__bytes_read.sum, dram__bytes_write.sum) of
-# `python bench.py --steps 1 --warmup 3 --no-cpu-baseline`. It is reported only while the kernel
-# sources hash to the value they had when it was taken.
-PCG_TRAFFIC = {"bytes": 189.64e6 + 229.73e6, "sources_sha256_16": "e9afb547dd722423"}
+# DRAM bytes (read + write) of one launch of the HDM solve kernel (pcg2_mg_kernel) at MBB 600x200,
+# rtol 1e-8, from a full ncu capture (dram__bytes_read.sum, dram__bytes_write.sum) of
+# `python -m paper_2004_05756_gb300.profcase --call hdm --rtol 1e-8 --reps 1`. It is reported only
+# while the kernel sources hash to the value they had when it was taken.
+PCG_TRAFFIC = {"bytes": 168.303104e6 + 267.38432e6, "sources_sha256_16": "5ba5bc210325e492"}
 
 
 def pcg_traffic():
     import hashlib
     h = hashlib.sha256()
-    for f in ("pcg2.cu", "pcg2.cuh", "common.cuh"):
+    for f in ("pcg2.cu", "pcg2.cuh", "common.cuh", "mg.cuh"):
         with open(os.path.join(ROOT, "paper_2004_05756_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return PCG_TRAFFIC["bytes"] if h.hexdigest()[:16] == PCG_TRAFFIC["sources_sha256_16"] else None
