@@ -344,7 +344,8 @@ def run_ours(args, rank, world):
         T.topo_compliance_grad(rho, Uc, F, J, dc, dpsi)
         e1.record(stream)
         Usnap[s % k].copy_(Uc[0])
-        kk = T.topo_rom_build(rho, Usnap, Phi, H, b, f)
+        # the element path forms H(rho) per density from Hel: the build forms Phi and b only
+        kk = T.topo_rom_build(rho, Usnap, Phi, None if Hel is not None else H, b, f)
         if Hel is not None:
             T.topo_rom_elem(Phi[:kk], kk, Hel)
         e2.record(stream)

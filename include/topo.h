@@ -186,8 +186,9 @@ topo_status topo_solve_hdm(topo_ctx* ctx, const double* rho, const double* F, do
  * N x m, ld) in order, dropping a column whose orthogonalised norm is < 1e-10 times the
  * largest snapshot norm. Writes the k kept orthonormal columns to Phi (FP64, capacity
  * N x m, same ld), then H = Phi^T K(rho) Phi (FP64 k x k, row-major, leading dimension k,
- * capacity m*m) and b = Phi^T f (FP64[k]; f FP64[N]) (Eq. hatkbm). k_out is a HOST int;
- * the call synchronises to return it. Usnap and Phi may be the same buffer. */
+ * capacity m*m) and b = Phi^T f (FP64[k]; f FP64[N]) (Eq. hatkbm). H may be NULL: then only
+ * Phi and b are formed (the element path forms H(rho) per density from topo_rom_elem). k_out
+ * is a HOST int; the call synchronises to return it. Usnap and Phi may be the same buffer. */
 topo_status topo_rom_build(topo_ctx* ctx, const double* rho, const double* Usnap, int m, int ld,
                            double* Phi, int* k_out, double* H, double* b, const double* f);
 

@@ -139,14 +139,22 @@ __global__ void atv_partial_kernel(const double* __restrict__ A, long long lda, 
   }
 }
 
-// out[j] = (subtract ? base[j] - s : s), s = sum_g partial[g * k + j] (fixed order).
+// out[j] = (subtract ? base[j] - s : s), s = sum_g partial[g * k + j]: one warp per j, lanes
+// summing g = lane, lane + 32, ... in order, then a shuffle tree (an order fixed by G alone).
 __global__ void atv_final_kernel(const double* partial, int G, int k, double* out, const double* base,
                                  const int* gate) {
   if (gate && *gate == 0) return;
-  for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < k; j += gridDim.x * blockDim.x) {
-    double s = 0.0;
-    for (int g = 0; g < G; ++g) s += partial[(size_t)g * k + j];
-    out[j] = base ? base[j] - s : s;
+  const int l = threadIdx.x & 31, nw = (gridDim.x * blockDim.x) >> 5;
+  for (int j = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < k; j += nw) {
+    double s0 = 0.0, s1 = 0.0;
+    int g = l;
+    for (; g + 32 < G; g += 64) {
+      s0 += __ldcg(partial + (size_t)g * k + j);
+      s1 += __ldcg(partial + (size_t)(g + 32) * k + j);
+    }
+    if (g < G) s0 += __ldcg(partial + (size_t)g * k + j);
+    const double s = warp_sum(s0 + s1);
+    if (l == 0) out[j] = base ? base[j] - s : s;
   }
 }
 
@@ -465,7 +473,7 @@ static topo_status launch_atv(topo_ctx* c, const double* A, long long lda, int k
   if ((size_t)rs.G * k > partial_cap) return fail(c, TOPO_ERR_INVALID, "internal: atv partial buffer too small");
   atv_partial_kernel<<<rs.G, 256, 0, c->stream>>>(A, lda, k, v, N, rs.rows, partial_buf, gate);
   note_launch();
-  atv_final_kernel<<<1, 128, 0, c->stream>>>(partial_buf, rs.G, k, out, base, gate);
+  atv_final_kernel<<<(k + 7) / 8, 256, 0, c->stream>>>(partial_buf, rs.G, k, out, base, gate);
   note_launch();
   TOPO_CUDA_TRY(c, cudaGetLastError());
   return TOPO_OK;
@@ -600,7 +608,8 @@ extern "C" topo_status topo_rom_build(topo_ctx* c, const double* rho, const doub
   *k_out = 0;
   if (m < 1 || m > 128) return fail(c, TOPO_ERR_INVALID, "topo_rom_build: 1 <= m <= 128");
   if ((long long)ld < N) return fail(c, TOPO_ERR_INVALID, "topo_rom_build: ld < N");
-  if (!dev_ptr_ok(rho) || !dev_ptr_ok(Usnap) || !dev_ptr_ok(Phi) || !dev_ptr_ok(H) || !dev_ptr_ok(b) || !dev_ptr_ok(f))
+  if (!dev_ptr_ok(rho) || !dev_ptr_ok(Usnap) || !dev_ptr_ok(Phi) || (H && !dev_ptr_ok(H)) || !dev_ptr_ok(b) ||
+      !dev_ptr_ok(f))
     return fail(c, TOPO_ERR_INVALID, "topo_rom_build: null or misaligned pointer");
   size_t pcap = partial_capacity(c, N, m);
   size_t need = std::max(project_scratch(c, m, ld, TOPO_FP64), (pcap + 2 * 128 + 64) * sizeof(double));
@@ -656,6 +665,7 @@ extern "C" topo_status topo_rom_build(topo_ctx* c, const double* rho, const doub
   TOPO_CUDA_TRY(c, cudaGetLastError());
   *k_out = k;
   if (k == 0) return TOPO_OK;
+  if (!H) return launch_atv(c, Phi, ld, k, f, N, partial, pcap, b, nullptr);  // b = Phi^T f only
   return project(c, rho, Phi, k, ld, TOPO_FP64, H, b, f, scratch);
 }
 

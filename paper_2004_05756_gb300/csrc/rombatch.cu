@@ -68,14 +68,18 @@ __global__ void __launch_bounds__(256) assemble_multi_partial_kernel(const doubl
     for (int q = 0; q < nr; ++q) partial[((size_t)blockIdx.x * nr + q) * npair + p] = acc[q];
 }
 
-// H_r (k x k row-major, symmetric) = sum over the G partials in CTA order, for the nr candidates.
+// H_r (k x k row-major, symmetric) = sum over the G partials, for the nr candidates: a warp
+// per entry, lanes summing g = lane, lane + 32, ... in order, then a shuffle tree (fixed order).
 __global__ void assemble_multi_final_kernel(const double* __restrict__ partial, int G, int k, int nr, double* H) {
   const int npair = k * (k + 1) / 2;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < (long long)nr * npair;
-       t += (long long)gridDim.x * blockDim.x) {
+  const int l = threadIdx.x & 31;
+  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long t = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; t < (long long)nr * npair; t += nw) {
     const int q = (int)(t / npair), p = (int)(t % npair);
     double s = 0.0;
-    for (int g = 0; g < G; ++g) s += __ldcg(partial + ((size_t)g * nr + q) * npair + p);
+    for (int g = l; g < G; g += 32) s += __ldcg(partial + ((size_t)g * nr + q) * npair + p);
+    s = warp_sum(s);
+    if (l != 0) continue;
     int i = 0, rem = p;
     while (rem >= k - i) {
       rem -= k - i;
@@ -179,8 +183,8 @@ extern "C" topo_status topo_rom_eval_batch(topo_ctx* c, int R, const double* psi
     assemble_multi_partial_kernel<<<dim3((unsigned)G, (npair + 255) / 256), std::min(256, ((npair + 31) / 32) * 32), 0,
                                     c->stream>>>(Hel, E, rows, npair, nr, per, part);
     note_launch();
-    assemble_multi_final_kernel<<<(int)std::min<long long>(4LL * c->num_sms, ((long long)nr * npair + 127) / 128), 128,
-                                  0, c->stream>>>(part, (int)G, k, nr, H);
+    assemble_multi_final_kernel<<<(int)std::min<long long>(8LL * c->num_sms, ((long long)nr * npair + 7) / 8), 256, 0,
+                                  c->stream>>>(part, (int)G, k, nr, H);
     note_launch();
     TOPO_CUDA_TRY(c, cudaGetLastError());
     double* y_g = yhat ? yhat + (size_t)r0 * k : ybuf;

@@ -569,3 +569,23 @@ def test_full_size_solve_cant96x48x48_fp64(torch):
     assert abs(Jg - gold["J"]) <= 1e-10 * abs(gold["J"]) + bound, (Jg, gold["J"], bound)
     for i, v in samples:
         assert abs(ug[i] - v) <= 1e-6 * gold["u_norm"], (i, ug[i], v)
+
+
+def test_rom_build_without_H_gives_the_same_basis(torch):
+    """topo_rom_build with H = NULL (the element path's form) writes the same Phi and b, bit for
+    bit, as the full build."""
+    p = CASES["q4_37x13"]()
+    T = ctx_for(p)
+    psi, rho = _design(p)
+    U = _snapshots(p, psi, 6)
+    Ud = cols(U)
+    f = dev(p.F[:, 0])
+    out = []
+    for with_H in (True, False):
+        Phi = torch.zeros_like(Ud)
+        H = torch.zeros(36, dtype=torch.float64, device="cuda") if with_H else None
+        b = torch.zeros(6, dtype=torch.float64, device="cuda")
+        k = T.topo_rom_build(dev(rho), Ud, Phi, H, b, f)
+        out.append((k, Phi.cpu().numpy(), b.cpu().numpy()))
+    assert out[0][0] == out[1][0]
+    assert np.array_equal(out[0][1], out[1][1]) and np.array_equal(out[0][2], out[1][2])
