@@ -270,6 +270,98 @@ topo_status topo_compliance_grad(topo_ctx* ctx, const double* rho, const double*
                                  const double* F, double* J, double* dc_rho, double* dc_psi);
 
 /* ---------------------------------------------------------------------------------------
+ * Trust-region step of one major iteration of the error-aware trust-region method
+ * (Algorithm 2, Section 4.2; Algorithm 1 for the acceptance and radius rule) for compliance.
+ * A run's state lives in device memory and every decision (trial selection, acceptance,
+ * radius) is taken on the device, so a major iteration needs no host read-back:
+ *   topo_tr_project  target psi_x = P_C(psi_c - (move / ||g||_inf) g)   (step 3, subproblem)
+ *   topo_tr_trials   psi_s = psi_c + s (psi_x - psi_c), s = 0, 1, 1/2, ...
+ *   topo_rom_eval_batch on the trials                            (m_k and theta_k, step 3)
+ *   topo_tr_select   the candidate psi_hat and its reduced state
+ *   topo_filter, topo_solve_hdm, topo_compliance_grad at psi_hat      (J(psi_hat), step 4)
+ *   topo_tr_update   varrho_k, acceptance, Delta_{k+1}                (steps 4-6)
+ * The subproblem (step 3) is solved approximately by one projected-gradient step with
+ * backtracking, the Armijo rule along a feasible direction (Bertsekas, Nonlinear Programming,
+ * Section 2.3), stopped at the trust-region constraint as the paper stops its MMA iterations
+ * (end of Section 4.2); the feasible set is convex, so every trial is feasible.
+ * --------------------------------------------------------------------------------------- */
+
+/* Device-resident state of one run (128 bytes, caller-owned device memory, 8-byte aligned). */
+typedef struct {
+  double delta;      /* Delta_k, the current radius (after topo_tr_update: Delta_{k+1}) */
+  double delta_max;  /* Delta_max */
+  double delta_prev; /* the radius the last update started from */
+  double J_c;        /* J(psi^(k)), full-order compliance at the centre */
+  double Jk_c;       /* m_k(psi^(k)), reduced compliance at the centre (trial 0) */
+  double Jk_hat;     /* m_k(psi_hat) */
+  double J_hat;      /* J(psi_hat) */
+  double theta_hat;  /* theta_k(psi_hat) = ||f - K(rho(psi_hat)) u_k(psi_hat)||_2 (Eq. trcon-topopt) */
+  double step;       /* s of the candidate: psi_hat = psi^(k) + s (psi_x - psi^(k)) */
+  double ratio;      /* varrho_k; -inf when the predicted reduction is not positive */
+  double gtd;        /* g . (psi_x - psi^(k)), the slope the decrease test uses */
+  double pad0;
+  int sel;           /* trial index of the candidate (1 .. R-1) */
+  int inside;        /* 1 when the candidate passed both tests of topo_tr_select */
+  int accepted;      /* 1 when psi^(k+1) = psi_hat */
+  int iter;          /* major iterations completed */
+  int pad1[4];
+} topo_tr_state;
+
+/* Host parameters of the acceptance and radius rule (Algorithm 2, steps 5-6) and of the
+ * decrease test. Section 5 uses gamma1 = 0.5, gamma2 = 1, eta1 = 0.1, eta2 = 0.75. */
+typedef struct {
+  double gamma1, gamma2; /* radius factors below eta1 and on [eta1, eta2) */
+  double eta1, eta2;     /* acceptance and very-successful thresholds */
+  double grow;           /* radius factor from eta2 on, capped at delta_max (the paper leaves it open) */
+  double c1;             /* Armijo constant of the decrease test, 0 <= c1 < 1 */
+} topo_tr_params;
+
+/* State of a new run at its first centre: delta = tau ||r(0, rho)||_2 = tau ||f||_2 over the free
+ * DOFs (Eq. trrad0), delta_max = dmax_factor * delta (Section 5: 100), J_c = *J_c (device
+ * scalar, from topo_compliance_grad), every other field zero. f: FP64[N] (device). tau > 0,
+ * dmax_factor >= 1. */
+topo_status topo_tr_init(topo_ctx* ctx, topo_tr_state* st, const double* f, double tau, double dmax_factor,
+                         const double* J_c);
+
+/* out = P_C(psi - tau g), the Euclidean projection onto C = {x in [0,1]^Ne : sum_e x_e <= vmax}
+ * (Eq. feaset-topopt with unit element volumes): out = clip(psi - tau g - mu, 0, 1) with the
+ * volume multiplier mu >= 0 found as the root of a piecewise-linear function, exactly on its
+ * last linear piece. tau = t, or t / max_e |g_e| when scaled != 0 (t is then a move limit in
+ * design units). g may be NULL (a plain projection of psi: the feasibility restoration of a
+ * starting design). With t = 1, scaled = 0 and g = grad J, stats[1] is the criticality measure
+ * ||psi - P_C(psi - grad J)|| of Section 4.1. All FP64[N_e] device arrays; out may alias psi
+ * but not g. stats (device FP64[4]): g.(out - psi) (0 without g), ||out - psi||_2, mu,
+ * sum_e out_e. vmax >= 0 (+inf: box only). Deterministic: the sums run in a fixed order. */
+topo_status topo_tr_project(topo_ctx* ctx, const double* psi, const double* g, double t, int scaled, double vmax,
+                            double* out, double* stats);
+
+/* Trial designs: row r of trials (stride ldt >= N_e) = psi_c + s_r (psi_x - psi_c) with s_0 = 0
+ * and s_r = 2^-(r-1), r = 1 .. R-1 (each rounded once: s_r (psi_x - psi_c) is exact). 2 <= R <= 64. */
+topo_status topo_tr_trials(topo_ctx* ctx, int R, const double* psi_c, const double* psi_x, double* trials, int ldt);
+
+/* The candidate of a trust-region step from the reduced evaluations of the trials (Jk[R] and
+ * resnorm[2R] of topo_rom_eval_batch, yhat[R*k]): the smallest r >= 1 with
+ *   resnorm[2r] <= st->delta  and  Jk[r] <= Jk[0] + (c1 s_r) * gtd,
+ * or r = R - 1 when none passes. Writes st->sel, inside, step, Jk_c = Jk[0], Jk_hat, theta_hat,
+ * gtd (= *gtd, device scalar: stats[0] of the topo_tr_project that formed psi_x), and
+ * psi_hat = trials[sel] (FP64[N_e]), u_hat = Phi y_sel (FP64[N], Phi N x k at ld), the
+ * reduced state at the candidate (the start of its full-order solve). */
+topo_status topo_tr_select(topo_ctx* ctx, topo_tr_state* st, const topo_tr_params* prm, int R, const double* Jk,
+                           const double* resnorm, const double* gtd, const double* trials, int ldt, const double* Phi,
+                           int k, int ld, const double* yhat, double* psi_hat, double* u_hat);
+
+/* Algorithm 2, steps 4-6, after the full-order evaluation of the candidate (J_hat: device
+ * scalar): varrho_k = (J_c - J_hat) / (Jk_c - Jk_hat) (-inf when the denominator is not
+ * positive); accepted = varrho_k >= eta1; delta <- gamma1 delta when not accepted, gamma2 delta
+ * when varrho_k < eta2, else min(grow delta, delta_max). On acceptance J_c <- J_hat and the
+ * candidate's design, state and gradient are copied over the centre's (psi_c, u_c: FP64[N_e],
+ * FP64[N]; g_c <- g_hat, FP64[N_e]) and, when u_slot is not NULL, its state into u_slot (a
+ * column of the snapshot window). Nothing is copied on rejection. */
+topo_status topo_tr_update(topo_ctx* ctx, topo_tr_state* st, const topo_tr_params* prm, const double* J_hat,
+                           double* psi_c, const double* psi_hat, double* u_c, const double* u_hat, double* g_c,
+                           const double* g_hat, double* u_slot);
+
+/* ---------------------------------------------------------------------------------------
  * Batched form: many independent 2D problems (uneven sizes, 1..32 load cases each) behind one
  * handle. Each instance owns a context (topo_batch_context) on the batch's stream, so every
  * single-instance call above also works on it. Argument arrays are HOST arrays of count entries

@@ -108,8 +108,8 @@ def ratio(J_c: float, J_hat: float, Jk_c: float, Jk_hat: float) -> float:
 def radius_update(varrho: float, delta: float, delta_max: float, prm: dict) -> tuple[bool, float]:
     """Algorithm 2, steps 5-6: accept when varrho >= eta1; the new radius is gamma1 Delta below
     eta1, gamma2 Delta on [eta1, eta2) and min(grow Delta, Delta_max) from eta2 on."""
-    accepted = varrho >= prm["eta1"]
-    if varrho < prm["eta1"]:
+    accepted = bool(varrho >= prm["eta1"])  # False for NaN as well
+    if not accepted:
         return accepted, prm["gamma1"] * delta
     if varrho < prm["eta2"]:
         return accepted, prm["gamma2"] * delta

@@ -31,7 +31,8 @@ EXPORTS = ["topo_create", "topo_destroy", "topo_last_error", "topo_set_param", "
            "topo_rom_solve_elem", "topo_rom_solve_elem_noalloc", "topo_rom_eval_batch", "topo_batch_create",
            "topo_batch_destroy",
            "topo_batch_last_error", "topo_batch_context", "topo_batch_solve_hdm", "topo_batch_filter",
-           "topo_batch_compliance_grad", "topo_batch_rom_solve_elem"]
+           "topo_batch_compliance_grad", "topo_batch_rom_solve_elem", "topo_tr_init", "topo_tr_project",
+           "topo_tr_trials", "topo_tr_select", "topo_tr_update"]
 
 
 class TopoError(RuntimeError):
@@ -51,6 +52,20 @@ class topo_solve_info(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("outer", ctypes.c_int), ("relres", ctypes.c_double),
                 ("status", ctypes.c_int), ("floor", ctypes.c_double), ("poly", ctypes.c_int),
                 ("mg_levels", ctypes.c_int), ("fallback", ctypes.c_int)]
+
+
+class topo_tr_state(ctypes.Structure):
+    """Host image of the device-resident trust-region state (128 bytes)."""
+    _fields_ = [(n, ctypes.c_double) for n in ("delta", "delta_max", "delta_prev", "J_c", "Jk_c", "Jk_hat", "J_hat",
+                                               "theta_hat", "step", "ratio", "gtd", "pad0")] + \
+               [(n, ctypes.c_int) for n in ("sel", "inside", "accepted", "iter")] + [("pad1", ctypes.c_int * 4)]
+
+
+class topo_tr_params(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in ("gamma1", "gamma2", "eta1", "eta2", "grow", "c1")]
+
+
+TR_STATE_BYTES = ctypes.sizeof(topo_tr_state)
 
 
 _lib = None
@@ -92,6 +107,11 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "topo_batch_filter": ([P, P, P, I], I),
         "topo_batch_compliance_grad": ([P, P, P, P, P, P, P, P, P], I),
         "topo_batch_rom_solve_elem": ([P, P, P, P, P, P, P, P], I),
+        "topo_tr_init": ([P, P, P, D, D, P], I),
+        "topo_tr_project": ([P, P, P, D, I, D, P, P], I),
+        "topo_tr_trials": ([P, I, P, P, P, I], I),
+        "topo_tr_select": ([P, P, ctypes.POINTER(topo_tr_params), I, P, P, P, P, I, P, I, I, P, P, P], I),
+        "topo_tr_update": ([P, P, ctypes.POINTER(topo_tr_params), P, P, P, P, P, P, P, P], I),
     }
     for name, (args, res) in sig.items():
         fn = getattr(L, name)
@@ -235,6 +255,49 @@ class Topo:
         m, ld = _cols(U, self.N)
         self._chk(self.lib.topo_compliance_grad(self.h, _ptr(rho), _ptr(U), m, ld, _ptr(F), _ptr(J),
                                                 _ptr(dc_rho), _ptr(dc_psi)), "topo_compliance_grad")
+
+    # -- trust-region step (Algorithm 2) ----------------------------------------------------
+    def topo_tr_init(self, st, f, tau: float, dmax_factor: float, J_c):
+        self._chk(self.lib.topo_tr_init(self.h, _ptr(st), _ptr(f), float(tau), float(dmax_factor), _ptr(J_c)),
+                  "topo_tr_init")
+
+    def topo_tr_project(self, psi, g, t: float, scaled: bool, vmax: float, out, stats):
+        self._chk(self.lib.topo_tr_project(self.h, _ptr(psi), _ptr(g), float(t), 1 if scaled else 0, float(vmax),
+                                           _ptr(out), _ptr(stats)), "topo_tr_project")
+
+    def topo_tr_trials(self, psi_c, psi_x, trials):
+        """trials: (R, ldt) tensor; row r = psi_c + s_r (psi_x - psi_c)."""
+        R, ldt = int(trials.shape[0]), int(trials.stride(0)) if trials.shape[0] > 1 else int(self.Ne)
+        self._chk(self.lib.topo_tr_trials(self.h, R, _ptr(psi_c), _ptr(psi_x), _ptr(trials), ldt), "topo_tr_trials")
+
+    def topo_tr_select(self, st, prm, Jk, resnorm, gtd, trials, Phi, k: int, yhat, psi_hat, u_hat):
+        R, ldt = int(trials.shape[0]), int(trials.stride(0)) if trials.shape[0] > 1 else int(self.Ne)
+        ld = _ld(Phi, self.N)
+        self._chk(self.lib.topo_tr_select(self.h, _ptr(st), ctypes.byref(prm), R, _ptr(Jk), _ptr(resnorm), _ptr(gtd),
+                                          _ptr(trials), ldt, _ptr(Phi), int(k), ld, _ptr(yhat), _ptr(psi_hat),
+                                          _ptr(u_hat)), "topo_tr_select")
+
+    def topo_tr_update(self, st, prm, J_hat, psi_c, psi_hat, u_c, u_hat, g_c, g_hat, u_slot=None):
+        self._chk(self.lib.topo_tr_update(self.h, _ptr(st), ctypes.byref(prm), _ptr(J_hat), _ptr(psi_c),
+                                          _ptr(psi_hat), _ptr(u_c), _ptr(u_hat), _ptr(g_c), _ptr(g_hat),
+                                          _ptr(u_slot)), "topo_tr_update")
+
+
+def tr_state_tensor():
+    """A zeroed device buffer for one topo_tr_state (FP64 view of its 128 bytes)."""
+    import torch
+    return torch.zeros(TR_STATE_BYTES // 8, dtype=torch.float64, device="cuda")
+
+
+def tr_state_read(st) -> dict:
+    """Copy a device topo_tr_state to the host and decode it (synchronises its stream)."""
+    raw = st.detach().cpu().numpy().tobytes()
+    h = topo_tr_state.from_buffer_copy(raw)
+    return {n: getattr(h, n) for n, _ in topo_tr_state._fields_ if not n.startswith("pad")}
+
+
+def tr_params(gamma1=0.5, gamma2=1.0, eta1=0.1, eta2=0.75, grow=2.0, c1=1e-4) -> topo_tr_params:
+    return topo_tr_params(gamma1, gamma2, eta1, eta2, grow, c1)
 
 
 def _cols(t, N: int):

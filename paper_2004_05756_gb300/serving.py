@@ -1,43 +1,39 @@
-"""Serving form: continuous batching of design-evaluation requests on one GPU.
+"""Serving form: continuous batching of trust-region design evaluations on one GPU.
 
-A request is one trust-region design evaluation in the shape of one major iteration of the
-paper's Algorithm 2, for one problem (2D Q4 MBB or 3D H8 cantilever):
+A request is one major iteration of the error-aware trust-region method (Algorithm 2) for one
+problem (2D Q4 MBB or 3D H8 cantilever), run by TrustRegionRun on the device:
 
-  1. filter the centre design and solve the full-order model there (the new snapshot);
-  2. build the reduced basis from the snapshot window and the element reduced matrices of the
-     basis;
-  3. evaluate the proposed candidate with the reduced model: reduced solve, residual estimate
-     theta = ||f - K(rho) Phi y|| (the error-aware trust-region constraint, Eq. trcon-topopt);
-  4. the trust-region constraint theta <= Delta = tau ||f|| (tau = 0.1: the scaling of the
-     initial radius, Eq. trrad0, since r(0, rho) = -f) decides the candidate the way the
-     subproblem's constraint does: the largest step from the centre toward the proposal,
-     s = 1, 1/2, ..., 2^-tr_halvings, whose reduced evaluation satisfies it is taken; if none
-     does, the proposal (s = 1) is evaluated with a full-order solve started from its reduced
-     state u_k;
-  5. compliance and filtered gradient at the candidate (from u_k, or from the HDM state).
+  1. model update: the reduced basis of the run's snapshot window and its element reduced
+     matrices;
+  2. step: the projected-gradient target psi_x = P_C(psi_c - move g / ||g||_inf) and the trial
+     steps psi_c + s (psi_x - psi_c), s = 0, 1, 1/2, ..., 1/64, all evaluated by the reduced
+     model in one batched call; the candidate is the longest trial inside the error-aware trust
+     region (theta <= Delta, Eq. trcon-topopt) with an Armijo decrease of the model;
+  3. the full-order solve at the candidate (started from its reduced state), its compliance
+     and gradient;
+  4. varrho_k, acceptance and the radius update (gamma1 = 0.5, gamma2 = 1, eta1 = 0.1,
+     eta2 = 0.75, Delta_max = 100 Delta_0, Section 5), and the criticality measure.
 
-Requests either stand alone (their window is the one centre snapshot) or belong to a session:
-the consecutive evaluations of one optimisation run. A session keeps its context, snapshot
-window (the last kmax centre states), basis, element reduced matrices and last centre state
-resident in device memory between its requests, so its basis grows with the run and its centre
-solves start from the previous centre's state (a warm start of the iterative solve; the
-converged result is the same fixed point). The designs of a session follow a seeded random
-walk: the centre of step t is the previous centre plus a smoothed perturbation of amplitude
-0.02, the candidate the centre plus one of amplitude 0.05.
+Requests either stand alone (a fresh run from a seeded design: the feasibility projection, the
+full-order solve at the start, Delta_0 = tau ||f||, then one major iteration) or belong to a
+session, the consecutive major iterations of one optimisation run. A session keeps its context
+and its run's state (centre design and gradient, the window of the last kmax centre states,
+the radius and compliances) resident in device memory between its requests.
 
 The server keeps `slots` request slots. Requests start in arrival order as soon as a slot is
 free and, for a standalone request or the first request of a session, its estimated device
 memory fits the free budget (admission by free HBM). Requests of one session run in order;
 requests of different sessions and standalone requests overlap on the GPU. A session's memory
 is released after its last request. When a request does not fit, the least recently used idle
-session (resident, between two of its requests) is evicted: its window, basis, element
-reduced matrices and last centre state are copied to pinned host memory and its device memory
-is freed. Its next request admits the memory again and copies the state back, so an evicted
-session's results are the same as if it had stayed resident. Every persistent solve uses a fixed share of the GPU (its
-SMs divided by the slots), which also fixes its reduction order: a request's results are
-bitwise the same alone and in a mix.
+session (resident, between two of its requests) is evicted: the tensors that carry its run are
+copied to pinned host memory and its device memory is freed. Its next request admits the
+memory again and copies the state back, so an evicted session's results are the same as if it
+had stayed resident. Every persistent solve uses a fixed share of the GPU (its SMs divided by
+the slots), which also fixes its reduction order: a request's results are bitwise the same
+alone and in a mix.
 
-All arithmetic runs in libtopo's kernels; this module only schedules and marshals.
+All arithmetic and every decision of the method run in libtopo's kernels; this module only
+schedules and marshals.
 """
 from __future__ import annotations
 
@@ -50,6 +46,7 @@ import time
 import numpy as np
 
 from . import workloads as w
+from .trust_region import TrustRegionRun
 
 
 @dataclasses.dataclass
@@ -67,16 +64,21 @@ class Request:
 @dataclasses.dataclass
 class Result:
     rid: int
-    J: float
-    theta: float
-    delta: float
-    used_hdm: bool
-    Jk: float
-    grad_norm: float
-    hdm_iters: int
-    k: int
-    step: float  # trust-region step taken toward the proposed candidate (1 on fallback)
-    rom_evals: int
+    J: float          # J at the centre after the iteration (J(psi_hat) when accepted)
+    J_hat: float      # J(psi_hat), the full-order compliance at the candidate
+    Jk: float         # m_k(psi_hat)
+    Jk_c: float       # m_k(psi_c)
+    theta: float      # theta_k(psi_hat), the trust-region constraint at the candidate
+    delta: float      # Delta_k, the radius the iteration used
+    delta_next: float # Delta_{k+1}
+    ratio: float      # varrho_k
+    accepted: bool
+    inside: bool      # the candidate passed both tests of the step search
+    step: float       # s of the candidate
+    k: int            # reduced basis size
+    chi: float        # criticality measure of the centre after the iteration
+    hdm_iters: int    # iterations of the request's full-order solves
+    rom_evals: int    # reduced evaluations of the request (the trials, centre included)
     t_arrival: float
     t_start: float
     t_done: float
@@ -96,45 +98,36 @@ def _sizes(dim: int, shape):
     return (nx + 1) * (ny + 1) * (nz + 1), nx * ny * nz
 
 
-def estimate_bytes(dim: int, shape, k: int = 1) -> int:
+def estimate_bytes(dim: int, shape, k: int = 1, trials: int = 7) -> int:
     """Device memory a request (or a session with a window of k snapshots) keeps resident
-    (FP64): the assembled stencil of the solve (3^d d^2 words per node), PCG vectors and
-    scratch, densities, the window and the basis, the element reduced matrices and a few
-    vectors of the request itself."""
+    (FP64): the assembled stencil of the solve (3^d d^2 words per node) with the multigrid
+    hierarchy's copies, PCG vectors and scratch, and the run's own buffers (window, basis,
+    element reduced matrices, trials and vectors)."""
     nodes, nel = _sizes(dim, shape)
     ndof = dim * nodes
     nc = (9 if dim == 2 else 27) * dim * dim
-    words = nc * nodes + 8 * ndof + 6 * nel + 2 * k * ndof + (k * (k + 1) // 2) * (nel + 1) + 6 * ndof
-    return 8 * words + (4 << 20)
+    ne, N, R, L = nel, ndof, trials + 1, k
+    run = 2 * L * N + (ne + 1) * L * (L + 1) // 2 + R * ne + 2 * R + R * L + L + 9 * ne + 2 * N + 32
+    words = 2 * nc * nodes + 10 * ndof + 6 * nel + run
+    return 8 * words + (8 << 20)
 
 
 class _Session:
     """Resident state of one optimisation run (device tensors on the session's own stream)."""
-
-    STATE = ("window", "Phi", "Hel", "u_prev")  # device tensors that carry the run
 
     def __init__(self, srv: "Server", req: Request, held: int):
         torch = srv.torch
         self.srv = srv
         self.p = w.build_problem(req.dim, req.shape)
         self.stream = torch.cuda.Stream()
-        self.kmax = srv.kmax
-        p = self.p
-        f64 = dict(dtype=torch.float64, device="cuda")
-        # The tensors come from the server's one allocation stream: blocks a spilled session
+        self.seed = req.seed
+        # the run's buffers come from the server's one allocation stream: blocks a spilled session
         # frees go back to that stream's pool, where the next session's allocations reuse them
-        # without emptying the allocator's cache (which would synchronise the device).
-        with torch.cuda.stream(srv.alloc_stream):
-            self.window = torch.zeros((self.kmax, p.ndof), **f64)
-            self.Phi = torch.zeros((self.kmax, p.ndof), **f64)
-            self.Hel = torch.zeros((p.nel + 1) * self.kmax * (self.kmax + 1) // 2, **f64)
-            self.u_prev = torch.zeros((1, p.ndof), **f64)
-        self.stream.wait_stream(srv.alloc_stream)
+        # without emptying the allocator's cache (which would synchronise the device)
         with torch.cuda.stream(self.stream):
             self._open_context()
-        self.nwin = 0
-        self.seed = req.seed
-        self.psi = w.design_field(p, req.seed)  # centre of step 0
+            self.run = srv.new_run(self.T, self.p, w.design_field(self.p, req.seed), srv.kmax,
+                                   alloc_stream=srv.alloc_stream)
         # admission state, guarded by the server's lock
         self.held = held          # device bytes admitted for the session
         self.counted = True       # held is part of the server's in-use total
@@ -150,59 +143,54 @@ class _Session:
         self.T.topo_set_param(native.TOPO_PARAM_PCG_MAX_CTAS, self.srv.ctas)
 
     def evict(self):
-        """Copy the state to pinned host memory, then free the context and device tensors."""
+        """Copy the run's carried tensors to pinned host memory, then free the context and every
+        device buffer of the run."""
         torch = self.srv.torch
         with torch.cuda.stream(self.stream):
             host = {}
-            for name in self.STATE:
-                t = getattr(self, name)
+            for name in self.run.CARRIED:
+                t = getattr(self.run, name)
                 host[name] = torch.empty(t.shape, dtype=t.dtype, pin_memory=True)
                 host[name].copy_(t, non_blocking=True)
         self.stream.synchronize()
         self.T.close()
         self.T = None
-        for name in self.STATE:
-            setattr(self, name, None)
+        self.run.free()
         self._host = host
         self.resident = False
 
     def restore(self):
-        """Recreate the context and copy the spilled state back (bitwise the same)."""
+        """Recreate the context and the run's buffers and copy the carried state back (bitwise
+        the same)."""
         torch = self.srv.torch
-        with torch.cuda.stream(self.srv.alloc_stream):
-            for name in self.STATE:
-                h = self._host[name]
-                setattr(self, name, torch.empty(h.shape, dtype=h.dtype, device="cuda"))
-        self.stream.wait_stream(self.srv.alloc_stream)
         with torch.cuda.stream(self.stream):
             self._open_context()
-            for name in self.STATE:
-                getattr(self, name).copy_(self._host[name], non_blocking=True)
+            self.run.T = self.T
+            self.run.alloc()
+            for name in self.run.CARRIED:
+                getattr(self.run, name).copy_(self._host[name], non_blocking=True)
         self.stream.synchronize()
         self._host = None
         self.resident = True
 
-    def designs(self, step: int):
-        """Centre and candidate of the given step (the steps of a session arrive in order)."""
-        if step > 0:
-            self.psi = w.perturbed_designs(self.p, self.psi, 1, amplitude=0.02,
-                                           first_seed=w.seed_for(f"walk{self.seed}", 2 * step))[:, 0]
-        psi_x = w.perturbed_designs(self.p, self.psi, 1, amplitude=0.05,
-                                    first_seed=w.seed_for(f"walk{self.seed}", 2 * step + 1))[:, 0]
-        return self.psi, psi_x
+    def iterate(self) -> dict:
+        with self.srv.torch.cuda.stream(self.stream):
+            return self.run.iterate()
 
     def close(self):
         self.stream.synchronize()
         if self.T is not None:
             self.T.close()
             self.T = None
+        if self.run is not None:
+            self.run.free()
 
 
 class Server:
     """Continuous-batching server over libtopo contexts."""
 
     def __init__(self, slots: int = 4, budget_bytes: int | None = None, tau: float = 0.1, rtol: float = 1e-8,
-                 maxit: int = 400000, kmax: int = 8, tr_halvings: int = 6):
+                 maxit: int = 400000, kmax: int = 8, trials: int = 7, move: float = 0.2, volfrac: float = 0.5):
         import torch
         from . import build, native
         build.build()
@@ -215,13 +203,15 @@ class Server:
         self.rtol = rtol
         self.maxit = maxit
         self.kmax = kmax
-        self.tr_halvings = tr_halvings
+        self.trials = trials
+        self.move = move
+        self.volfrac = volfrac
         props = torch.cuda.get_device_properties(torch.cuda.current_device())
         # every persistent solve of a request uses this many CTAs (the SMs split over the slots;
         # one solve CTA fills an SM)
         self.ctas = max(1, props.multi_processor_count // slots)
         self.streams = [torch.cuda.Stream() for _ in range(slots)]
-        self.alloc_stream = torch.cuda.Stream()  # allocation stream of every session's tensors
+        self.alloc_stream = torch.cuda.Stream()  # orders a session's first allocations
         self.evict_ms: list[float] = []    # wall time of each spill (copy out, context teardown)
         self.restore_ms: list[float] = []  # wall time of each restore
         self.lock = threading.Condition()
@@ -234,93 +224,36 @@ class Server:
         self.evictions = 0
         self.restores = 0
 
-    # -- one evaluation -----------------------------------------------------------------------
-    def _evaluate(self, T, p, psi_c, psi_x, window, nwin, Phi, Hel, U0, stream) -> dict:
-        """Steps 1-5 on context T. The new centre state goes to slot (nwin - 1) % kmax of the
-        window (kmax x N); U0 is the centre solve's initial guess and receives its solution."""
-        torch = self.torch
-        f64 = dict(dtype=torch.float64, device="cuda")
-        with torch.cuda.stream(stream):
-            rho = torch.empty(p.nel, **f64)
-            T.topo_filter(torch.as_tensor(psi_c).to(**f64), rho)
-            F = torch.as_tensor(p.F[:, :1].T.copy()).to(**f64)
-            f = F[0]
-            info = T.topo_solve_hdm(rho, F, U0, rtol=self.rtol, maxit=self.maxit, prec="fp64")
-            iters = info["iters"]
-            kmax = window.shape[0]
-            window[(nwin - 1) % kmax].copy_(U0[0])
-            m = min(nwin, kmax)
-            H = torch.zeros(m * m, **f64)
-            b = torch.zeros(m, **f64)
-            k = T.topo_rom_build(rho, window[:m], Phi, H, b, f)
-            T.topo_rom_elem(Phi[:k], k, Hel)
-            fnorm = float(np.linalg.norm(p.F[:, 0]))
-            delta = self.tau * fnorm
-            Hw = torch.zeros(k * k, **f64)
+    def new_run(self, T, p, psi0, L: int, alloc_stream=None) -> TrustRegionRun:
+        return TrustRegionRun(T, p, psi0, tau=self.tau, move=self.move, trials=self.trials, volfrac=self.volfrac,
+                              L=L, rtol=self.rtol, maxit=self.maxit, alloc_stream=alloc_stream)
 
-            def rom_at(psi):
-                rho_s = torch.empty(p.nel, **f64)
-                T.topo_filter(torch.as_tensor(psi).to(**f64), rho_s)
-                y = torch.zeros(k, **f64)
-                Jk = torch.zeros(1, **f64)
-                T.topo_rom_solve_elem(rho_s, Hel, k, b[:k], Hw, y, Jk)
-                rn = torch.zeros(2, **f64)
-                uk = torch.zeros(p.ndof, **f64)
-                T.topo_rom_error(rho_s, Phi[:k], k, y, f, rn, uk)
-                return rho_s, uk, Jk.item(), rn[0].item()
-
-            # the largest step toward the proposal that the trust-region constraint admits
-            first = None
-            s, nrom, acc = 1.0, 0, None
-            for h in range(self.tr_halvings + 1):
-                ev = rom_at(psi_x if h == 0 else psi_c + s * (psi_x - psi_c))
-                nrom += 1
-                if first is None:
-                    first = ev
-                if ev[3] <= delta:
-                    acc = ev
-                    break
-                s *= 0.5
-            used_hdm = acc is None
-            if used_hdm:  # full-order solve at the proposal, from its reduced state
-                rho_x, uk, Jk, theta = first
-                s = 1.0
-                Ux = uk.reshape(1, -1).clone()
-                info2 = T.topo_solve_hdm(rho_x, F, Ux, rtol=self.rtol, maxit=self.maxit, prec="fp64")
-                iters += info2["iters"]
-            else:
-                rho_x, uk, Jk, theta = acc
-                Ux = uk.reshape(1, -1)
-            J = torch.zeros(1, **f64)
-            dc = torch.empty(p.nel, **f64)
-            dpsi = torch.empty(p.nel, **f64)
-            T.topo_compliance_grad(rho_x, Ux, F, J, dc, dpsi)
-            T.topo_check()
-            return dict(J=J.item(), theta=theta, delta=delta, used_hdm=bool(used_hdm), Jk=Jk,
-                        grad_norm=float(torch.linalg.vector_norm(dpsi).item()), hdm_iters=iters, k=k, step=s,
-                        rom_evals=nrom)
+    @staticmethod
+    def _result(out: dict, hdm_iters: int, rom_evals: int) -> dict:
+        return dict(J=out["J_c"], J_hat=out["J_hat"], Jk=out["Jk_hat"], Jk_c=out["Jk_c"], theta=out["theta_hat"],
+                    delta=out["delta_prev"], delta_next=out["delta"], ratio=out["ratio"],
+                    accepted=bool(out["accepted"]), inside=bool(out["inside"]), step=out["step"], k=out["k"],
+                    chi=out["chi"], hdm_iters=hdm_iters, rom_evals=rom_evals)
 
     def _standalone(self, req: Request, stream) -> dict:
         torch, native = self.torch, self.native
         p = w.build_problem(req.dim, req.shape)
-        f64 = dict(dtype=torch.float64, device="cuda")
         with torch.cuda.stream(stream):
             T = native.Topo(p, stream=stream)
-            T.topo_set_param(native.TOPO_PARAM_PCG_MAX_CTAS, self.ctas)
-            psi_c = w.design_field(p, req.seed)
-            psi_x = w.perturbed_designs(p, psi_c, 1, amplitude=0.05, first_seed=req.seed % 100000 + 1)[:, 0]
-            window = torch.zeros((1, p.ndof), **f64)
-            Phi = torch.zeros((1, p.ndof), **f64)
-            Hel = torch.zeros(p.nel + 1, **f64)
-            U0 = torch.zeros((1, p.ndof), **f64)
-            out = self._evaluate(T, p, psi_c, psi_x, window, 1, Phi, Hel, U0, stream)
-            T.close()
-        return out
+            try:
+                T.topo_set_param(native.TOPO_PARAM_PCG_MAX_CTAS, self.ctas)
+                run = self.new_run(T, p, w.design_field(p, req.seed), 1)
+                out = run.iterate()
+                res = self._result(out, run.hdm_iters, run.R)
+                run.free()
+            finally:
+                T.close()
+        return res
 
     def _in_session(self, S: _Session, req: Request) -> dict:
-        psi_c, psi_x = S.designs(req.step)
-        S.nwin += 1
-        return self._evaluate(S.T, S.p, psi_c, psi_x, S.window, S.nwin, S.Phi, S.Hel, S.u_prev, S.stream)
+        before = S.run.hdm_iters if req.step > 0 else 0
+        out = S.iterate()
+        return self._result(out, S.run.hdm_iters - before, S.run.R)
 
     # -- the stream -----------------------------------------------------------------------------
     def _evict_one(self, keep) -> bool:
@@ -514,8 +447,10 @@ def session_requests(count: int, rate_per_s: float, sessions: int = 8, seed: int
 def summarize(results: list[Result], wall: float) -> dict:
     lat = sorted(r.latency for r in results)
     pick = lambda q: lat[min(len(lat) - 1, int(math.ceil(q * len(lat))) - 1)] if lat else None
+    ratios = [r.ratio for r in results if math.isfinite(r.ratio)]
     return dict(requests=len(results), evals_per_s=len(results) / wall if wall > 0 else None,
                 p50_ms=1e3 * pick(0.50), p99_ms=1e3 * pick(0.99),
-                hdm_fallbacks=sum(r.used_hdm for r in results),
+                accepted=sum(r.accepted for r in results), inside=sum(r.inside for r in results),
+                median_ratio=float(np.median(ratios)) if ratios else None,
                 rom_evals=sum(r.rom_evals for r in results),
                 mean_basis_size=(sum(r.k for r in results) / len(results)) if results else None)

@@ -41,12 +41,18 @@ def test_struct_layout_matches_header(tmp_path):
     c = tmp_path / "sz.c"
     c.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "topo.h"\nint main(void){printf("%zu %zu %zu %zu\\n",'
                  'sizeof(topo_problem), offsetof(topo_problem, fixed_dof_mask), sizeof(topo_solve_info),'
-                 'offsetof(topo_solve_info, status)); return 0;}\n')
+                 'offsetof(topo_solve_info, status)); printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(topo_tr_state),'
+                 'offsetof(topo_tr_state, ratio), offsetof(topo_tr_state, sel), offsetof(topo_tr_state, iter),'
+                 'sizeof(topo_tr_params), offsetof(topo_tr_params, c1)); return 0;}\n')
     exe = tmp_path / "sz"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(c), "-o", str(exe)], check=True)
     vals = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True).stdout.split()]
     assert vals == [ctypes.sizeof(native.topo_problem), native.topo_problem.fixed_dof_mask.offset,
-                    ctypes.sizeof(native.topo_solve_info), native.topo_solve_info.status.offset]
+                    ctypes.sizeof(native.topo_solve_info), native.topo_solve_info.status.offset,
+                    ctypes.sizeof(native.topo_tr_state), native.topo_tr_state.ratio.offset,
+                    native.topo_tr_state.sel.offset, native.topo_tr_state.iter.offset,
+                    ctypes.sizeof(native.topo_tr_params), native.topo_tr_params.c1.offset]
+    assert native.TR_STATE_BYTES == 128
 
 
 @pytest.mark.parametrize("bad", [

@@ -1,11 +1,12 @@
-"""Serving form: continuous batching of design-evaluation requests. Each request's results
-are bitwise the same alone and in the mix; one request is checked against the oracle; a tight
-memory budget admits one request at a time; under a budget too small for all sessions at once,
-idle sessions are spilled to host memory and restored with the same results."""
+"""Serving form: continuous batching of trust-region major iterations (Algorithm 2). Each
+request's results are bitwise the same alone and in the mix; a standalone request and the
+requests of a session are replayed against the oracle's major iterations; a tight memory budget
+admits one request at a time; under a budget too small for all sessions at once, idle sessions
+are spilled to host memory and restored with the same results."""
 import numpy as np
 import pytest
 
-from oracle import fem, hatfilter, rom
+from oracle import trust
 from paper_2004_05756_gb300 import workloads as w
 from tests.gpu_util import require_cuda
 
@@ -20,6 +21,14 @@ def _requests():
     return [Request(rid=i, dim=d, shape=s, seed=sd, arrival=0.01 * i) for i, (d, s, sd) in enumerate(REQS)]
 
 
+FIELDS = ("J", "J_hat", "Jk", "Jk_c", "theta", "delta", "delta_next", "ratio", "accepted", "inside", "step", "k",
+          "chi")
+
+
+def _key(r):
+    return tuple(getattr(r, f) for f in FIELDS)
+
+
 def test_alone_equals_mix_bitwise():
     require_cuda()
     from paper_2004_05756_gb300.serving import Server
@@ -28,44 +37,37 @@ def test_alone_equals_mix_bitwise():
     assert srv.max_concurrency >= 2  # requests did overlap
     for req in _requests():
         alone = Server(slots=3).run([req], realtime=False)[0]
-        m = mix[req.rid]
-        assert (alone.J, alone.theta, alone.Jk, alone.used_hdm) == (m.J, m.theta, m.Jk, m.used_hdm), req
+        assert _key(alone) == _key(mix[req.rid]), req
 
 
-def _oracle_step(p, psi_c, psi_x, Phi, halvings=6):
-    """The candidate of a request by the oracle: the largest step s = 1, 1/2, ... toward the
-    proposal whose reduced residual satisfies theta <= 0.1 ||f||, else the proposal itself by
-    a direct solve. Returns (s, theta, J_k, J, fallback)."""
-    f = p.F[:, 0]
-    delta = 0.1 * np.linalg.norm(f)
-    s, first = 1.0, None
-    for h in range(halvings + 1):
-        psi = psi_x if h == 0 else psi_c + s * (psi_x - psi_c)
-        ev = rom.rom_eval(p, hatfilter.filter_fwd(p, psi), Phi, f)
-        if first is None:
-            first = ev
-        if ev["resnorm"] <= delta:
-            return s, ev["resnorm"], ev["Jk"], ev["Jk"], False
-        s *= 0.5
-    rho_x = hatfilter.filter_fwd(p, psi_x)
-    return 1.0, first["resnorm"], first["Jk"], fem.compliance(p, fem.solve(p, rho_x)), True
+def _compare(res, o, it=0):
+    """A served major iteration against the oracle's: decisions equal, values within what their
+    FP64 arithmetic allows (compliances to about 1e-10, the residual norm's cancellation)."""
+    assert (res.step, res.inside, res.accepted, res.k) == (o["step"], o["inside"], o["accepted"], o["k"]), it
+    assert res.J_hat == pytest.approx(o["J_hat"], rel=1e-10), it
+    assert res.Jk == pytest.approx(o["Jk_hat"], rel=1e-9), it
+    assert res.Jk_c == pytest.approx(o["Jk_c"], rel=1e-9), it
+    assert res.theta == pytest.approx(o["theta_hat"], rel=1e-7), it
+    assert res.delta == pytest.approx(o["delta"], rel=1e-14), it
+    assert res.delta_next == pytest.approx(o["delta_next"], rel=1e-14), it
+    pred = o["Jk_c"] - o["Jk_hat"]
+    tol = 1e-9 * (abs(o["J_c"]) + abs(o["J_hat"]) + abs(o["ratio"]) * (abs(o["Jk_c"]) + abs(o["Jk_hat"])))
+    assert abs(res.ratio - o["ratio"]) <= tol / pred, (it, res.ratio, o["ratio"])
+    assert res.chi == pytest.approx(o["chi"], rel=1e-8), it
 
 
 def test_request_matches_oracle():
+    """A standalone request is one major iteration of a fresh run: the oracle's start and major
+    iteration on the same seeded design give the same decisions and values."""
     require_cuda()
     from paper_2004_05756_gb300.serving import Request, Server
     d, shape, seed = REQS[0]
-    res = Server(slots=1).run([Request(rid=0, dim=d, shape=shape, seed=seed)], realtime=False)[0]
+    res = Server(slots=1, rtol=1e-13).run([Request(rid=0, dim=d, shape=shape, seed=seed)], realtime=False)[0]
     p = w.build_problem(d, shape)
-    psi_c = w.design_field(p, seed)
-    psi_x = w.perturbed_designs(p, psi_c, 1, amplitude=0.05, first_seed=seed % 100000 + 1)[:, 0]
-    u_c = fem.solve(p, hatfilter.filter_fwd(p, psi_c))[:, 0]
-    Phi = rom.basis(u_c[:, None])
-    s, theta, Jk, J, fallback = _oracle_step(p, psi_c, psi_x, Phi)
-    assert res.step == s and res.used_hdm == fallback
-    assert res.theta == pytest.approx(theta, rel=1e-6)
-    assert res.Jk == pytest.approx(Jk, rel=1e-8)
-    assert res.J == pytest.approx(J, rel=1e-8)
+    prm = trust.default_params(L=1)
+    run = trust.start(p, w.design_field(p, seed), prm)
+    _compare(res, trust.major_iteration(p, run, prm))
+    assert res.rom_evals == prm["trials"] + 1
 
 
 def test_admission_by_memory_budget():
@@ -92,9 +94,9 @@ def _session_requests(steps=4):
 
 
 def test_sessions_alone_equal_mix_and_basis_grows():
-    """Sessions keep their basis between requests: results are bitwise the same when a
-    session runs alone and when its requests interleave with the others', the basis grows
-    with the session, and the reduced model takes over from the full-order fallback."""
+    """Sessions keep their run between requests: results are bitwise the same when a session
+    runs alone and when its requests interleave with the others', the basis grows with every
+    accepted step up to the window, and accepted steps decrease the compliance."""
     require_cuda()
     from paper_2004_05756_gb300.serving import Server
     reqs = _session_requests()
@@ -104,38 +106,33 @@ def test_sessions_alone_equal_mix_and_basis_grows():
     assert srv.max_concurrency >= 2
     for s in range(len(SESS)):
         mine = [r for r in _session_requests() if r.session == s]
-        alone = Server(slots=3, kmax=4).run(mine, realtime=False)
+        alone = sorted(Server(slots=3, kmax=4).run(mine, realtime=False), key=lambda r: r.index)
         for a in alone:
-            m = mix[a.rid]
-            assert (a.J, a.theta, a.Jk, a.used_hdm, a.k, a.step) == (m.J, m.theta, m.Jk, m.used_hdm, m.k, m.step), \
-                (s, a.index)
-        assert [a.k for a in sorted(alone, key=lambda r: r.index)] == [1, 2, 3, 4]
-    # the trust-region step search finds admissible candidates: the reduced model answers
-    assert sum(not r.used_hdm for r in mix.values()) >= len(mix) // 2, \
-        [(r.session, r.index, r.step, r.theta / r.delta) for r in mix.values()]
+            assert _key(a) == _key(mix[a.rid]), (s, a.index)
+        acc = 0
+        J = None
+        for a in alone:
+            assert a.k == min(1 + acc, 4), (s, a.index, a.k, acc)
+            if a.accepted:
+                acc += 1
+                assert a.J == a.J_hat and (J is None or a.J < J)
+            J = a.J
+        assert acc >= 2, [(a.ratio, a.accepted) for a in alone]
 
 
-def test_session_request_matches_oracle():
-    """Step 1 of a session: a two-snapshot window (centres of steps 0 and 1), the reduced
-    evaluation at the candidate, against the oracle's direct solves and reduced model."""
+def test_session_requests_match_oracle():
+    """Three requests of one session against three major iterations of the oracle's run."""
     require_cuda()
     from paper_2004_05756_gb300.serving import Request, Server
     d, shape = SESS[0]
-    reqs = [Request(rid=t, dim=d, shape=shape, seed=100, arrival=0.0, session=0, step=t, last=t == 1)
-            for t in range(2)]
-    res = sorted(Server(slots=1, kmax=4).run(reqs, realtime=False), key=lambda r: r.index)[1]
+    reqs = [Request(rid=t, dim=d, shape=shape, seed=100, arrival=0.0, session=0, step=t, last=t == 2)
+            for t in range(3)]
+    res = sorted(Server(slots=1, kmax=4, rtol=1e-13).run(reqs, realtime=False), key=lambda r: r.index)
     p = w.build_problem(d, shape)
-    psi0 = w.design_field(p, 100)
-    psi1 = w.perturbed_designs(p, psi0, 1, amplitude=0.02, first_seed=w.seed_for("walk100", 2))[:, 0]
-    psix = w.perturbed_designs(p, psi1, 1, amplitude=0.05, first_seed=w.seed_for("walk100", 3))[:, 0]
-    U = np.stack([fem.solve(p, hatfilter.filter_fwd(p, q))[:, 0] for q in (psi0, psi1)], 1)
-    Phi = rom.basis(U)
-    s, theta, Jk, J, fallback = _oracle_step(p, psi1, psix, Phi)
-    assert res.k == Phi.shape[1] == 2
-    assert res.step == s and res.used_hdm == fallback
-    assert res.theta == pytest.approx(theta, rel=1e-6)
-    assert res.Jk == pytest.approx(Jk, rel=1e-7)
-    assert res.J == pytest.approx(J, rel=1e-7)
+    prm = trust.default_params(L=4)
+    run = trust.start(p, w.design_field(p, 100), prm)
+    for t in range(3):
+        _compare(res[t], trust.major_iteration(p, run, prm), t)
 
 
 def test_idle_sessions_evicted_under_memory_pressure_same_results():
@@ -157,4 +154,4 @@ def test_idle_sessions_evicted_under_memory_pressure_same_results():
     assert set(got) == set(ref)
     for rid, a in ref.items():
         b = got[rid]
-        assert (a.J, a.theta, a.Jk, a.used_hdm, a.k, a.step) == (b.J, b.theta, b.Jk, b.used_hdm, b.k, b.step), rid
+        assert _key(a) == _key(b), rid
