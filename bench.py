@@ -735,7 +735,61 @@ def run_batch(args):
             times.append(timed(run))
         launches = per_step * args.steps if graph is not None else native.launch_count() - n0
         infos = B.topo_batch_solve_hdm(rhos, Fs, [torch.zeros_like(F) for F in Fs], rtol=1e-8, maxit=100000)
+        J_batch = J.cpu().numpy().copy()
+        # the same instances' state solves as sequential topo_solve_hdm calls (one context each,
+        # the single-solve path's defaults), timed the same way
+        ctxs = [native.Topo(p, stream=stream) for p in probs]
+        Us2 = [torch.zeros_like(F) for F in Fs]
+
+        def sequential():
+            for T, rho, F, U in zip(ctxs, rhos, Fs, Us2):
+                U.zero_()
+                T.topo_solve_hdm(rho, F, U, rtol=1e-8, maxit=100000, prec="fp64", info=False)
+
+        flush.zero_()
+        timed(sequential)  # warm-up: first-call scratch
+        seq_times = []
+        for _ in range(max(1, min(args.steps, 3))):
+            flush.zero_()
+            seq_times.append(timed(sequential))
+        seq_infos = [T.topo_solve_hdm(rho, F, torch.zeros_like(F), rtol=1e-8, maxit=100000, prec="fp64")
+                     for T, rho, F in zip(ctxs, rhos, Fs)]
+        for T in ctxs:
+            T.close()
+        solve_only = []
+        for _ in range(max(1, min(args.steps, 3))):
+            for U in Us:
+                U.zero_()
+            flush.zero_()
+            solve_only.append(timed(lambda: B.topo_batch_solve_hdm(rhos, Fs, Us, rtol=1e-8, maxit=100000,
+                                                                   info=False)))
+        rho_host = [r.cpu().numpy() for r in rhos]
     ms = statistics.fmean(times)
+    at_floor = [i for i, x in enumerate(infos) if x["relres"] > 1e-8]
+    cpu = None
+    if not args.no_cpu_baseline:
+        # cpu_baseline leg: the oracle's HDM evaluation (filter, SuperLU solve, compliance) of the
+        # instances whose batched solve stopped at its FP64 rounding floor above rtol, timed as
+        # run; their compliance errors against the oracle come with it
+        from oracle import fem, hatfilter
+        t0 = time.perf_counter()
+        errs = []
+        for i in at_floor:
+            pi = probs[i]
+            rho_o = hatfilter.filter_fwd(pi, w.design_field(pi, insts[i]["design_seed"]))
+            Jo = fem.compliance(pi, fem.solve(pi, rho_o))
+            errs.append({"instance": i, "shape": [pi.nx, pi.ny], "load_cases": int(pi.F.shape[1]),
+                         "relres": infos[i]["relres"], "floor": infos[i]["floor"],
+                         "J_rel_err": float(abs(J_batch[i] - Jo) / abs(Jo)),
+                         "rho_max_abs_err": float(np.max(np.abs(rho_host[i] - rho_o)))})
+        t_cpu = time.perf_counter() - t0
+        hi = host_info()
+        cpu = {"value": len(at_floor) / t_cpu if at_floor else None, "unit": UNIT,
+               "cores": max(1, hi["blas_threads"] or 1), "kind": "oracle",
+               "sample": f"oracle HDM evaluations (filter, SuperLU solve, compliance) of the {len(at_floor)} "
+                         f"instances whose batched solve stopped at the FP64 floor", "host": hi,
+               "floor_limited": errs,
+               "max_J_rel_err": max((e["J_rel_err"] for e in errs), default=None)}
     ndof = sum(p.ndof for p in probs)
     # FP64 work of the solves: 51 flops per DOF, load case and iteration (stencil apply 36,
     # delta 2, updates and dots 13)
@@ -751,17 +805,40 @@ def run_batch(args):
                        "load_cases": nlc},
             "max_iters": max(x["iters"] for x in infos), "all_converged": all(x["status"] == 0 for x in infos),
             "max_relres": max(x["relres"] for x in infos), "max_floor": max(x["floor"] for x in infos),
-            "instances_at_floor": sum(1 for x in infos if x["relres"] > 1e-8), "gpu_launches": launches,
+            "instances_at_floor": len(at_floor), "gpu_launches": launches,
+            "batch_solve_ms": statistics.fmean(solve_only),
+            "sequential": {"what": f"the same {len(probs)} state solves as sequential topo_solve_hdm calls (one "
+                                   f"context per instance, multigrid-preconditioned, rtol 1e-8), CUDA events",
+                           "ms": statistics.fmean(seq_times), "runs": len(seq_times),
+                           "speedup_of_batch_solve": statistics.fmean(seq_times) / statistics.fmean(solve_only),
+                           "max_iters": max(x["iters"] for x in seq_infos),
+                           "all_converged": all(x["status"] == 0 for x in seq_infos)},
+            "cpu_baseline": cpu,
             "cuda_graph": graph is not None, "cuda_graph_error": graph_error,
             "roofline": {"kernel": "pcg2_batch_kernel (all instances' solves, one launch)", "bound": "alu",
                          "achieved": flops / (ms * 1e-3) / 1e12, "peak": fp64_peak / 1e12, "unit": "TFLOP/s",
                          "frac": flops / (ms * 1e-3) / fp64_peak, "traffic": None}}
 
 
+def _serving_line(srv, reqs, res, wall, clocks=None):
+    from paper_2004_05756_gb300 import serving
+    s = serving.summarize(res, wall)
+    return {"requests": len(reqs), "evals_per_s": s["evals_per_s"], "p50_ms": s["p50_ms"], "p99_ms": s["p99_ms"],
+            "accepted": s["accepted"], "inside": s["inside"], "median_ratio": s["median_ratio"],
+            "rom_evals": s["rom_evals"], "mean_basis_size": s["mean_basis_size"],
+            "max_concurrency": srv.max_concurrency, "session_evictions": srv.evictions,
+            "session_restores": srv.restores, "evict_ms_total": sum(srv.evict_ms),
+            "restore_ms_total": sum(srv.restore_ms), "wall_s": wall, "clocks": clocks}
+
+
 def run_serving(args):
     """Serving form: a seeded Poisson stream of trust-region major iterations, 50/50 2D Q4
     (100x50 .. 800x400) and 3D H8 (32^3 .. 96x48x48), admitted by free HBM into slots that
-    overlap on the GPU. Reports evals/s and p50/p99 latency (arrival to completion)."""
+    overlap on the GPU. Reports evals/s and p50/p99 latency (arrival to completion).
+
+    With --sweep: the capacity first (a saturated stream: --cap-requests requests all queued at
+    t = 0, throughput = capacity), then --sweep-requests Poisson requests (seed 7) at 0.5, 1 and
+    2 times that capacity, each with the SM clocks sampled while it runs."""
     import torch
     from paper_2004_05756_gb300 import serving
 
@@ -770,6 +847,35 @@ def run_serving(args):
     warm = serving.poisson_requests(2, rate_per_s=100.0, seed=99, q4=((100, 50), (120, 60)),
                                     h8=((16, 16, 16), (20, 20, 20)))
     srv.run(warm, realtime=False)
+    base = {"metric": METRIC, "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 1, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic"}
+    if args.sweep:
+        cap_reqs = serving.poisson_requests(args.cap_requests, rate_per_s=1.0, seed=7)
+        sampler = ClockSampler(torch.cuda.current_device())
+        sampler.start()
+        t0 = time.perf_counter()
+        res = srv.run(cap_reqs, realtime=False)
+        wall = time.perf_counter() - t0
+        cap_line = _serving_line(srv, cap_reqs, res, wall, sampler.stop())
+        cap = cap_line["evals_per_s"]
+        runs = []
+        for f in (0.5, 1.0, 2.0):
+            srv = serving.Server(slots=args.slots)
+            reqs = serving.poisson_requests(args.sweep_requests, rate_per_s=f * cap, seed=7)
+            sampler = ClockSampler(torch.cuda.current_device())
+            sampler.start()
+            t0 = time.perf_counter()
+            res = srv.run(reqs, realtime=True)
+            wall = time.perf_counter() - t0
+            line = _serving_line(srv, reqs, res, wall, sampler.stop())
+            line.update(load=f, rate_per_s=f * cap)
+            runs.append(line)
+        return dict(base, value=cap, config={
+            "workload": f"serving sweep: capacity from {args.cap_requests} requests queued at t=0, then "
+                        f"{args.sweep_requests} Poisson requests (seed 7) at 0.5/1/2 x capacity; 50/50 Q4 "
+                        f"100x50..800x400 and H8 32^3..96x48x48 standalone requests (a fresh run's first major "
+                        f"iteration), {args.slots} slots", "slots": args.slots},
+            capacity=cap_line, sweep=runs)
     if args.sessions > 0:
         reqs = serving.session_requests(args.requests, rate_per_s=args.rate, sessions=args.sessions, seed=7)
     else:
@@ -777,20 +883,13 @@ def run_serving(args):
     t0 = time.perf_counter()
     res = srv.run(reqs, realtime=True)
     wall = time.perf_counter() - t0
-    s = serving.summarize(res, wall)
-    return {"metric": METRIC, "value": s["evals_per_s"], "unit": UNIT, "n_gpus": 1, "steps": 1, "warmup": 1,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"serving: {len(reqs)} Poisson requests at {args.rate}/s, 50/50 Q4 100x50..800x400 "
-                                   f"and H8 32^3..96x48x48, {args.slots} slots, " +
-                                   (f"{args.sessions} sessions (resident run, window {srv.kmax})" if args.sessions
-                                    else "standalone requests (a fresh run's first major iteration)"),
-                       "slots": args.slots,
-                       "rate_per_s": args.rate, "sessions": args.sessions},
-            "p50_ms": s["p50_ms"], "p99_ms": s["p99_ms"], "accepted": s["accepted"], "inside": s["inside"],
-            "median_ratio": s["median_ratio"], "rom_evals": s["rom_evals"], "mean_basis_size": s["mean_basis_size"],
-            "max_concurrency": srv.max_concurrency, "session_evictions": srv.evictions,
-            "session_restores": srv.restores, "evict_ms_total": sum(srv.evict_ms),
-            "restore_ms_total": sum(srv.restore_ms), "wall_s": wall}
+    line = _serving_line(srv, reqs, res, wall)
+    return dict(base, value=line["evals_per_s"], config={
+        "workload": f"serving: {len(reqs)} Poisson requests at {args.rate}/s, 50/50 Q4 100x50..800x400 "
+                    f"and H8 32^3..96x48x48, {args.slots} slots, " +
+                    (f"{args.sessions} sessions (resident run, window {srv.kmax})" if args.sessions
+                     else "standalone requests (a fresh run's first major iteration)"),
+        "slots": args.slots, "rate_per_s": args.rate, "sessions": args.sessions}, **line)
 
 
 def main():
@@ -817,6 +916,10 @@ def main():
     ap.add_argument("--slots", type=int, default=4, help="serving: concurrent request slots")
     ap.add_argument("--requests", type=int, default=32, help="serving: requests in the stream")
     ap.add_argument("--rate", type=float, default=2.0, help="serving: Poisson arrival rate (requests/s)")
+    ap.add_argument("--sweep", action="store_true",
+                    help="serving: measure capacity, then Poisson streams at 0.5, 1 and 2 x capacity")
+    ap.add_argument("--cap-requests", type=int, default=400, help="serving sweep: requests of the capacity run")
+    ap.add_argument("--sweep-requests", type=int, default=2000, help="serving sweep: requests per load level")
     ap.add_argument("--sessions", type=int, default=8,
                     help="serving: optimisation sessions the requests belong to (0 = standalone requests)")
     args = ap.parse_args()

@@ -408,17 +408,29 @@ class Server:
 
         threads = []
         sessions: dict[int, list[Request]] = {}
+        standalone = [r for r in reqs if r.session is None]
         for req in reqs:
-            if req.session is None:
-                threads.append(threading.Thread(target=standalone_worker, args=(req,), daemon=True))
-            else:
+            if req.session is not None:
                 sessions.setdefault(req.session, []).append(req)
         for sid, sreqs in sessions.items():
             sreqs.sort(key=lambda r: r.step)
             threads.append(threading.Thread(target=session_worker, args=(sid, sreqs), daemon=True))
-        for th in threads:
+
+        def dispatch():
+            # a standalone request's thread starts at its arrival, so a long stream holds threads
+            # only for the requests that have arrived and not finished
+            for req in standalone:
+                wait_arrival(req)
+                th = threading.Thread(target=standalone_worker, args=(req,), daemon=True)
+                th.start()
+                threads.append(th)
+
+        for th in list(threads):
             th.start()
-        for th in threads:
+        dispatcher = threading.Thread(target=dispatch, daemon=True)
+        dispatcher.start()
+        dispatcher.join()
+        for th in list(threads):
             th.join()
         if errors:
             rid, e = errors[0]
