@@ -28,6 +28,7 @@ namespace topo {
 
 constexpr int MG_MAX_LEVELS = 12;
 constexpr int MG_MAX_DEG = 4;          // Chebyshev smoothing steps per side
+constexpr int MG_STALL_ITERS = 64;    // iterations within which the V-cycle must halve ||r||
 constexpr int MG_COARSE_MAX = 160;     // DOFs of the coarsest level (dense inverse)
 constexpr double MG_RATIO = 30.0;      // Chebyshev interval [lambda_max / 30, lambda_max]
 constexpr size_t MG_TAIL_BYTES = 96 * 1024;  // shared memory for the vectors of the levels on CTA 0

@@ -246,6 +246,7 @@ __device__ __forceinline__ void pcg2_body(const Pcg2Args<DIM>& a, const unsigned
   __shared__ int mg_halo[MG_MAX_LEVELS][2], mg_rest[MG_MAX_LEVELS][2], mg_prol[MG_MAX_LEVELS][2];
   __shared__ int mg_okc;
   __shared__ int sh_fallback;  // multigrid: the FP32 V-cycle lost positive definiteness
+  __shared__ double sh_rrchk[P2_MAX_COLS];  // multigrid: r.r at the last stagnation checkpoint
   __shared__ int s_okw;
   const Grid& g = a.g;
   const int m = a.m;
@@ -535,7 +536,10 @@ __device__ __forceinline__ void pcg2_body(const Pcg2Args<DIM>& a, const unsigned
   // the preconditioner in use: 2 multigrid, 1 polynomial, 0 Jacobi. The multigrid solve drops
   // to the polynomial if its FP32 V-cycle stops being positive definite (r.z <= 0 or p.K p <= 0:
   // designs whose conditioning is beyond the V-cycle's FP32 arithmetic, e.g. loads on void)
-  int mode = PK == 2 ? 2 : (poly > 1 ? 1 : 0);
+  // (an instance of a batched multigrid launch whose mesh is too small to coarsen, mg.L < 2, runs
+  // the polynomial from the start)
+  const bool mg_on = PK == 2 && a.mg.L >= 2;
+  int mode = mg_on ? 2 : (poly > 1 ? 1 : 0);
   const bool f32pre = mode != 0;  // an FP32 preconditioner on an FP32 copy of the stencil
   if (threadIdx.x == 0) sh_fallback = 0;
   double gmax = 0.0;
@@ -561,15 +565,15 @@ __device__ __forceinline__ void pcg2_body(const Pcg2Args<DIM>& a, const unsigned
     if (threadIdx.x == 0) {
       double bm = 0.0;
       for (int q = 0; q < nwarps; ++q) bm = fmax(bm, red[q]);
-      if (PK == 2)
-        a.mg.lmax[rank] = bm;  // level 0
+      if (mg_on)
+        a.mg.lmax[rank] = bm;  // level 0 (an instance without levels has no mg.lmax)
       else
         *P(0, 0) = bm;
     }
   }
   if (!sync_reduce(0)) return;
   if constexpr (PK == 2) {
-    if (!mg_setup()) return;
+    if (mg_on && !mg_setup()) return;
   }
   if (poly > 1) {
     // (the multigrid solve keeps these for its fallback; its level-0 bound is in mg.lmax)
@@ -578,7 +582,7 @@ __device__ __forceinline__ void pcg2_body(const Pcg2Args<DIM>& a, const unsigned
     // rho_0 = 1 / sigma, rho_j = 1 / (2 sigma - rho_{j-1}), c1_j = rho_j rho_{j-1},
     // c2_j = 2 rho_j / delta (theta, delta: centre and half-width of the interval).
     if (threadIdx.x == 0) {
-      const double* bpart = PK == 2 ? a.mg.lmax : part + (size_t)((bar & 1) * P2_SLOTS * m) * G;
+      const double* bpart = mg_on ? a.mg.lmax : part + (size_t)((bar & 1) * P2_SLOTS * m) * G;
       double lmax = 0.0;
       for (unsigned q = 0; q < G; ++q) lmax = fmax(lmax, bpart[q]);
       if (!(lmax > 0.0) || !isfinite(lmax)) lmax = 1.0;
@@ -1303,11 +1307,35 @@ __device__ __forceinline__ void pcg2_body(const Pcg2Args<DIM>& a, const unsigned
     for (int c = 0; c < m; ++c) all = all && sh_done[c];
     if (all || iters >= a.maxit) break;
     bool restart = true;
+    // multigrid stagnation: a V-cycle in FP32 cannot resolve every stiffness contrast (a stiff
+    // island held only by void elements); when r.r of a column still in progress has not fallen
+    // to a quarter within MG_STALL_ITERS iterations, the solve continues with the polynomial.
+    // Every CTA tests the same reduced values, so all switch at the same iteration.
+    int chk_it = iters;
+    if (PK == 2 && mode == 2) {
+      __syncthreads();
+      if (threadIdx.x == 0)
+        for (int c = 0; c < m; ++c) sh_rrchk[c] = sh_rr[c];
+      __syncthreads();
+    }
     while (true) {
       if (!phase_w(restart)) return;
       if (PK == 2 && mode == 2 && sh_fallback) {
         mode = 1;  // every CTA reduced the same values: all switch here
         break;
+      }
+      if (PK == 2 && mode == 2 && iters - chk_it >= MG_STALL_ITERS) {
+        bool stalled = false;
+        for (int c = 0; c < m; ++c) stalled = stalled || (!sh_done[c] && sh_rr[c] > 0.25 * sh_rrchk[c]);
+        __syncthreads();
+        if (threadIdx.x == 0)
+          for (int c = 0; c < m; ++c) sh_rrchk[c] = sh_rr[c];
+        __syncthreads();
+        chk_it = iters;
+        if (stalled) {
+          mode = 1;
+          break;
+        }
       }
       bool any = false;
       for (int c = 0; c < m; ++c) any = any || !sh_done[c];
@@ -1332,7 +1360,7 @@ __device__ __forceinline__ void pcg2_body(const Pcg2Args<DIM>& a, const unsigned
     a.info[0] = iters;
     a.info[1] = 0;
     a.info[2] = conv ? 0 : TOPO_ERR_NOT_CONVERGED;
-    a.info[3] = (PK == 2 && mode != 2) ? 1 : 0;  // multigrid fell back to the polynomial
+    a.info[3] = (mg_on && mode != 2) ? 1 : 0;  // multigrid fell back to the polynomial
     a.info_rr[0] = worst;
   }
 }
@@ -1584,7 +1612,13 @@ topo_status solve_stencil_fp64(topo_ctx* c, const double* rho, const double* F, 
     // vectors of the levels CTA 0 runs alone (the V-cycle)
     const size_t dyn = std::max(((size_t)a.mg.nc * (a.mg.nc + 1) / 2 + a.mg.nc) * sizeof(double),
                                 (size_t)a.mg.tail_floats * sizeof(float));
-    TOPO_CUDA_TRY(c, cudaFuncSetAttribute(pcg2_mg_kernel<DIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn));
+    // the attribute is the kernel's largest request, whatever this launch needs: host threads that
+    // launch concurrently then never lower it under one another's launch
+    constexpr size_t dyn_max = std::max(((size_t)MG_COARSE_MAX * (MG_COARSE_MAX + 1) / 2 + MG_COARSE_MAX) * sizeof(double),
+                                        MG_TAIL_BYTES);
+    if (dyn > dyn_max) return fail(c, TOPO_ERR_INVALID, "multigrid shared memory %zu B above %zu B", dyn, dyn_max);
+    TOPO_CUDA_TRY(c, cudaFuncSetAttribute(pcg2_mg_kernel<DIM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)dyn_max));
     cfg.dynamicSmemBytes = dyn;
     TOPO_CUDA_TRY(c, cudaLaunchKernelEx(&cfg, pcg2_mg_kernel<DIM>, a));
   } else

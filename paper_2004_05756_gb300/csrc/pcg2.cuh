@@ -72,4 +72,5 @@ topo_status build_pcg2_args(topo_ctx* c, const double* rho, const double* F, dou
 // Resident CTAs per SM of the batched kernel.
 int pcg2_occupancy();
 
+
 }  // namespace topo

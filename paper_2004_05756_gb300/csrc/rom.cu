@@ -19,6 +19,10 @@
 
 namespace topo {
 
+// dynamic shared memory of the k x k Cholesky kernels at the largest k (128): k^2 + k doubles
+constexpr int kCholSmemMax = (128 * 128 + 128) * (int)sizeof(double);
+
+
 // ---------------------------------------------------------------------------------------
 // C = A^T B over N rows (A: N x k1, B: N x k2, column-major, leading dims lda, ldb), written as
 // per-CTA partial sums partial[blockIdx.x][i * k2 + j] (FP64). A CTA owns a contiguous row
@@ -557,9 +561,9 @@ topo_status launch_reduced_solve(topo_ctx* c, int k, const double* b, double* H_
   }
   const size_t sm_chol = (size_t)k * k * sizeof(double);
   const size_t sm_solve = sm_chol + k * sizeof(double);
-  if (sm_solve > 48 * 1024) {
-    TOPO_CUDA_TRY(c, cudaFuncSetAttribute(cholesky_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_solve));
-    TOPO_CUDA_TRY(c, cudaFuncSetAttribute(chol_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_solve));
+  if (sm_solve > 48 * 1024) {  // one value for every k, so concurrent host threads never lower it
+    TOPO_CUDA_TRY(c, cudaFuncSetAttribute(cholesky_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kCholSmemMax));
+    TOPO_CUDA_TRY(c, cudaFuncSetAttribute(chol_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kCholSmemMax));
   }
   cholesky_kernel<<<1, 256, sm_chol, c->stream>>>(H_work, k, &c->d_sync->status, ok, nullptr);
   note_launch();
@@ -697,9 +701,9 @@ extern "C" topo_status topo_rom_solve(topo_ctx* c, const double* rho, const doub
   TOPO_CUDA_TRY(c, cudaMemsetAsync(flags, 0, 8 * sizeof(int), c->stream));
   const size_t sm_chol = (size_t)k * k * sizeof(double);
   const size_t sm_solve = sm_chol + k * sizeof(double);
-  if (sm_solve > 48 * 1024) {
-    TOPO_CUDA_TRY(c, cudaFuncSetAttribute(cholesky_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_solve));
-    TOPO_CUDA_TRY(c, cudaFuncSetAttribute(chol_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm_solve));
+  if (sm_solve > 48 * 1024) {  // one value for every k, so concurrent host threads never lower it
+    TOPO_CUDA_TRY(c, cudaFuncSetAttribute(cholesky_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kCholSmemMax));
+    TOPO_CUDA_TRY(c, cudaFuncSetAttribute(chol_solve_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kCholSmemMax));
   }
   if (prec == TOPO_FP64) {
     cholesky_kernel<<<1, 256, sm_chol, c->stream>>>(H_work, k, &c->d_sync->status, flags + 4, nullptr);

@@ -182,7 +182,10 @@ static topo_status elem_impl(topo_ctx* c, const double* Phi, int k, long long ld
   const size_t budget = 96 * 1024;
   int EB = (int)std::max<size_t>(1, std::min<size_t>(64, (budget - 2 * npair) / (2 * (size_t)ND * k * sizeof(double))));
   const size_t smem = 2 * (size_t)EB * ND * k * sizeof(double) + 2 * (size_t)npair + 16;
-  TOPO_CUDA_TRY(c, cudaFuncSetAttribute(rom_elem_kernel<DIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  // smem <= budget + 16 for every k; the attribute takes that bound, one value for every call, so
+  // host threads that launch concurrently never lower it under one another's launch
+  TOPO_CUDA_TRY(c, cudaFuncSetAttribute(rom_elem_kernel<DIM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)(budget + 16)));
   ElemArgs<DIM> a;
   a.g = c->g;
   a.ke = ke;

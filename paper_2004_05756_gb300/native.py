@@ -350,6 +350,17 @@ class TopoBatch:
         if st != TOPO_OK:
             raise TopoError(st, f"{what}: {self.lib.topo_batch_last_error(self.h).decode(errors='replace')}")
 
+    def set_param(self, which: int, value: float):
+        """topo_set_param on every instance context (e.g. TOPO_PARAM_PCG_MG: 1 runs the batched
+        solve with the multigrid preconditioner, 0 with Jacobi)."""
+        for i in range(self.count):
+            c = ctypes.c_void_p()
+            self._chk(self.lib.topo_batch_context(self.h, i, ctypes.byref(c)), "topo_batch_context")
+            st = self.lib.topo_set_param(c, int(which), float(value))
+            if st != TOPO_OK:
+                raise TopoError(st, f"topo_set_param on instance {i}: "
+                                    f"{self.lib.topo_last_error(c).decode(errors='replace')}")
+
     def close(self):
         if getattr(self, "h", None):
             self.lib.topo_batch_destroy(self.h)
@@ -373,7 +384,8 @@ class TopoBatch:
             self._chk(st, "topo_batch_solve_hdm")
         if not info:
             return None
-        return [dict(iters=x.iters, relres=x.relres, status=x.status, floor=x.floor) for x in inf]
+        return [dict(iters=x.iters, relres=x.relres, status=x.status, floor=x.floor, poly=x.poly,
+                     mg_levels=x.mg_levels, fallback=x.fallback) for x in inf]
 
     def topo_batch_compliance_grad(self, rhos, Us, Fs, J, dcs, dpsis=None):
         ms, lds = zip(*[_cols(U, 0) for U in Us])

@@ -158,3 +158,22 @@ def test_mg_too_small_to_coarsen_uses_polynomial(torch):
     info = T.topo_solve_hdm(dev(rho), cols(p.F), U, rtol=1e-13, maxit=1000, prec="fp64")
     assert info["mg_levels"] == 0 and info["poly"] >= 1
     _check(p, rho, U, info, Jo)
+
+
+def test_mg_stagnation_falls_back_to_polynomial(torch):
+    """A seeded design whose FP32 V-cycle stalls (a stiff region held by void elements, two top-edge
+    load cases: the 68x34 instance of the 256-instance batch): the solve notices that the residual
+    no longer halves, finishes with the polynomial preconditioner and reports the fallback,
+    instead of running to maxit."""
+    from paper_2004_05756_gb300.native import Topo
+    d = w.batch_instances(256)[103]
+    p = d["problem"]
+    assert (p.nx, p.ny, p.F.shape[1]) == (68, 34, 2)
+    rho = hatfilter.filter_fwd(p, w.design_field(p, d["design_seed"]))
+    Jo = _oracle(p, rho)
+    T = Topo(p)
+    U = torch.zeros((2, p.ndof), dtype=torch.float64, device="cuda")
+    info = T.topo_solve_hdm(dev(rho), cols(p.F), U, rtol=1e-8, maxit=20000, prec="fp64")
+    T.topo_check()
+    assert info["status"] == 0 and info["fallback"] == 1 and info["iters"] < 2000, info
+    _check(p, rho, U, info, Jo, rtol=1e-8)
