@@ -1569,6 +1569,69 @@ int pcg2_occupancy() {
 // Degree of the polynomial preconditioner when TOPO_PARAM_PCG_POLY is 0.
 static int pcg_poly_auto(int dim) { return dim == 2 ? 8 : 4; }
 
+// One 2D solve staged for a share of at most max_ctas CTAs, to be launched on any stream: the
+// same preconditioner choice, grid size and arguments as topo_solve_hdm (the batched multigrid
+// form launches many such solves concurrently, one stream each).
+topo_status stage_solo2(topo_ctx* c, const double* rho, const double* F, double* U, int m, int ld, double rtol,
+                        int maxit, int max_ctas, SoloLaunch2* out) {
+  const Grid& g = c->g;
+  const long long nunits = (long long)((g.nnx + 31) / 32) * g.nny * g.nnz;
+  const bool want_mg = c->pcg_mg != 0;
+  int occ = 0;
+  if (want_mg)
+    TOPO_CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pcg2_mg_kernel<2>, P2_THREADS_SOLO, 0));
+  else
+    TOPO_CUDA_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, pcg2_kernel<2>, P2_THREADS_SOLO, 0));
+  if (occ < 1) return fail(c, TOPO_ERR_CUDA, "pcg2 kernel cannot be resident");
+  const int per_sm = c->pcg_blocks_per_sm > 0 ? std::min(c->pcg_blocks_per_sm, occ) : std::min(occ, 2);
+  long long G = std::min<long long>((long long)per_sm * c->num_sms, std::max(1, max_ctas));
+  const long long maxG = (nunits + P2_THREADS_SOLO / 32 - 1) / (P2_THREADS_SOLO / 32);
+  if (G > maxG) G = std::max(1LL, maxG);
+  const int poly = c->pcg_poly > 0 ? c->pcg_poly : pcg_poly_auto(2);
+  topo_status st = build_pcg2_args<2>(c, rho, F, U, m, ld, rtol, maxit, (int)G, &out->a, c->d_sync, poly, want_mg);
+  if (st) return st;
+  out->mg = want_mg && out->a.mg.L >= 2;
+  if (want_mg && !out->mg) {
+    st = build_pcg2_args<2>(c, rho, F, U, m, ld, rtol, maxit, (int)G, &out->a, c->d_sync, poly, false);
+    if (st) return st;
+  }
+  out->G = (unsigned)G;
+  out->dyn = 0;
+  if (out->mg) {
+    const MgArgs& M = out->a.mg;
+    out->dyn = std::max(((size_t)M.nc * (M.nc + 1) / 2 + M.nc) * sizeof(double), (size_t)M.tail_floats * sizeof(float));
+    constexpr size_t dyn_max = std::max(((size_t)MG_COARSE_MAX * (MG_COARSE_MAX + 1) / 2 + MG_COARSE_MAX) * sizeof(double),
+                                        MG_TAIL_BYTES);
+    if (out->dyn > dyn_max) return fail(c, TOPO_ERR_INVALID, "multigrid shared memory %zu B above %zu B", out->dyn, dyn_max);
+    // one value for every launch (see solve_stencil_fp64); set here, never while launching
+    TOPO_CUDA_TRY(c, cudaFuncSetAttribute(pcg2_mg_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)dyn_max));
+  }
+  return TOPO_OK;
+}
+
+// The staged solve's state resets and its cooperative launch on stream (no host synchronisation,
+// no attribute or occupancy calls: capturable in a CUDA graph).
+cudaError_t launch_solo2(topo_ctx* c, const SoloLaunch2& s, cudaStream_t stream) {
+  cudaError_t e = cudaMemsetAsync(c->d_bar, 0, sizeof(GridBar), stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s.a.zflag, 0, sizeof(unsigned long long) * s.G, stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(s.a.info, 0, 32, stream);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(s.G);
+  cfg.blockDim = dim3(P2_THREADS_SOLO);
+  cfg.dynamicSmemBytes = s.dyn;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  e = s.mg ? cudaLaunchKernelEx(&cfg, pcg2_mg_kernel<2>, s.a) : cudaLaunchKernelEx(&cfg, pcg2_kernel<2>, s.a);
+  if (e == cudaSuccess) note_launch();
+  return e;
+}
+
 template <int DIM>
 topo_status solve_stencil_fp64(topo_ctx* c, const double* rho, const double* F, double* U, int m, int ld, double rtol,
                                int maxit, topo_solve_info* info_host) {

@@ -72,5 +72,17 @@ topo_status build_pcg2_args(topo_ctx* c, const double* rho, const double* F, dou
 // Resident CTAs per SM of the batched kernel.
 int pcg2_occupancy();
 
+// A single 2D solve (topo_solve_hdm's preconditioner choice and arguments) staged for a share of
+// at most max_ctas CTAs and launched on a given stream: the batched multigrid form runs many
+// concurrently. The solve's info words are a.info (iters, -, status, fallback) and a.info_rr.
+struct SoloLaunch2 {
+  Pcg2Args<2> a;
+  unsigned G;
+  size_t dyn;
+  int mg;
+};
+topo_status stage_solo2(topo_ctx* c, const double* rho, const double* F, double* U, int m, int ld, double rtol,
+                        int maxit, int max_ctas, SoloLaunch2* out);
+cudaError_t launch_solo2(topo_ctx* c, const SoloLaunch2& s, cudaStream_t stream);
 
 }  // namespace topo

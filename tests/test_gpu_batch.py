@@ -21,17 +21,25 @@ def _instances():
     return out
 
 
-def test_batched_solve_matches_singles_and_oracle():
+@pytest.mark.parametrize("mg", [1, 0], ids=["multigrid", "jacobi"])
+def test_batched_solve_matches_singles_and_oracle(mg):
+    """Both launches of the batched solve: the multigrid one (default; the two smallest meshes
+    do not coarsen and run the polynomial inside it) and the Jacobi one."""
     torch = require_cuda()
-    from paper_2004_05756_gb300.native import Topo, TopoBatch
+    from paper_2004_05756_gb300.native import Topo, TopoBatch, TOPO_PARAM_PCG_MG
     inst = _instances()
     B = TopoBatch([p for p, _ in inst])
+    B.set_param(TOPO_PARAM_PCG_MG, mg)
     rhos = [dev(hatfilter.filter_fwd(p, psi)) for p, psi in inst]
     Fs = [cols(p.F) for p, _ in inst]
     Us = [torch.zeros_like(F) for F in Fs]
     infos = B.topo_batch_solve_hdm(rhos, Fs, Us, rtol=1e-13, maxit=100000)
     for i, (p, psi) in enumerate(inst):
         assert infos[i]["status"] == 0 and infos[i]["relres"] <= max(1e-13, infos[i]["floor"]), (i, infos[i])
+        if mg and p.ndof > 400:
+            assert infos[i]["mg_levels"] >= 2 and infos[i]["fallback"] == 0, (i, infos[i])
+        if not mg:
+            assert infos[i]["mg_levels"] == 0 and infos[i]["poly"] == 1, (i, infos[i])
         rho = rhos[i].cpu().numpy()
         Uo = fem.solve(p, rho)
         Ug = host_cols(Us[i])
