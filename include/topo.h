@@ -376,13 +376,22 @@ const char* topo_batch_last_error(const topo_batch* batch);
 /* The context of instance i (owned by the batch). */
 topo_status topo_batch_context(topo_batch* batch, int i, topo_ctx** out);
 
-/* All state solves (Eq. linelastsoln) in ONE persistent cooperative launch: each instance runs
- * the FP64 assembled-stencil PCG of topo_solve_hdm on its own group of co-resident CTAs (sized by
- * nodes x load cases x mesh width) with its own barrier and convergence; instances that do not
- * fit the co-resident capacity run in further waves. The first call tunes the CTAs per SM on
- * short runs (initial guesses are saved and restored) and caches the choice in the batch.
- * U[i] holds the initial guess and receives the solution. info_host (host array of count, may be
- * NULL) makes the call synchronise and report per instance. */
+/* All state solves (Eq. linelastsoln) of the batch, in one of two forms chosen by the instance
+ * contexts' TOPO_PARAM_PCG_MG (set it on every instance through topo_batch_context):
+ *  - 1 on every instance (the default): each instance runs topo_solve_hdm's multigrid-
+ *    preconditioned FP64 solve as its own persistent cooperative launch with a fixed share of
+ *    the SMs (SMs / S CTAs), on one of S internal streams (instances assigned largest first to
+ *    the least loaded stream; the streams fork from and join back to the batch's stream). The
+ *    first call tunes S over 4, 8 and 16 on short runs.
+ *  - otherwise: ONE persistent cooperative launch in which each instance runs the Jacobi-
+ *    preconditioned FP64 stencil PCG on its own group of co-resident CTAs (sized by nodes x load
+ *    cases x mesh width) with its own barrier and convergence; instances that do not fit the
+ *    co-resident capacity run in further waves. The first call tunes the CTAs per SM.
+ * Tuning runs save and restore the initial guesses. U[i] holds the initial guess and receives
+ * the solution. A call identical to the previous one (same arguments, no info) replays its staged
+ * launches without host synchronisation. info_host (host array of count, may be NULL) makes the
+ * call synchronise and report per instance (iterations, relative residual, FP64 floor, status,
+ * preconditioner fields as topo_solve_hdm). */
 topo_status topo_batch_solve_hdm(topo_batch* batch, const double* const* rho, const double* const* F,
                                  double* const* U, const int* m, const int* ld, double rtol, int maxit,
                                  topo_solve_info* info_host);
