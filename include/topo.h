@@ -78,8 +78,9 @@ typedef struct {
                      and for the multigrid preconditioner */
   int mg_levels;  /* levels of the multigrid preconditioner of the FP64 stencil solve (0 when the
                      solve used another preconditioner) */
-  int fallback;   /* 1 when the FP32 V-cycle stopped being positive definite (conditioning beyond
-                     FP32) and the solve restarted from its true residual with FP64 Jacobi */
+  int fallback;   /* 1 when the multigrid solve continued with the polynomial preconditioner from
+                     its true residual: the FP32 V-cycle stopped being positive definite, or the
+                     residual stopped halving within 64 iterations (conditioning beyond FP32) */
 } topo_solve_info;
 
 /* Tunable parameters (topo_set_param). */
