@@ -33,10 +33,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 # DRAM bytes (read + write) of one launch of the HDM solve kernel (pcg2_mg_kernel) at MBB 600x200,
-# rtol 1e-8, from a full ncu capture (dram__bytes_read.sum, dram__bytes_write.sum) of
+# rtol 1e-8, from an ncu capture (dram__bytes_read.sum, dram__bytes_write.sum) of
 # `python -m paper_2004_05756_gb300.profcase --call hdm --rtol 1e-8 --reps 1`. It is reported only
 # while the kernel sources hash to the value they had when it was taken.
-PCG_TRAFFIC = {"bytes": 168.303104e6 + 267.38432e6, "sources_sha256_16": "5ba5bc210325e492"}
+PCG_TRAFFIC = {"bytes": 303.934464e6 + 377.437696e6, "sources_sha256_16": "45ad17115a3bd2ad"}
 
 
 def pcg_traffic():
