@@ -67,6 +67,12 @@ struct topo_batch {
   std::vector<topo::SoloLaunch2> c_solo;
   std::vector<int> c_stream_of;  // per instance, launch order is c_order
   std::vector<int> c_order;
+  // batched reduced solves: device tables, partial sums, flags and their signature
+  void* d_rom;
+  size_t rom_bytes;
+  std::vector<unsigned long long> sig_rom;
+  int rom_items, rom_ypairs;
+  size_t rom_inst_off, rom_item_off, rom_red_off, rom_part_off;
   char err[512];
 };
 
@@ -392,6 +398,173 @@ static topo_status batch_solve_dim(topo_batch* b, const double* const* rho, cons
   return TOPO_OK;
 }
 
+// ---------------------------------------------------------------------------------------
+// Batched reduced solves (element path): H_i = sum_e E(rho_i,e) Hel_i[e] + Hel_i[N_e,i], then
+// y_i = H_i^-1 b_i, J_i = b_i^T y_i, for every instance in three launches.
+// ---------------------------------------------------------------------------------------
+struct BromInst {
+  const double* Hel;
+  const double* rho;
+  double* H;
+  long long nel;     // element rows; row nel (weight 1) holds the Dirichlet term
+  long long part0;   // offset of the instance's first item partial (doubles)
+  int npair, k, item0, nitems;
+  double E0, Emin;
+  int ipenal, pad;
+};
+struct BromItem {
+  long long r0, r1;  // rows [r0, r1) of instance inst
+  int inst, local;   // local: index of the item within its instance
+};
+constexpr int BROM_CHUNK = 256;  // rows whose moduli a CTA stages at a time
+
+// partial[part0 + local * npair + p] = sum over the item's rows e of E_e Hel[e][p] (thread = p;
+// grid.y covers the pairs). The item's moduli are computed once per row into shared memory.
+__global__ void __launch_bounds__(256) brom_partial_kernel(const BromInst* __restrict__ insts,
+                                                           const BromItem* __restrict__ items, double* partial) {
+  __shared__ double Es[BROM_CHUNK];
+  const BromItem it = items[blockIdx.x];
+  const BromInst& I = insts[it.inst];
+  const int p = blockIdx.y * blockDim.x + threadIdx.x;
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (long long c0 = it.r0; c0 < it.r1; c0 += BROM_CHUNK) {
+    const int n = (int)min((long long)BROM_CHUNK, it.r1 - c0);
+    __syncthreads();
+    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+      const long long e = c0 + t;
+      Es[t] = e < I.nel ? young<double>(__ldg(I.rho + e), I.E0, I.Emin, I.ipenal) : 1.0;
+    }
+    __syncthreads();
+    if (p < I.npair) {
+      int t = 0;
+      for (; t + 3 < n; t += 4) {
+        double h[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) h[q] = __ldcs(I.Hel + (c0 + t + q) * I.npair + p);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[q] = fma(Es[t + q], h[q], acc[q]);
+      }
+      for (; t < n; ++t) acc[0] = fma(Es[t], __ldcs(I.Hel + (c0 + t) * I.npair + p), acc[0]);
+    }
+  }
+  if (p < I.npair) partial[I.part0 + (long long)it.local * I.npair + p] = (acc[0] + acc[1]) + (acc[2] + acc[3]);
+}
+
+// H_i from its items' partials, summed in item order (block = instance, thread = pair).
+__global__ void __launch_bounds__(256) brom_final_kernel(const BromInst* __restrict__ insts, const double* partial) {
+  const BromInst& I = insts[blockIdx.x];
+  for (int p = threadIdx.x; p < I.npair; p += blockDim.x) {
+    double s = 0.0;
+    for (int q = 0; q < I.nitems; ++q) s += __ldcg(partial + I.part0 + (long long)q * I.npair + p);
+    int i = 0, rem = p;
+    while (rem >= I.k - i) {
+      rem -= I.k - i;
+      ++i;
+    }
+    const int j = i + rem;
+    I.H[i * I.k + j] = s;
+    I.H[j * I.k + i] = s;
+  }
+}
+
+static topo_status batch_rom_solve_multi(topo_batch* b, const double* const* rho, const double* const* Hel,
+                                         const int* k, const double* const* bvec, double* const* H_work,
+                                         double* const* yhat, double* Jk) {
+  const int n = b->count;
+  std::vector<unsigned long long> sig;
+  sig.reserve(6 * (size_t)n + 1);
+  for (int i = 0; i < n; ++i) {
+    sig.push_back((unsigned long long)(uintptr_t)rho[i]);
+    sig.push_back((unsigned long long)(uintptr_t)Hel[i]);
+    sig.push_back((unsigned long long)k[i]);
+    sig.push_back((unsigned long long)(uintptr_t)bvec[i]);
+    sig.push_back((unsigned long long)(uintptr_t)H_work[i]);
+    sig.push_back((unsigned long long)(uintptr_t)yhat[i]);
+  }
+  sig.push_back((unsigned long long)(uintptr_t)Jk);
+  if (sig != b->sig_rom) {
+    // items: about eight per SM over the whole batch, each at least one chunk of rows
+    long long total = 0;
+    for (int i = 0; i < n; ++i) total += b->ctx[i]->g.nel + 1;
+    long long per = std::max<long long>(BROM_CHUNK, (total + 8LL * b->num_sms - 1) / (8LL * b->num_sms));
+    per = (per + BROM_CHUNK - 1) / BROM_CHUNK * BROM_CHUNK;
+    std::vector<BromInst> insts(n);
+    std::vector<BromItem> items;
+    std::vector<RedSolve> red(n);
+    long long part = 0;
+    int maxpair = 1;
+    for (int i = 0; i < n; ++i) {
+      const topo_ctx* c = b->ctx[i];
+      BromInst& I = insts[i];
+      I.Hel = Hel[i];
+      I.rho = rho[i];
+      I.H = H_work[i];
+      I.nel = c->g.nel;
+      I.npair = k[i] * (k[i] + 1) / 2;
+      I.k = k[i];
+      I.E0 = c->g.E0;
+      I.Emin = c->g.Emin;
+      I.ipenal = c->g.ipenal;
+      I.pad = 0;
+      I.item0 = (int)items.size();
+      const long long rows = c->g.nel + 1;
+      int local = 0;
+      for (long long r0 = 0; r0 < rows; r0 += per, ++local) items.push_back({r0, std::min(rows, r0 + per), i, local});
+      I.nitems = local;
+      I.part0 = part;
+      part += (long long)local * I.npair;
+      maxpair = std::max(maxpair, I.npair);
+    }
+    const size_t oi = 0, oit = (sizeof(BromInst) * n + 255) & ~(size_t)255;
+    const size_t ored = oit + ((sizeof(BromItem) * items.size() + 255) & ~(size_t)255);
+    const size_t ook = ored + ((sizeof(RedSolve) * n + 255) & ~(size_t)255);
+    const size_t opart = ook + ((sizeof(int) * n + 255) & ~(size_t)255);
+    const size_t need = opart + sizeof(double) * (size_t)part;
+    if (need > b->rom_bytes) {
+      TOPO_CUDA_TRY(b->ctx[0], cudaStreamSynchronize(b->stream));
+      if (b->d_rom) cudaFree(b->d_rom);
+      b->d_rom = nullptr;
+      b->rom_bytes = 0;
+      TOPO_CUDA_TRY(b->ctx[0], cudaMalloc(&b->d_rom, need));
+      b->rom_bytes = need;
+    }
+    char* base = (char*)b->d_rom;
+    for (int i = 0; i < n; ++i)
+      red[i] = {H_work[i], bvec[i], yhat[i], Jk + i, &b->ctx[i]->d_sync->status, (int*)(base + ook) + i, k[i], 0};
+    const size_t tbytes = opart;
+    if (tbytes > b->stage_bytes) {
+      TOPO_CUDA_TRY(b->ctx[0], cudaStreamSynchronize(b->stream));
+      if (b->h_stage) cudaFreeHost(b->h_stage);
+      b->h_stage = nullptr;
+      TOPO_CUDA_TRY(b->ctx[0], cudaMallocHost(&b->h_stage, tbytes));
+      b->stage_bytes = tbytes;
+    }
+    // the pinned staging may still feed a previous call's copies: wait for them
+    TOPO_CUDA_TRY(b->ctx[0], cudaStreamSynchronize(b->stream));
+    char* h = (char*)b->h_stage;
+    memcpy(h + oi, insts.data(), sizeof(BromInst) * n);
+    memcpy(h + oit, items.data(), sizeof(BromItem) * items.size());
+    memcpy(h + ored, red.data(), sizeof(RedSolve) * n);
+    TOPO_CUDA_TRY(b->ctx[0], cudaMemcpyAsync(base, h, ook, cudaMemcpyHostToDevice, b->stream));
+    b->rom_items = (int)items.size();
+    b->rom_ypairs = (maxpair + 255) / 256;
+    b->rom_inst_off = oi;
+    b->rom_item_off = oit;
+    b->rom_red_off = ored;
+    b->rom_part_off = opart;
+    b->sig_rom = sig;
+  }
+  char* base = (char*)b->d_rom;
+  const BromInst* d_inst = (const BromInst*)(base + b->rom_inst_off);
+  brom_partial_kernel<<<dim3((unsigned)b->rom_items, (unsigned)b->rom_ypairs), 256, 0, b->stream>>>(
+      d_inst, (const BromItem*)(base + b->rom_item_off), (double*)(base + b->rom_part_off));
+  note_launch();
+  brom_final_kernel<<<n, 256, 0, b->stream>>>(d_inst, (const double*)(base + b->rom_part_off));
+  note_launch();
+  TOPO_CUDA_TRY(b->ctx[0], launch_chol_small_multi((const RedSolve*)(base + b->rom_red_off), n, b->stream));
+  return TOPO_OK;
+}
+
 }  // namespace topo
 
 using namespace topo;
@@ -439,6 +612,7 @@ extern "C" topo_status topo_batch_destroy(topo_batch* b) {
   cudaFree(b->d_args);
   cudaFree(b->d_tab);
   if (b->h_stage) cudaFreeHost(b->h_stage);
+  cudaFree(b->d_rom);
   delete b;
   return TOPO_OK;
 }
@@ -540,6 +714,18 @@ extern "C" topo_status topo_batch_rom_solve_elem(topo_batch* b, const double* co
                                                  const int* k, const double* const* bvec, double* const* H_work,
                                                  double* const* yhat, double* Jk) {
   if (!b || !rho || !Hel || !k || !bvec || !H_work || !yhat || !Jk) return TOPO_ERR_INVALID;
+  bool small = true;
+  for (int i = 0; i < b->count; ++i) {
+    if (k[i] < 1 || k[i] > 128 || !dev_ptr_ok(rho[i]) || !dev_ptr_ok(Hel[i]) || !dev_ptr_ok(bvec[i]) ||
+        !dev_ptr_ok(H_work[i]) || !dev_ptr_ok(yhat[i]) || !dev_ptr_ok(Jk))
+      return bfail(b, TOPO_ERR_INVALID, "batched reduced solve: 1 <= k <= 128 and device pointers required");
+    small = small && k[i] <= 32;
+  }
+  if (small) {
+    topo_status s = batch_rom_solve_multi(b, rho, Hel, k, bvec, H_work, yhat, Jk);
+    return s ? bfail(b, s, b->ctx[0]->err) : TOPO_OK;
+  }
+  // a basis above 32 vectors: one call per instance (the CTA-wide Cholesky of topo_rom_solve_elem)
   for (int i = 0; i < b->count; ++i) {
     topo_status s = topo_rom_solve_elem(b->ctx[i], rho[i], Hel[i], k[i], bvec[i], H_work[i], yhat[i], Jk + i);
     if (s) return bfail(b, s, b->ctx[i]->err);

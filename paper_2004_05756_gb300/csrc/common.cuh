@@ -598,6 +598,20 @@ long long residual_tiles(topo_ctx* c);
 // partials reduced to out2[0..1] (device). r may be NULL (norms only).
 topo_status launch_residual64(topo_ctx* c, const double* rho, const double* u, const double* f, double* r,
                               double* out2);
+// One reduced solve of a batch of different problems (k <= 32): the FP64 Cholesky of H (k x k,
+// row-major, overwritten by L), y = H^-1 b, *J = b^T y, *ok = 1 (0 and NOT_SPD in *status on a
+// non-positive pivot). launch_chol_small_multi runs n of them, one warp each (rom.cu).
+struct RedSolve {
+  double* H;
+  const double* b;
+  double* y;
+  double* J;
+  int* status;
+  int* ok;
+  int k;
+  int pad;
+};
+cudaError_t launch_chol_small_multi(const RedSolve* tab, int n, cudaStream_t stream);
 // Deterministic sum of n doubles -> *out (device), two passes.
 topo_status launch_sum(topo_ctx* c, const double* x, long long n, double* out);
 // Tensor-core contraction (tcgen05, kind::tf32 with an exact hi/lo split of each FP32 operand):

@@ -349,6 +349,18 @@ __global__ void __launch_bounds__(32) chol_small_batch_kernel(double* H, int k, 
   chol_small_body<KMAX>(H + (size_t)r * k * k, k, b, y + (size_t)r * k, J + r, status, ok + r);
 }
 
+// Reduced solves of different problems (each its own H, b, k <= 32), one warp each.
+__global__ void __launch_bounds__(32) chol_small_multi_kernel(const RedSolve* __restrict__ tab) {
+  const RedSolve t = tab[blockIdx.x];
+  chol_small_body<32>(t.H, t.k, t.b, t.y, t.J, t.status, t.ok);
+}
+
+cudaError_t launch_chol_small_multi(const RedSolve* tab, int n, cudaStream_t stream) {
+  chol_small_multi_kernel<<<n, 32, 0, stream>>>(tab);
+  note_launch();
+  return cudaGetLastError();
+}
+
 // Solve L L^T x = rhs (L lower, row-major). mode 0: y = x; mode 1: y += x. Skipped (y left
 // unchanged) when *skip is non-zero; NaN output when the factorisation failed.
 __global__ void chol_solve_kernel(const double* L, int k, const double* rhs, double* y, int mode, const int* ok_flag,

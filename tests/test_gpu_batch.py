@@ -66,7 +66,13 @@ def test_batched_solve_matches_singles_and_oracle(mg):
         assert relerr(outs[i].cpu().numpy(), hatfilter.filter_fwd(p, psi)) < 1e-14
 
 
-def test_batched_rom_solve_elem():
+@pytest.mark.parametrize("ks", [[4, 6, 8, 3], [32, 16, 8, 1], [32, 16, 8, 40]],
+                         ids=["small", "k_up_to_32", "one_k_above_32"])
+def test_batched_rom_solve_elem(ks):
+    """Reduced solves of every instance: bases up to 32 vectors take the three-launch path
+    (all instances' assemblies in one launch, one warp per Cholesky), a basis above 32 the
+    per-instance calls; both against the oracle's reduced solve, and the cached path of an
+    identical second call bitwise equal to the first."""
     torch = require_cuda()
     from paper_2004_05756_gb300.native import TopoBatch
     inst = _instances()[:4]
@@ -74,9 +80,10 @@ def test_batched_rom_solve_elem():
     from paper_2004_05756_gb300.native import load
     import ctypes
     rng = np.random.default_rng(3)
-    rhos, Hels, ks, bs, Hws, ys, refs = [], [], [], [], [], [], []
+    rhos, Hels, bs, Hws, ys, refs = [], [], [], [], [], []
     for i, (p, psi) in enumerate(inst):
-        k = [4, 6, 8, 3][i]
+        k = min(ks[i], p.ndof)
+        ks[i] = k
         Phi, _ = np.linalg.qr(rng.standard_normal((p.ndof, k)))
         rho = rng.uniform(1e-3, 1, p.nel)
         npair = k * (k + 1) // 2
@@ -87,13 +94,16 @@ def test_batched_rom_solve_elem():
         b = rng.standard_normal(k)
         H = Phi.T @ fem.apply_K(p, rho, Phi)
         refs.append(b @ rom.solve_reduced(0.5 * (H + H.T), b))
-        rhos.append(dev(rho)); Hels.append(Hel); ks.append(k); bs.append(dev(b))
+        rhos.append(dev(rho)); Hels.append(Hel); bs.append(dev(b))
         Hws.append(torch.zeros(k * k, dtype=torch.float64, device="cuda"))
         ys.append(torch.zeros(k, dtype=torch.float64, device="cuda"))
     Jk = torch.zeros(len(inst), dtype=torch.float64, device="cuda")
     B.topo_batch_rom_solve_elem(rhos, Hels, ks, bs, Hws, ys, Jk)
+    first = Jk.cpu().numpy().copy()
     for i in range(len(inst)):
-        assert abs(Jk[i].item() - refs[i]) <= 1e-10 * abs(refs[i])
+        assert abs(first[i] - refs[i]) <= 1e-10 * abs(refs[i]), (i, ks[i], first[i], refs[i])
+    B.topo_batch_rom_solve_elem(rhos, Hels, ks, bs, Hws, ys, Jk)
+    assert np.array_equal(Jk.cpu().numpy(), first)
 
 
 def test_batched_step_in_cuda_graph():
