@@ -672,9 +672,12 @@ def run_ours(args, rank, world):
 
 def run_batch(args):
     """Batched form: 256 uneven MBB instances (nx log-uniform in [40, 400], ny = nx/2, 1..8
-    top-edge load cases, own seeded design). One step = one HDM design evaluation of every
-    instance: batched filter, ALL state solves in one persistent launch, batched compliance
-    and filtered gradient. Metric: design evaluations (instances) per second."""
+    top-edge load cases, own seeded design, a reduced basis of k in {8, 16, 32} vectors). One
+    step = one HDM design evaluation of every instance (batched filter, all state solves,
+    batched compliance and filtered gradient) plus one reduced solve of every instance at its
+    design (all instances' reduced matrices and Cholesky solves in three launches). The bases are
+    seeded random vectors orthonormalised by topo_rom_build (the reduced solve's cost does not
+    depend on the basis). Metric: instances evaluated per second."""
     import torch
     from paper_2004_05756_gb300 import build, native
     from paper_2004_05756_gb300 import workloads as w
@@ -695,6 +698,28 @@ def run_batch(args):
         dcs = [torch.empty(p.nel, **f64) for p in probs]
         dps = [torch.empty(p.nel, **f64) for p in probs]
         flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+        # reduced bases (setup, untimed): k seeded random vectors per instance, orthonormalised by
+        # the library, and their element reduced matrices
+        gen = torch.Generator(device="cuda")
+        gen.manual_seed(4242)
+        B.topo_batch_filter(psis, rhos)
+        ks, Hels, bs, Hws, ys = [], [], [], [], []
+        for i, (p, d) in enumerate(zip(probs, insts)):
+            T = B.context(i)
+            k = d["k"]
+            snaps = torch.randn((k, p.ndof), generator=gen, **f64)
+            Phi = torch.zeros((k, p.ndof), **f64)
+            bvec = torch.zeros(k, **f64)
+            kk = T.topo_rom_build(rhos[i], snaps, Phi, None, bvec, Fs[i][0])
+            Hel = torch.empty((p.nel + 1) * kk * (kk + 1) // 2, **f64)
+            T.topo_rom_elem(Phi[:kk], kk, Hel)
+            ks.append(kk)
+            Hels.append(Hel)
+            bs.append(bvec[:kk])
+            Hws.append(torch.empty(kk * kk, **f64))
+            ys.append(torch.empty(kk, **f64))
+            del snaps, Phi
+        Jk = torch.zeros(len(probs), **f64)
 
         def body():
             B.topo_batch_filter(psis, rhos)
@@ -702,6 +727,7 @@ def run_batch(args):
                 U.zero_()
             B.topo_batch_solve_hdm(rhos, Fs, Us, rtol=1e-8, maxit=100000, info=False)
             B.topo_batch_compliance_grad(rhos, Us, Fs, J, dcs, dps)
+            B.topo_batch_rom_solve_elem(rhos, Hels, ks, bs, Hws, ys, Jk)
 
         def timed(run):
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -764,6 +790,17 @@ def run_batch(args):
             solve_only.append(timed(lambda: B.topo_batch_solve_hdm(rhos, Fs, Us, rtol=1e-8, maxit=100000,
                                                                    info=False)))
         rho_host = [r.cpu().numpy() for r in rhos]
+        # the reduced solves alone: the batched call against one call per instance
+        rom_batch, rom_each = [], []
+        ctxs = [B.context(i) for i in range(len(probs))]
+        Jk1 = torch.zeros(len(probs), **f64)
+        for _ in range(max(1, min(args.steps, 3))):
+            flush.zero_()
+            rom_batch.append(timed(lambda: B.topo_batch_rom_solve_elem(rhos, Hels, ks, bs, Hws, ys, Jk)))
+            flush.zero_()
+            rom_each.append(timed(lambda: [T.topo_rom_solve_elem(rhos[i], Hels[i], ks[i], bs[i], Hws[i], ys[i],
+                                                                 Jk1[i:i + 1]) for i, T in enumerate(ctxs)]))
+        rom_dev = float((Jk - Jk1).abs().max().item() / Jk1.abs().max().item())
     ms = statistics.fmean(times)
     at_floor = [i for i, x in enumerate(infos) if x["relres"] > 1e-8]
     cpu = None
@@ -800,13 +837,19 @@ def run_batch(args):
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": f"batch256: {len(probs)} MBB Q4 instances, nx 40..400 log-uniform, "
-                                   f"{ndof} DOFs, {nlc} load cases; one HDM eval each per step, solves in one "
-                                   f"persistent launch", "instances": len(probs), "total_dofs": ndof,
-                       "load_cases": nlc},
+                                   f"{ndof} DOFs, {nlc} load cases, reduced bases k in {{8, 16, 32}}; one HDM "
+                                   f"eval and one reduced solve of every instance per step",
+                       "instances": len(probs), "total_dofs": ndof, "load_cases": nlc,
+                       "l2": "flushed between steps (256 MB write)"},
             "max_iters": max(x["iters"] for x in infos), "all_converged": all(x["status"] == 0 for x in infos),
             "max_relres": max(x["relres"] for x in infos), "max_floor": max(x["floor"] for x in infos),
             "instances_at_floor": len(at_floor), "gpu_launches": launches,
             "batch_solve_ms": statistics.fmean(solve_only),
+            "rom_reduced_solves": {"what": "all instances' reduced solves (k in {8, 16, 32}) in one "
+                                           "topo_batch_rom_solve_elem call, against one topo_rom_solve_elem "
+                                           "call per instance", "batched_ms": statistics.fmean(rom_batch),
+                                   "per_instance_ms": statistics.fmean(rom_each),
+                                   "max_rel_diff_of_Jk": rom_dev},
             "sequential": {"what": f"the same {len(probs)} state solves as sequential topo_solve_hdm calls (one "
                                    f"context per instance, multigrid-preconditioned, rtol 1e-8), CUDA events",
                            "ms": statistics.fmean(seq_times), "runs": len(seq_times),

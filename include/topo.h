@@ -402,7 +402,13 @@ topo_status topo_batch_filter(topo_batch* batch, const double* const* in, double
 topo_status topo_batch_compliance_grad(topo_batch* batch, const double* const* rho, const double* const* U,
                                        const int* m, const int* ld, const double* const* F, double* J,
                                        double* const* dc_rho, double* const* dc_psi);
-/* topo_rom_solve_elem on every instance; k is a HOST array, Jk a DEVICE array of count. */
+/* topo_rom_solve_elem on every instance (Section 3.1 Eq. rom_soln with the element reduced
+ * matrices of topo_rom_elem); k is a HOST array, Jk a DEVICE array of count. When every k <= 32
+ * all instances run in three launches: one assembly of every H_i over a table of (instance, row
+ * range) items, one fixed-order reduction per instance, one warp per Cholesky; the tables are
+ * staged once and reused while the arguments are unchanged (no host synchronisation then).
+ * Otherwise each instance runs topo_rom_solve_elem. A non-positive pivot sets NOT_SPD in that
+ * instance's context status and NaN in its y and Jk. */
 topo_status topo_batch_rom_solve_elem(topo_batch* batch, const double* const* rho, const double* const* Hel,
                                       const int* k, const double* const* b, double* const* H_work,
                                       double* const* yhat, double* Jk);

@@ -170,9 +170,24 @@ class Topo:
         if st != TOPO_OK:
             raise TopoError(st, f"{what}: {self.lib.topo_last_error(self.h).decode(errors='replace')}")
 
+    @classmethod
+    def borrowed(cls, handle, problem, stream=None):
+        """A view of a context the caller does not own (an instance of a topo_batch): the same
+        methods, and close() leaves the context to its owner."""
+        t = cls.__new__(cls)
+        t.lib = load()
+        t.problem = problem
+        t.stream = stream
+        t.h = handle
+        t.N = problem.ndof
+        t.Ne = problem.nel
+        t._borrowed = True
+        return t
+
     def close(self):
         if getattr(self, "h", None):
-            self.lib.topo_destroy(self.h)
+            if not getattr(self, "_borrowed", False):
+                self.lib.topo_destroy(self.h)
             self.h = None
 
     def __del__(self):
@@ -349,6 +364,12 @@ class TopoBatch:
     def _chk(self, st, what):
         if st != TOPO_OK:
             raise TopoError(st, f"{what}: {self.lib.topo_batch_last_error(self.h).decode(errors='replace')}")
+
+    def context(self, i: int):
+        """Topo view of instance i's context (owned by the batch)."""
+        c = ctypes.c_void_p()
+        self._chk(self.lib.topo_batch_context(self.h, int(i), ctypes.byref(c)), "topo_batch_context")
+        return Topo.borrowed(c, self.problems[i])
 
     def set_param(self, which: int, value: float):
         """topo_set_param on every instance context (e.g. TOPO_PARAM_PCG_MG: 1 runs the batched
