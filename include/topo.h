@@ -127,13 +127,27 @@ typedef enum {
                                       to coarsen use the polynomial */
   TOPO_PARAM_MG_DEGREE = 13,       /* multigrid: Chebyshev smoothing steps before and after the
                                       coarse correction, 1 .. 4 (default 2) */
-  TOPO_PARAM_MG_SINGLE_NODES = 14  /* multigrid: coarse levels with at most this many nodes run on
+  TOPO_PARAM_MG_SINGLE_NODES = 14, /* multigrid: coarse levels with at most this many nodes run on
                                       one CTA, their vectors in its shared memory, with block
                                       barriers instead of halo exchanges between CTAs (default
                                       -1: 1024 in 2D, 0 in 3D; levels whose vectors do not fit
                                       96 KB with those of
                                       the coarser levels stay on all CTAs; the coarsest level
                                       always runs on one CTA and level 0 never does) */
+  TOPO_PARAM_FILTER = 15,          /* density filter of topo_filter and of every call that filters
+                                      (topo_rom_eval_batch, topo_compliance_grad's dc_psi): 0 = the
+                                      linear cone filter of radius rmin (default); 1 = the Helmholtz
+                                      filter of Section 2.2 (Eq. helm-soln .. cdens-star): nodal
+                                      phi = H^-1 b(psi) with the Q1 Helmholtz operator
+                                      -r^2 Lap + 1 under Neumann conditions, rho_e = the average of
+                                      phi over the element's nodes. Solved exactly by the cosine
+                                      eigenvectors of the 1D Q1 Neumann matrices (two transforms of
+                                      FP64 mode products and a diagonal scaling); self-adjoint, so
+                                      adjoint = 1 gives the same map */
+  TOPO_PARAM_HELMHOLTZ_R = 16      /* the Helmholtz length r in element lengths (0 = default:
+                                      rmin / (2 sqrt 3), the length the filter's cited reference
+                                      relates to a cone radius rmin; the paper prints
+                                      r = 2 sqrt(3) R) */
 } topo_param;
 
 /* Create a context for one problem; computes K_e (2x2(x2) Gauss quadrature), the filter

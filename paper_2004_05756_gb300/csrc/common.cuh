@@ -568,6 +568,11 @@ struct topo_ctx {
   int pcg_mg;        // FP64 stencil PCG: 1 = multigrid V-cycle preconditioner, 0 = polynomial / Jacobi
   int mg_deg;        // multigrid: Chebyshev smoothing steps per side (1 .. 4)
   long long mg_single_nodes;  // multigrid: levels with at most this many nodes run on one CTA
+  int filter_kind;   // 0 = linear cone filter, 1 = Helmholtz filter
+  double helm_r;     // Helmholtz length r (element lengths; 0 = rmin / (2 sqrt 3))
+  double helm_r_built;  // the r the cosine and diagonal data were built for (-1 = none)
+  double* d_helm;    // Helmholtz filter: cosine matrices, diagonal, work buffers
+  size_t helm_bytes;
   char err[512];
 };
 
@@ -612,6 +617,9 @@ struct RedSolve {
   int pad;
 };
 cudaError_t launch_chol_small_multi(const RedSolve* tab, int n, cudaStream_t stream);
+// The Helmholtz filter of R fields (its own adjoint): field r at in + r ldin -> out + r ldout
+// (helmholtz.cu).
+topo_status helmholtz_apply(topo_ctx* c, const double* in, long long ldin, double* out, long long ldout, int R);
 // Deterministic sum of n doubles -> *out (device), two passes.
 topo_status launch_sum(topo_ctx* c, const double* x, long long n, double* out);
 // Tensor-core contraction (tcgen05, kind::tf32 with an exact hi/lo split of each FP32 operand):

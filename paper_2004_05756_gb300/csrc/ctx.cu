@@ -297,6 +297,8 @@ __global__ void dot_cols_partial_kernel(const double* F, const double* U, long l
 
 static topo_status filter_launch(topo_ctx* c, const double* in, double* out, int mode, int R = 1,
                                  long long ldin = 0, long long ldout = 0) {
+  if (mode != 0 && c->filter_kind == 1)  // the Helmholtz filter is its own adjoint
+    return helmholtz_apply(c, in, R > 1 ? ldin : c->g.nel, out, R > 1 ? ldout : c->g.nel, R);
   FilterArgs a;
   a.ldin = ldin;
   a.ldout = ldout;
@@ -537,6 +539,7 @@ extern "C" topo_status topo_destroy(topo_ctx* c) {
   cudaFree(c->d_bar);
   cudaFree(c->d_scratch);
   cudaFree(c->d_red);
+  cudaFree(c->d_helm);
   free(c);
   return TOPO_OK;
 }
@@ -602,6 +605,14 @@ extern "C" topo_status topo_set_param(topo_ctx* c, topo_param which, double v) {
       if (!(v >= -1 && v <= 1e9 && v == (long long)v))
         return fail(c, TOPO_ERR_INVALID, "mg single-CTA node count must be an integer in [-1,1e9]");
       c->mg_single_nodes = (long long)v;
+      return TOPO_OK;
+    case TOPO_PARAM_FILTER:
+      if (!(v == 0 || v == 1)) return fail(c, TOPO_ERR_INVALID, "filter must be 0 (cone) or 1 (Helmholtz)");
+      c->filter_kind = (int)v;
+      return TOPO_OK;
+    case TOPO_PARAM_HELMHOLTZ_R:
+      if (!(v >= 0 && v <= 1e4)) return fail(c, TOPO_ERR_INVALID, "Helmholtz length must be in [0,1e4]");
+      c->helm_r = v;
       return TOPO_OK;
     case TOPO_PARAM_PCG_BLOCKS_PER_SM:
       if (!(v >= 0 && v <= 8)) return fail(c, TOPO_ERR_INVALID, "blocks per SM must be in [0,8]");

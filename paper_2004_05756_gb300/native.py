@@ -22,7 +22,8 @@ PREC = {"fp64": TOPO_FP64, "fp32": TOPO_FP32_REFINED, "fp32_bf16ke": TOPO_FP32_B
 (TOPO_PARAM_INNER_RTOL, TOPO_PARAM_MAX_OUTER, TOPO_PARAM_WAIT_CYCLES, TOPO_PARAM_ROM_REFINE,
  TOPO_PARAM_TILE_X, TOPO_PARAM_PCG_BLOCKS_PER_SM, TOPO_PARAM_INNER_CAP, TOPO_PARAM_HDM_KERNEL,
  TOPO_PARAM_PCG_MAX_CTAS, TOPO_PARAM_ROM_TENSOR, TOPO_PARAM_APPLY_STAGES, TOPO_PARAM_PCG_POLY,
- TOPO_PARAM_PCG_MG, TOPO_PARAM_MG_DEGREE, TOPO_PARAM_MG_SINGLE_NODES) = range(15)
+ TOPO_PARAM_PCG_MG, TOPO_PARAM_MG_DEGREE, TOPO_PARAM_MG_SINGLE_NODES, TOPO_PARAM_FILTER,
+ TOPO_PARAM_HELMHOLTZ_R) = range(17)
 
 # Every entry point declared in include/topo.h (checked by the tests).
 EXPORTS = ["topo_create", "topo_destroy", "topo_last_error", "topo_set_param", "topo_check", "topo_sizes",
