@@ -207,6 +207,20 @@ topo_status topo_solve_hdm(topo_ctx* ctx, const double* rho, const double* F, do
 topo_status topo_rom_build(topo_ctx* ctx, const double* rho, const double* Usnap, int m, int ld,
                            double* Phi, int* k_out, double* H, double* b, const double* f);
 
+/* POD of a snapshot block (Section 4.2, Eq. rob-optim: POD_n, the first n left singular vectors,
+ * of the previous trust-region centres' states): U is N x m at ld (1 <= m <= 64); column skip
+ * (-1 = none) is left out; Pod (N x (n + 1 if append else n), ldp) receives the n leading left
+ * singular vectors of the remaining m' columns, orthonormal, followed by a copy of append
+ * (FP64[N], may be NULL): the block whose Gram-Schmidt orthonormalisation (topo_rom_build) is the
+ * basis of Eq. rob-optim. sigma (device FP64[m']) receives the singular values in descending
+ * order when n >= 1. 0 <= n <= m'. Method: the Gram matrix U^T U in FP64 and its cyclic Jacobi
+ * eigen-decomposition on one CTA: a singular value carries an error of about
+ * eps sigma_max^2 / sigma_i and its vector a loss of orthogonality of about eps sigma_max^2 /
+ * sigma_i^2; one below about 1.2e-7 of the largest is rounding noise of the Gram matrix, and its
+ * vector is returned as zero (topo_rom_build then drops it). */
+topo_status topo_rom_pod(topo_ctx* ctx, const double* U, int m, int ld, int skip, int n, const double* append,
+                         double* Pod, int ldp, double* sigma);
+
 /* Reduced solve at a new density (Section 3.1 and the cost analysis of Section 3.4):
  * H(rho) = Phi^T K(rho) Phi, Cholesky H = L L^T in FP64, yhat = H^{-1} b, Jk = b^T yhat.
  * Phi: FP64 N x k, ld; b FP64[k]; H_work FP64 k*k (on exit: L in the lower triangle,

@@ -34,6 +34,13 @@ def basis(U: np.ndarray, drop_tol: float = 1e-10) -> np.ndarray:
     return Q
 
 
+def pod(U: np.ndarray, n: int) -> tuple[np.ndarray, np.ndarray]:
+    """POD_n(U) of Section 4.2 (Eq. rob-optim): the first n left singular vectors of U (numpy's
+    SVD) and all its singular values, descending."""
+    Uu, s, _ = np.linalg.svd(np.asarray(U, dtype=float), full_matrices=False)
+    return Uu[:, :n], s
+
+
 def project(p, rho: np.ndarray, Phi: np.ndarray, f: np.ndarray):
     """H = Phi^T K(rho) Phi and b = Phi^T f (Eq. hatkbm, written as the plain product)."""
     W = fem.apply_K(p, rho, Phi)

@@ -33,7 +33,10 @@ Readings where the paper leaves a choice (each is one line of the design notes):
   * The reduced basis is the orthonormalisation of the L most recent centre snapshots, the
     newest being the current centre's (Eq. rob-optim with every POD vector of the window
     kept; for compliance the adjoint snapshots equal the primal ones). A rejected step adds
-    no snapshot, since the centre does not move.
+    no snapshot, since the centre does not move. With prm["n_max"] set, the basis is Eq.
+    rob-optim with POD truncation instead: GramSchmidt([POD_n(U_prev), u_c]) where U_prev holds
+    the L most recent previous centres and n = min(number of previous centres - 1, n_max)
+    (n_k = min(k - 1, n_max) of Section 4.2, k previous centres).
 """
 from __future__ import annotations
 
@@ -153,7 +156,13 @@ def major_iteration(p, run: Run, prm: dict) -> dict:
     quantities of the iteration."""
     vmax = prm["volfrac"] * p.nel
     # step 2: model from the basis of the window (whose newest snapshot is the centre's)
-    Phi = rom.basis(np.stack(run.window[-prm["L"]:], axis=1))
+    if prm.get("n_max") is None:
+        Phi = rom.basis(np.stack(run.window[-prm["L"]:], axis=1))
+    else:
+        prev = run.window[:-1][-prm["L"]:]
+        n = max(0, min(len(prev) - 1, prm["n_max"]))
+        P = rom.pod(np.stack(prev, axis=1), n)[0] if n > 0 else np.zeros((p.ndof, 0))
+        Phi = rom.basis(np.column_stack([P, run.window[-1]]))
     # step 3: projected-gradient target, trial steps, the largest admissible one
     g = run.g
     t = prm["move"] / float(np.max(np.abs(g)))
@@ -181,7 +190,7 @@ def major_iteration(p, run: Run, prm: dict) -> dict:
                delta_next=delta_next, psi_x=psi_x, psi_hat=psi_hat)
     if accepted:
         run.psi, run.u, run.J, run.g = psi_hat, h["U"][:, 0], J_hat, h["dpsi"]
-        run.window = (run.window + [run.u])[-prm["L"]:]
+        run.window = (run.window + [run.u])[-(prm["L"] + (0 if prm.get("n_max") is None else 1)):]
     run.delta = delta_next
     run.iters += 1
     out["chi"] = criticality(run.psi, run.g, vmax)

@@ -612,6 +612,174 @@ topo_status reduced_solve(topo_ctx* c, int k, const double* b, double* H_work, d
   return launch_reduced_solve(c, k, b, H_work, yhat, Jk, (int*)c->d_red);
 }
 
+
+// ---------------------------------------------------------------------------------------
+// POD of a snapshot block (Section 4.2, Eq. rob-optim): the leading left singular vectors of U
+// from the eigen-decomposition of its Gram matrix U^T U (FP64) by the cyclic Jacobi method on one
+// CTA: each step rotates M/2 disjoint index pairs of the round-robin schedule at once (columns,
+// then rows, then the accumulated eigenvectors), sweeps until the off-diagonal mass is below
+// 1e-30 of the diagonal's (at most 40 sweeps).
+// ---------------------------------------------------------------------------------------
+constexpr int POD_MAX = 64;
+
+// Gram (m x m, row-major) with column `skip` left out -> coefficients coef (m x n, row-major:
+// Pod_i = sum_j coef[j][i] U_j) and the singular values sigma[0 .. m' - 1], m' = m - (skip >= 0).
+__global__ void __launch_bounds__(256) pod_jacobi_kernel(const double* __restrict__ gram, int m, int skip, int n,
+                                                        double* coef, double* sigma) {
+  extern __shared__ double sm[];
+  const int mp = m - (skip >= 0 ? 1 : 0);
+  const int M = mp + (mp & 1);  // even (a dummy index when mp is odd)
+  const int ldm = POD_MAX + 1;
+  double* G = sm;               // M x ldm
+  double* V = G + POD_MAX * ldm;  // M x ldm
+  __shared__ int idx[POD_MAX];    // local index -> column of U
+  __shared__ int pp[POD_MAX / 2], qq[POD_MAX / 2];
+  __shared__ double cs[POD_MAX / 2], sn[POD_MAX / 2];
+  __shared__ int order[POD_MAX];
+  __shared__ int done;
+  __shared__ double red[2][8];
+  if (threadIdx.x == 0) {
+    int t = 0;
+    for (int j = 0; j < m; ++j)
+      if (j != skip) idx[t++] = j;
+    done = 0;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < M * M; t += blockDim.x) {
+    const int r = t / M, c = t % M;
+    G[r * ldm + c] = (r < mp && c < mp) ? gram[idx[r] * m + idx[c]] : 0.0;
+    V[r * ldm + c] = r == c ? 1.0 : 0.0;
+  }
+  __syncthreads();
+  for (int sweep = 0; sweep < 40 && M > 1; ++sweep) {
+    for (int round = 0; round < M - 1; ++round) {
+      if (threadIdx.x < M / 2) {
+        const int i = threadIdx.x;
+        auto pos = [&](int k) { return k == 0 ? 0 : ((k - 1 + round) % (M - 1)) + 1; };
+        int p = pos(i), q = pos(M - 1 - i);
+        if (p > q) {
+          const int t = p;
+          p = q;
+          q = t;
+        }
+        pp[i] = p;
+        qq[i] = q;
+        const double apq = G[p * ldm + q], app = G[p * ldm + p], aqq = G[q * ldm + q];
+        double c = 1.0, s = 0.0;
+        if (q < mp && apq != 0.0) {
+          const double tau = (aqq - app) / (2.0 * apq);
+          const double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+          c = 1.0 / sqrt(1.0 + t * t);
+          s = t * c;
+        }
+        cs[i] = c;
+        sn[i] = s;
+      }
+      __syncthreads();
+      // columns of G and V: (x_p, x_q) <- (c x_p - s x_q, s x_p + c x_q)
+      for (int t = threadIdx.x; t < M * (M / 2); t += blockDim.x) {
+        const int r = t / (M / 2), k = t % (M / 2);
+        const int p = pp[k], q = qq[k];
+        const double c = cs[k], s = sn[k];
+        const double gp = G[r * ldm + p], gq = G[r * ldm + q];
+        G[r * ldm + p] = c * gp - s * gq;
+        G[r * ldm + q] = s * gp + c * gq;
+        const double vp = V[r * ldm + p], vq = V[r * ldm + q];
+        V[r * ldm + p] = c * vp - s * vq;
+        V[r * ldm + q] = s * vp + c * vq;
+      }
+      __syncthreads();
+      // rows of G
+      for (int t = threadIdx.x; t < M * (M / 2); t += blockDim.x) {
+        const int col = t / (M / 2), k = t % (M / 2);
+        const int p = pp[k], q = qq[k];
+        const double c = cs[k], s = sn[k];
+        const double gp = G[p * ldm + col], gq = G[q * ldm + col];
+        G[p * ldm + col] = c * gp - s * gq;
+        G[q * ldm + col] = s * gp + c * gq;
+      }
+      __syncthreads();
+    }
+    // off-diagonal and diagonal mass (fixed order)
+    double off = 0.0, dia = 0.0;
+    for (int t = threadIdx.x; t < mp * mp; t += blockDim.x) {
+      const int r = t / mp, c = t % mp;
+      const double g = G[r * ldm + c];
+      if (r == c)
+        dia += g * g;
+      else
+        off += g * g;
+    }
+    off = warp_sum(off);
+    dia = warp_sum(dia);
+    if ((threadIdx.x & 31) == 0) {
+      red[0][threadIdx.x >> 5] = off;
+      red[1][threadIdx.x >> 5] = dia;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double o = 0.0, d = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+        o += red[0][w];
+        d += red[1][w];
+      }
+      done = !(o > 1e-30 * d);
+    }
+    __syncthreads();
+    if (done) break;
+  }
+  // eigenvalues in descending order (ties by index); small ones are rounding noise of the Gram
+  // matrix (absolute error ~ eps lambda_max): their vectors are left out
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < mp; ++i) order[i] = i;
+    for (int i = 1; i < mp; ++i) {
+      const int v = order[i];
+      const double lv = G[v * ldm + v];
+      int j = i - 1;
+      while (j >= 0 && G[order[j] * ldm + order[j]] < lv) {
+        order[j + 1] = order[j];
+        --j;
+      }
+      order[j + 1] = v;
+    }
+  }
+  __syncthreads();
+  const double lmax = mp > 0 ? fmax(G[order[0] * ldm + order[0]], 0.0) : 0.0;
+  for (int i = threadIdx.x; i < mp; i += blockDim.x) sigma[i] = sqrt(fmax(G[order[i] * ldm + order[i]], 0.0));
+  for (int t = threadIdx.x; t < m * n; t += blockDim.x) {
+    const int j = t / n, i = t % n;
+    double v = 0.0;
+    if (i < mp && j != skip) {
+      const int jl = j - (skip >= 0 && j > skip ? 1 : 0);
+      const int e = order[i];
+      const double lam = G[e * ldm + e];
+      if (lam > 64.0 * 2.220446049250313e-16 * lmax) v = V[jl * ldm + e] / sqrt(lam);
+    }
+    coef[t] = v;
+  }
+}
+
+// Pod_i = sum_j coef[j][i] U_j (i < n), then Pod_n = append (when given).
+__global__ void __launch_bounds__(256) pod_combine_kernel(const double* __restrict__ U, long long ld, int m,
+                                                         const double* __restrict__ coef, int n,
+                                                         const double* __restrict__ append, double* Pod,
+                                                         long long ldp, long long N) {
+  extern __shared__ double cf[];  // m x n
+  for (int t = threadIdx.x; t < m * n; t += blockDim.x) cf[t] = coef[t];
+  __syncthreads();
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < N; r += (long long)gridDim.x * blockDim.x) {
+    double u[POD_MAX];
+#pragma unroll 8
+    for (int j = 0; j < m; ++j) u[j] = U[(long long)j * ld + r];
+    for (int i = 0; i < n; ++i) {
+      double acc = 0.0;
+      for (int j = 0; j < m; ++j) acc = fma(cf[j * n + i], u[j], acc);
+      Pod[(long long)i * ldp + r] = acc;
+    }
+    if (append) Pod[(long long)n * ldp + r] = append[r];
+  }
+}
+
 }  // namespace topo
 
 using namespace topo;
@@ -785,4 +953,41 @@ extern "C" topo_status topo_rom_error(topo_ctx* c, const double* rho, const doub
   note_launch();
   TOPO_CUDA_TRY(c, cudaGetLastError());
   return launch_residual64(c, rho, uk, f, nullptr, resnorm);
+}
+
+extern "C" topo_status topo_rom_pod(topo_ctx* c, const double* U, int m, int ld, int skip, int n,
+                                    const double* append, double* Pod, int ldp, double* sigma) {
+  if (!c) return TOPO_ERR_INVALID;
+  const long long N = c->g.ndof;
+  const int mp = m - (skip >= 0 ? 1 : 0);
+  if (m < 1 || m > POD_MAX) return fail(c, TOPO_ERR_INVALID, "topo_rom_pod: 1 <= m <= 64");
+  if (skip < -1 || skip >= m) return fail(c, TOPO_ERR_INVALID, "topo_rom_pod: skip must be -1 or a column index");
+  if (n < 0 || n > mp) return fail(c, TOPO_ERR_INVALID, "topo_rom_pod: 0 <= n <= the columns kept");
+  if ((long long)ld < N || (long long)ldp < N) return fail(c, TOPO_ERR_INVALID, "topo_rom_pod: ld and ldp >= N");
+  if (!dev_ptr_ok(U) || !dev_ptr_ok(Pod) || !dev_ptr_ok(sigma) || (append && !dev_ptr_ok(append)))
+    return fail(c, TOPO_ERR_INVALID, "topo_rom_pod: null or misaligned pointer");
+  if (n == 0 && !append) return TOPO_OK;
+  RowSplit rs = row_split(c, N, 2);
+  const size_t pcap = (size_t)rs.G * m * m;
+  const size_t gbytes = ((size_t)m * m * sizeof(double) + 255) & ~(size_t)255;
+  const size_t cbytes = ((size_t)m * std::max(n, 1) * sizeof(double) + 255) & ~(size_t)255;
+  topo_status s = ensure_scratch(c, pcap * sizeof(double) + gbytes + cbytes + 256);
+  if (s) return s;
+  double* partial = (double*)c->d_scratch;
+  double* gram = (double*)((char*)c->d_scratch + pcap * sizeof(double));
+  double* coef = (double*)((char*)gram + gbytes);
+  if (n > 0) {
+    s = launch_atb<double>(c, U, ld, m, U, ld, m, N, partial, pcap, gram, 1);
+    if (s) return s;
+    const int smem = 2 * POD_MAX * (POD_MAX + 1) * (int)sizeof(double);
+    TOPO_CUDA_TRY(c, cudaFuncSetAttribute(pod_jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    pod_jacobi_kernel<<<1, 256, smem, c->stream>>>(gram, m, skip, n, coef, sigma);
+    note_launch();
+  }
+  const long long blocks = std::min<long long>(4LL * c->num_sms, (N + 255) / 256);
+  pod_combine_kernel<<<(int)blocks, 256, (size_t)m * std::max(n, 1) * sizeof(double), c->stream>>>(
+      U, ld, m, coef, n, append, Pod, ldp, N);
+  note_launch();
+  TOPO_CUDA_TRY(c, cudaGetLastError());
+  return TOPO_OK;
 }

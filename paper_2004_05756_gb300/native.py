@@ -33,7 +33,7 @@ EXPORTS = ["topo_create", "topo_destroy", "topo_last_error", "topo_set_param", "
            "topo_batch_destroy",
            "topo_batch_last_error", "topo_batch_context", "topo_batch_solve_hdm", "topo_batch_filter",
            "topo_batch_compliance_grad", "topo_batch_rom_solve_elem", "topo_tr_init", "topo_tr_project",
-           "topo_tr_trials", "topo_tr_select", "topo_tr_update"]
+           "topo_tr_trials", "topo_tr_select", "topo_tr_update", "topo_rom_pod"]
 
 
 class TopoError(RuntimeError):
@@ -109,6 +109,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "topo_batch_compliance_grad": ([P, P, P, P, P, P, P, P, P], I),
         "topo_batch_rom_solve_elem": ([P, P, P, P, P, P, P, P], I),
         "topo_tr_init": ([P, P, P, D, D, P], I),
+        "topo_rom_pod": ([P, P, I, I, I, I, P, P, I, P], I),
         "topo_tr_project": ([P, P, P, D, I, D, P, P], I),
         "topo_tr_trials": ([P, I, P, P, P, I], I),
         "topo_tr_select": ([P, P, ctypes.POINTER(topo_tr_params), I, P, P, P, P, I, P, I, I, P, P, P], I),
@@ -235,6 +236,13 @@ class Topo:
         ld = _ld(Phi, self.N)
         self._chk(self.lib.topo_rom_solve(self.h, _ptr(rho), _ptr(Phi), int(k), ld, _ptr(b), _ptr(H_work),
                                           _ptr(yhat), _ptr(Jk), PREC[prec]), "topo_rom_solve")
+
+    def topo_rom_pod(self, U, n: int, Pod, sigma, skip: int = -1, append=None):
+        """U: (m, ld) snapshot block; Pod: (n + (append is not None), ldp)."""
+        m, ld = _cols(U, self.N)
+        _, ldp = _cols(Pod, self.N)
+        self._chk(self.lib.topo_rom_pod(self.h, _ptr(U), m, ld, int(skip), int(n), _ptr(append), _ptr(Pod), ldp,
+                                        _ptr(sigma)), "topo_rom_pod")
 
     def topo_rom_elem(self, Phi, k: int, Hel):
         ld = _ld(Phi, self.N)

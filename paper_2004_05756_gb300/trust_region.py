@@ -32,12 +32,16 @@ class TrustRegionRun:
 
     def __init__(self, T, p, psi0, *, tau: float = 0.1, dmax_factor: float = 100.0, move: float = 0.2,
                  trials: int = 7, volfrac: float = 0.5, L: int = 8, rtol: float = 1e-8, maxit: int = 400000,
-                 params: native.topo_tr_params | None = None, alloc_stream=None):
+                 params: native.topo_tr_params | None = None, alloc_stream=None, pod_nmax: int | None = None):
         import torch
         self.torch = torch
         self.alloc_stream = alloc_stream  # allocate the buffers on this stream's pool (None: current)
         self.T, self.p = T, p
         self.move, self.R, self.L = float(move), int(trials) + 1, int(L)
+        # POD truncation (Eq. rob-optim): basis = GramSchmidt([POD_n(previous centres), u_c]) with
+        # n = min(previous - 1, pod_nmax); the ring then holds L previous centres and the current
+        self.pod_nmax = pod_nmax
+        self.ring = self.L + (1 if pod_nmax is not None else 0)
         self.vmax = float(volfrac) * p.nel
         self.rtol, self.maxit = float(rtol), int(maxit)
         self.prm = params if params is not None else native.tr_params()
@@ -64,7 +68,7 @@ class TrustRegionRun:
     def _alloc(self):
         torch, p = self.torch, self.p
         f64 = dict(dtype=torch.float64, device="cuda")
-        ne, N, R, L = p.nel, p.ndof, self.R, self.L
+        ne, N, R, L = p.nel, p.ndof, self.R, self.ring
         self.F = torch.as_tensor(np.ascontiguousarray(p.F[:, :1].T)).to(**f64)
         self.f = self.F[0]
         self.psi_c = torch.empty(ne, **f64)
@@ -90,6 +94,9 @@ class TrustRegionRun:
         self.st = self.out[:native.TR_STATE_BYTES // 8]
         self.stats_dir = self.out[16:20]
         self.stats_crit = self.out[20:24]
+        if self.pod_nmax is not None:
+            self.pbuf = torch.zeros((L, N), **f64)   # the POD vectors followed by u_c
+            self.sigma = torch.zeros(L, **f64)
 
     def free(self):
         """Drop every device buffer (after the carried ones were copied out)."""
@@ -121,8 +128,14 @@ class TrustRegionRun:
     def iterate(self) -> dict:
         """One major iteration; returns the state after it with the iteration's quantities."""
         T = self.T
-        m = min(self.nwin, self.L)
-        k = T.topo_rom_build(self.rho, self.window[:m], self.Phi, None, self.b, self.f)
+        m = min(self.nwin, self.ring)
+        if self.pod_nmax is None:
+            k = T.topo_rom_build(self.rho, self.window[:m], self.Phi, None, self.b, self.f)
+        else:
+            cur = (self.nwin - 1) % self.ring
+            n = max(0, min(m - 2, self.pod_nmax))
+            T.topo_rom_pod(self.window[:m], n, self.pbuf[:n + 1], self.sigma, skip=cur, append=self.window[cur])
+            k = T.topo_rom_build(self.rho, self.pbuf[:n + 1], self.Phi, None, self.b, self.f)
         T.topo_rom_elem(self.Phi[:k], k, self.Hel)
         T.topo_tr_project(self.psi_c, self.g_c, self.move, True, self.vmax, self.psi_x, self.stats_dir)
         T.topo_tr_trials(self.psi_c, self.psi_x, self.trials)
@@ -135,7 +148,7 @@ class TrustRegionRun:
         info = T.topo_solve_hdm(self.rho, self.F, self.u_hat, rtol=self.rtol, maxit=self.maxit, prec="fp64")
         T.topo_compliance_grad(self.rho, self.u_hat, self.F, self.J, self.dc, self.g_hat)
         # the centre's state is the newest window column; an accepted candidate's goes to the next slot
-        slot = self.window[self.nwin % self.L]
+        slot = self.window[self.nwin % self.ring]
         T.topo_tr_update(self.st, self.prm, self.J, self.psi_c, self.psi_hat, slot, self.u_hat[0], self.g_c,
                          self.g_hat, None)
         T.topo_tr_project(self.psi_c, self.g_c, 1.0, False, self.vmax, self.scratch, self.stats_crit)

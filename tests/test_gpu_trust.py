@@ -265,7 +265,8 @@ def test_parameter_validation(torch):
         T.topo_tr_init(st, th.zeros(p.ndof, dtype=th.float64, device="cuda"), 0.0, 100.0, one)
 
 
-RUNS = [("q4", (48, 16), 3, 6), ("h8", (8, 6, 4), 5, 4)]
+RUNS = [("q4", (48, 16), 3, 6, None), ("h8", (8, 6, 4), 5, 4, None), ("q4_pod", (48, 16), 3, 7, 2),
+        ("h8_pod", (8, 6, 4), 5, 6, 2)]
 
 
 def _margins(o, prm):
@@ -285,13 +286,14 @@ def _margins(o, prm):
 def test_run_replays_oracle(torch, run):
     """Every major iteration of a run on the device against the oracle's, from the same start."""
     from paper_2004_05756_gb300.trust_region import TrustRegionRun
-    kind, shape, seed, iters = run
-    p = w.build_problem(2 if kind == "q4" else 3, shape)
+    kind, shape, seed, iters, n_max = run
+    p = w.build_problem(2 if kind.startswith("q4") else 3, shape)
     psi0 = w.design_field(p, seed)
-    prm = trust.default_params(L=4)
+    L = 4 if n_max is None else 3
+    prm = trust.default_params(L=L, n_max=n_max)
     orc = trust.start(p, psi0, prm)
     T = _ctx(p)
-    gpu = TrustRegionRun(T, p, psi0, L=4, rtol=1e-13)
+    gpu = TrustRegionRun(T, p, psi0, L=L, rtol=1e-13, pod_nmax=n_max)
     s0 = gpu.state()
     assert s0["J_c"] == pytest.approx(orc.J, rel=1e-10)
     assert s0["delta"] == pytest.approx(orc.delta, rel=1e-14)

@@ -86,3 +86,26 @@ def test_cholesky_solve_matches_library():
     H = A @ A.T + 8 * np.eye(8)
     b = rng.standard_normal(8)
     assert np.abs(rom.solve_reduced(H, b) - np.linalg.solve(H, b)).max() < 1e-13
+
+
+def test_pod_pins():
+    """POD_n (Section 4.2): orthonormal vectors, singular values equal to the square roots of the
+    Gram matrix's eigenvalues (an independent route), the Eckart-Young projection error, a rank-one
+    closed form and optimality against random subspaces."""
+    rng = np.random.default_rng(9)
+    U = rng.normal(size=(200, 7)) @ np.diag([10, 5, 3, 1, 0.5, 0.1, 0.01]) @ rng.normal(size=(7, 7))
+    for n in range(0, 8):
+        P, s = rom.pod(U, n)
+        assert P.shape == (200, n)
+        assert np.allclose(P.T @ P, np.eye(n), atol=1e-12)
+        err = np.linalg.norm(U - P @ (P.T @ U)) ** 2
+        assert err == pytest.approx(np.sum(s[n:] ** 2), rel=1e-9, abs=1e-20)
+        for _ in range(5):
+            Q, _ = np.linalg.qr(rng.normal(size=(200, n)))
+            assert np.linalg.norm(U - Q @ (Q.T @ U)) ** 2 >= err * (1 - 1e-12)
+    _, s = rom.pod(U, 3)
+    assert np.allclose(np.sort(s ** 2), np.sort(np.linalg.eigvalsh(U.T @ U)), rtol=1e-9)
+    a, b = rng.normal(size=50), rng.normal(size=4)
+    P1, s1 = rom.pod(np.outer(a, b), 1)
+    assert s1[0] == pytest.approx(np.linalg.norm(a) * np.linalg.norm(b), rel=1e-13)
+    assert abs(abs(P1[:, 0] @ a) / np.linalg.norm(a) - 1) < 1e-13
