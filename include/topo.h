@@ -298,6 +298,20 @@ topo_status topo_rom_error(topo_ctx* ctx, const double* rho, const double* Phi, 
 topo_status topo_compliance_grad(topo_ctx* ctx, const double* rho, const double* U, int m, int ld,
                                  const double* F, double* J, double* dc_rho, double* dc_psi);
 
+/* General linear output j(u) = sum_c l_c^T u_c (Section 2.3-2.4; Eq. pap_sensitivity with
+ * dj/drho = 0): J = sum_c l_c^T u_c (device scalar), dc_rho_e = -p (E0 - Emin) rho_e^(p-1)
+ * sum_c lambda_{c,e}^T K_e u_{c,e} with the adjoint states Lam (K lambda_c = l_c, Eq.
+ * linelast-adj1: topo_solve_hdm with the output vectors as loads, K being symmetric), and, when
+ * dc_psi is not NULL, its filter adjoint. U, Lam, L: FP64 N x m at ld; Dirichlet rows of Lam
+ * are ignored. With Lam = U and L = F this is topo_compliance_grad. Works for full-order states
+ * and for ROM reconstructions u_k = Phi y, lambda_k = Phi z (Section 3.2) alike. */
+topo_status topo_output_grad(topo_ctx* ctx, const double* rho, const double* U, const double* Lam, int m, int ld,
+                             const double* L, double* J, double* dc_rho, double* dc_psi);
+
+/* Reduced load of a vector (Section 3.1 Eq. hatkbm's f_k = Phi^T f; Section 3.2's adjoint load
+ * Phi^T dj/du^T): out = Phi^T v (device FP64[k]); Phi N x k at ld, v FP64[N]. 1 <= k <= 128. */
+topo_status topo_rom_rhs(topo_ctx* ctx, const double* Phi, int k, int ld, const double* v, double* out);
+
 /* ---------------------------------------------------------------------------------------
  * Trust-region step of one major iteration of the error-aware trust-region method
  * (Algorithm 2, Section 4.2; Algorithm 1 for the acceptance and radius rule) for compliance.

@@ -200,6 +200,7 @@ struct GradArgs {
   int m;
   double* dc;
   long long ldr, ldu, ldd;  // strides of rho, U and dc between the designs of blockIdx.y
+  const double* Lam;        // adjoint states (N x m at ld) for a general output; null: compliance
 };
 
 template <int DIM>
@@ -228,6 +229,18 @@ __global__ void grad_kernel(const __grid_constant__ GradArgs<DIM> a) {
       double ue[ND];
 #pragma unroll
       for (int d = 0; d < ND; ++d) ue[d] = is_fixed(g, dofs[d]) ? 0.0 : u[dofs[d]];
+      if (a.Lam) {  // a general output: the mixed form lambda_e^T K_e u_e
+        const double* lam = a.Lam + (long long)col * a.ld;
+#pragma unroll(DIM == 2 ? ND : 1)
+        for (int r2 = 0; r2 < ND; ++r2) {
+          if (is_fixed(g, dofs[r2])) continue;
+          double t = 0.0;
+#pragma unroll
+          for (int c2 = 0; c2 < ND; ++c2) t = fma(a.ke.k[r2 * ND + c2], ue[c2], t);
+          ce = fma(lam[dofs[r2]], t, ce);
+        }
+        continue;
+      }
       // u_e^T K_e u_e in the symmetric form: row r2 sums K_e's entries right of the diagonal,
       // doubles that (exactly) and adds the diagonal term, ND (ND + 1) / 2 products instead of ND^2
 #pragma unroll(DIM == 2 ? ND : 1)
@@ -346,6 +359,7 @@ topo_status launch_grad_batch(topo_ctx* c, const double* rho, long long ldr, con
     a.ldr = ldr;
     a.ldu = ldu;
     a.ldd = ldd;
+    a.Lam = nullptr;
     grad_kernel<2><<<grid, 128, 0, c->stream>>>(a);
   } else {
     GradArgs<3> a;
@@ -359,6 +373,7 @@ topo_status launch_grad_batch(topo_ctx* c, const double* rho, long long ldr, con
     a.ldr = ldr;
     a.ldu = ldu;
     a.ldd = ldd;
+    a.Lam = nullptr;
     grad_kernel<3><<<grid, 128, 0, c->stream>>>(a);
   }
   note_launch();
@@ -652,19 +667,21 @@ extern "C" topo_status topo_filter(topo_ctx* c, const double* in, double* out, i
   return filter_launch(c, in, out, adjoint ? 2 : 1);
 }
 
-extern "C" topo_status topo_compliance_grad(topo_ctx* c, const double* rho, const double* U, int m, int ld,
-                                            const double* F, double* J, double* dc_rho, double* dc_psi) {
-  if (!c) return TOPO_ERR_INVALID;
+// J = sum_c l_c^T u_c, dc_rho_e = -E'(rho_e) sum_c w_{c,e}^T K_e u_{c,e} with w = Lam (a general
+// output) or w = u (compliance, Lam null), and the filter adjoint of dc_rho.
+static topo_status output_grad_impl(topo_ctx* c, const double* rho, const double* U, const double* Lam, int m,
+                                    int ld, const double* L, double* J, double* dc_rho, double* dc_psi,
+                                    const char* what) {
   const Grid& g = c->g;
-  if (m < 1 || (long long)ld < g.ndof) return fail(c, TOPO_ERR_INVALID, "compliance_grad: m >= 1 and ld >= N required");
-  if (!dev_ptr_ok(rho) || !dev_ptr_ok(U) || !dev_ptr_ok(F) || !dev_ptr_ok(J) || !dev_ptr_ok(dc_rho) ||
-      (dc_psi && !dev_ptr_ok(dc_psi)))
-    return fail(c, TOPO_ERR_INVALID, "compliance_grad: null or misaligned pointer");
-  // J = sum_c f_c^T u_c (fixed order)
+  if (m < 1 || (long long)ld < g.ndof) return fail(c, TOPO_ERR_INVALID, "%s: m >= 1 and ld >= N required", what);
+  if (!dev_ptr_ok(rho) || !dev_ptr_ok(U) || !dev_ptr_ok(L) || !dev_ptr_ok(J) || !dev_ptr_ok(dc_rho) ||
+      (dc_psi && !dev_ptr_ok(dc_psi)) || (Lam && !dev_ptr_ok(Lam)))
+    return fail(c, TOPO_ERR_INVALID, "%s: null or misaligned pointer", what);
+  // J = sum_c l_c^T u_c (fixed order)
   int G = red_blocks(c, g.ndof);
   topo_status s = ensure_red(c, sizeof(double) * (size_t)(G * m + 64));
   if (s) return s;
-  dot_cols_partial_kernel<<<dim3(G, m), 256, 0, c->stream>>>(F, U, g.ndof, ld, m, c->d_red);
+  dot_cols_partial_kernel<<<dim3(G, m), 256, 0, c->stream>>>(L, U, g.ndof, ld, m, c->d_red);
   note_launch();
   sum_final_kernel<<<1, 256, 0, c->stream>>>(c->d_red, G * m, J, 0);
   note_launch();
@@ -680,6 +697,7 @@ extern "C" topo_status topo_compliance_grad(topo_ctx* c, const double* rho, cons
     a.m = m;
     a.dc = dc_rho;
     a.ldr = a.ldu = a.ldd = 0;
+    a.Lam = Lam;
     grad_kernel<2><<<(int)blocks, 128, 0, c->stream>>>(a);
     note_launch();
   } else {
@@ -692,6 +710,7 @@ extern "C" topo_status topo_compliance_grad(topo_ctx* c, const double* rho, cons
     a.m = m;
     a.dc = dc_rho;
     a.ldr = a.ldu = a.ldd = 0;
+    a.Lam = Lam;
     grad_kernel<3><<<(int)blocks, 128, 0, c->stream>>>(a);
     note_launch();
   }
@@ -700,6 +719,18 @@ extern "C" topo_status topo_compliance_grad(topo_ctx* c, const double* rho, cons
   return TOPO_OK;
 }
 
+extern "C" topo_status topo_compliance_grad(topo_ctx* c, const double* rho, const double* U, int m, int ld,
+                                            const double* F, double* J, double* dc_rho, double* dc_psi) {
+  if (!c) return TOPO_ERR_INVALID;
+  return output_grad_impl(c, rho, U, nullptr, m, ld, F, J, dc_rho, dc_psi, "compliance_grad");
+}
+
+extern "C" topo_status topo_output_grad(topo_ctx* c, const double* rho, const double* U, const double* Lam, int m,
+                                        int ld, const double* L, double* J, double* dc_rho, double* dc_psi) {
+  if (!c) return TOPO_ERR_INVALID;
+  if (!Lam) return fail(c, TOPO_ERR_INVALID, "topo_output_grad: null adjoint states");
+  return output_grad_impl(c, rho, U, Lam, m, ld, L, J, dc_rho, dc_psi, "topo_output_grad");
+}
 
 extern "C" topo_status topo_launch_count(long long* out) {
   if (!out) return TOPO_ERR_INVALID;

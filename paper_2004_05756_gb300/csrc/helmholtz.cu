@@ -29,57 +29,65 @@ constexpr int GB_M = 64, GB_N = 64, GB_K = 16;
 constexpr double kPi = 3.141592653589793238462643383279502884;
 
 // C[b] = A[b] B[b] (row-major, leading dimensions lda, ldb, ldc; batch strides sA, sB, sC;
-// a stride of 0 shares the operand). Tile 64 x 64, 256 threads, 16 outputs each (rows ty + 16i,
-// columns tx + 16j: conflict-free shared-memory reads and coalesced stores).
+// a stride of 0 shares the operand). Tile TM x TN (64 x 64, or 32 x 32 when the big tiles would
+// leave SMs idle: FP64 FMA issue is the bound, so every SM should hold a tile), 256 threads as a
+// 16 x 16 grid, each with (TM / 16) x (TN / 16) outputs at rows ty + 16i and columns tx + 16j
+// (conflict-free shared-memory reads, coalesced stores).
+template <int TM, int TN>
 __global__ void __launch_bounds__(256) helm_gemm_kernel(int M, int N, int K, const double* __restrict__ A,
                                                         long long lda, long long sA, const double* __restrict__ B,
                                                         long long ldb, long long sB, double* __restrict__ C,
                                                         long long ldc, long long sC) {
-  __shared__ double As[GB_K][GB_M + 1];
-  __shared__ double Bs[GB_K][GB_N + 1];
+  constexpr int RI = TM / 16, RJ = TN / 16;
+  __shared__ double As[GB_K][TM + 1];
+  __shared__ double Bs[GB_K][TN + 1];
   const long long bz = blockIdx.z;
   A += bz * sA;
   B += bz * sB;
   C += bz * sC;
-  const int m0 = blockIdx.y * GB_M, n0 = blockIdx.x * GB_N;
+  const int m0 = blockIdx.y * TM, n0 = blockIdx.x * TN;
   const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  double acc[4][4];
+  double acc[RI][RJ];
 #pragma unroll
-  for (int i = 0; i < 4; ++i)
+  for (int i = 0; i < RI; ++i)
 #pragma unroll
-    for (int j = 0; j < 4; ++j) acc[i][j] = 0.0;
+    for (int j = 0; j < RJ; ++j) acc[i][j] = 0.0;
   for (int k0 = 0; k0 < K; k0 += GB_K) {
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < (TM * GB_K) / 256; ++q) {
       const int t = threadIdx.x + 256 * q;
-      const int r = t >> 4, kk = t & 15;
+      const int r = t / GB_K, kk = t % GB_K;
       const int gr = m0 + r, gk = k0 + kk;
       As[kk][r] = (gr < M && gk < K) ? A[(long long)gr * lda + gk] : 0.0;
-      const int kb = t >> 6, cb = t & 63;
+    }
+#pragma unroll
+    for (int q = 0; q < (TN * GB_K) / 256; ++q) {
+      const int t = threadIdx.x + 256 * q;
+      const int kb = t / TN, cb = t % TN;
       const int gkb = k0 + kb, gc = n0 + cb;
       Bs[kb][cb] = (gkb < K && gc < N) ? B[(long long)gkb * ldb + gc] : 0.0;
     }
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < GB_K; ++kk) {
-      double a[4], b[4];
+      double a[RI], b[RJ];
 #pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+      for (int i = 0; i < RI; ++i) a[i] = As[kk][ty + 16 * i];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+      for (int j = 0; j < RJ; ++j) b[j] = Bs[kk][tx + 16 * j];
 #pragma unroll
-      for (int i = 0; i < 4; ++i)
+      for (int i = 0; i < RI; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
+        for (int j = 0; j < RJ; ++j) acc[i][j] = fma(a[i], b[j], acc[i][j]);
     }
     __syncthreads();
   }
 #pragma unroll
-  for (int i = 0; i < 4; ++i) {
+  for (int i = 0; i < RI; ++i) {
     const int gr = m0 + ty + 16 * i;
     if (gr >= M) continue;
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
+    for (int j = 0; j < RJ; ++j) {
       const int gc = n0 + tx + 16 * j;
       if (gc < N) C[(long long)gr * ldc + gc] = acc[i][j];
     }
@@ -181,8 +189,14 @@ static long long grid_cap(topo_ctx* c, long long n) {
 
 static topo_status gemm(topo_ctx* c, int M, int N, int K, const double* A, long long lda, long long sA, const double* B,
                         long long ldb, long long sB, double* C, long long ldc, long long sC, int batch) {
-  const dim3 grid((unsigned)((N + GB_N - 1) / GB_N), (unsigned)((M + GB_M - 1) / GB_M), (unsigned)batch);
-  helm_gemm_kernel<<<grid, 256, 0, c->stream>>>(M, N, K, A, lda, sA, B, ldb, sB, C, ldc, sC);
+  const long long big = (long long)((N + GB_N - 1) / GB_N) * ((M + GB_M - 1) / GB_M) * batch;
+  if (big >= c->num_sms) {
+    const dim3 grid((unsigned)((N + GB_N - 1) / GB_N), (unsigned)((M + GB_M - 1) / GB_M), (unsigned)batch);
+    helm_gemm_kernel<GB_M, GB_N><<<grid, 256, 0, c->stream>>>(M, N, K, A, lda, sA, B, ldb, sB, C, ldc, sC);
+  } else {
+    const dim3 grid((unsigned)((N + 31) / 32), (unsigned)((M + 31) / 32), (unsigned)batch);
+    helm_gemm_kernel<32, 32><<<grid, 256, 0, c->stream>>>(M, N, K, A, lda, sA, B, ldb, sB, C, ldc, sC);
+  }
   note_launch();
   TOPO_CUDA_TRY(c, cudaGetLastError());
   return TOPO_OK;

@@ -991,3 +991,16 @@ extern "C" topo_status topo_rom_pod(topo_ctx* c, const double* U, int m, int ld,
   TOPO_CUDA_TRY(c, cudaGetLastError());
   return TOPO_OK;
 }
+
+extern "C" topo_status topo_rom_rhs(topo_ctx* c, const double* Phi, int k, int ld, const double* v, double* out) {
+  if (!c) return TOPO_ERR_INVALID;
+  const long long N = c->g.ndof;
+  if (k < 1 || k > 128) return fail(c, TOPO_ERR_INVALID, "topo_rom_rhs: 1 <= k <= 128");
+  if ((long long)ld < N) return fail(c, TOPO_ERR_INVALID, "topo_rom_rhs: ld < N");
+  if (!dev_ptr_ok(Phi) || !dev_ptr_ok(v) || !dev_ptr_ok(out))
+    return fail(c, TOPO_ERR_INVALID, "topo_rom_rhs: null or misaligned pointer");
+  const size_t pcap = partial_capacity(c, N, k);
+  topo_status s = ensure_scratch(c, pcap * sizeof(double) + 256);
+  if (s) return s;
+  return launch_atv(c, Phi, ld, k, v, N, (double*)c->d_scratch, pcap, out, nullptr);
+}

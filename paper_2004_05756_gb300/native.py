@@ -33,7 +33,8 @@ EXPORTS = ["topo_create", "topo_destroy", "topo_last_error", "topo_set_param", "
            "topo_batch_destroy",
            "topo_batch_last_error", "topo_batch_context", "topo_batch_solve_hdm", "topo_batch_filter",
            "topo_batch_compliance_grad", "topo_batch_rom_solve_elem", "topo_tr_init", "topo_tr_project",
-           "topo_tr_trials", "topo_tr_select", "topo_tr_update", "topo_rom_pod"]
+           "topo_tr_trials", "topo_tr_select", "topo_tr_update", "topo_rom_pod", "topo_output_grad",
+           "topo_rom_rhs"]
 
 
 class TopoError(RuntimeError):
@@ -110,6 +111,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "topo_batch_rom_solve_elem": ([P, P, P, P, P, P, P, P], I),
         "topo_tr_init": ([P, P, P, D, D, P], I),
         "topo_rom_pod": ([P, P, I, I, I, I, P, P, I, P], I),
+        "topo_output_grad": ([P, P, P, P, I, I, P, P, P, P], I),
+        "topo_rom_rhs": ([P, P, I, I, P, P], I),
         "topo_tr_project": ([P, P, P, D, I, D, P, P], I),
         "topo_tr_trials": ([P, I, P, P, P, I], I),
         "topo_tr_select": ([P, P, ctypes.POINTER(topo_tr_params), I, P, P, P, P, I, P, I, I, P, P, P], I),
@@ -279,6 +282,19 @@ class Topo:
         m, ld = _cols(U, self.N)
         self._chk(self.lib.topo_compliance_grad(self.h, _ptr(rho), _ptr(U), m, ld, _ptr(F), _ptr(J),
                                                 _ptr(dc_rho), _ptr(dc_psi)), "topo_compliance_grad")
+
+    def topo_output_grad(self, rho, U, Lam, L, J, dc_rho, dc_psi=None):
+        m, ld = _cols(U, self.N)
+        m2, ld2 = _cols(Lam, self.N)
+        m3, ld3 = _cols(L, self.N)
+        if (m2, ld2) != (m, ld) or (m3, ld3) != (m, ld):
+            raise ValueError("U, Lam and L must share their shape and leading dimension")
+        self._chk(self.lib.topo_output_grad(self.h, _ptr(rho), _ptr(U), _ptr(Lam), m, ld, _ptr(L), _ptr(J),
+                                            _ptr(dc_rho), _ptr(dc_psi)), "topo_output_grad")
+
+    def topo_rom_rhs(self, Phi, k: int, v, out):
+        self._chk(self.lib.topo_rom_rhs(self.h, _ptr(Phi), int(k), _ld(Phi, self.N), _ptr(v), _ptr(out)),
+                  "topo_rom_rhs")
 
     # -- trust-region step (Algorithm 2) ----------------------------------------------------
     def topo_tr_init(self, st, f, tau: float, dmax_factor: float, J_c):
