@@ -308,6 +308,18 @@ topo_status topo_compliance_grad(topo_ctx* ctx, const double* rho, const double*
 topo_status topo_output_grad(topo_ctx* ctx, const double* rho, const double* U, const double* Lam, int m, int ld,
                              const double* L, double* J, double* dc_rho, double* dc_psi);
 
+/* sigma_min(K(rho)) over the free DOFs, the constant of the a posteriori bounds of Section 3.3
+ * (Theorem rom_primal_error: ||u - u_k||_K <= sigma_min^-1/2 ||r||; for compliance
+ * |J - J_k| <= sigma_min^-1 ||r||^2), by shift-invert Lanczos: steps Lanczos steps on K^-1 (each one
+ * topo_solve_hdm at rtol, FP64, from a start vector that is zero on Dirichlet DOFs, with full
+ * CGS2 reorthogonalisation), then the largest eigenvalue theta of the tridiagonal matrix and its
+ * Ritz residual res = beta_m |s_m|. out (device FP64[4]): 1 / theta (the estimate; never below
+ * sigma_min in exact arithmetic), 1 / (theta + res) (below sigma_min when the Ritz value belongs
+ * to K^-1's largest eigenvalue: the lower bound to use in the error bounds), theta, res.
+ * 2 <= steps <= 64, 0 < rtol <= 1e-2. Allocates its Lanczos vectors ((steps + 1) N doubles) and
+ * synchronises the stream; a solve that does not converge returns TOPO_ERR_NOT_CONVERGED. */
+topo_status topo_sigma_min(topo_ctx* ctx, const double* rho, int steps, double rtol, double* out);
+
 /* Reduced load of a vector (Section 3.1 Eq. hatkbm's f_k = Phi^T f; Section 3.2's adjoint load
  * Phi^T dj/du^T): out = Phi^T v (device FP64[k]); Phi N x k at ld, v FP64[N]. 1 <= k <= 128. */
 topo_status topo_rom_rhs(topo_ctx* ctx, const double* Phi, int k, int ld, const double* v, double* out);

@@ -1004,3 +1004,121 @@ extern "C" topo_status topo_rom_rhs(topo_ctx* c, const double* Phi, int k, int l
   if (s) return s;
   return launch_atv(c, Phi, ld, k, v, N, (double*)c->d_scratch, pcap, out, nullptr);
 }
+
+// ---------------------------------------------------------------------------------------
+// sigma_min(K(rho)) by shift-invert Lanczos (Lanczos on K^-1, each step a topo_solve_hdm),
+// for the a posteriori bounds of Section 3.3 (Theorem rom_primal_error, rom_output_error).
+// ---------------------------------------------------------------------------------------
+namespace topo {
+
+// A start vector with no component on Dirichlet DOFs (the Krylov space then stays on the free
+// DOFs, where K is the paper's eliminated K_ff) and a deterministic spread elsewhere.
+__global__ void lanczos_start_kernel(Grid g, double* v) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < g.ndof; i += (long long)gridDim.x * blockDim.x)
+    v[i] = is_fixed(g, i) ? 0.0 : 1.0 + (double)(((unsigned long long)i * 2654435761ull) % 1024ull) / 1024.0;
+}
+
+__global__ void lanczos_alpha_kernel(const double* h1, const double* h2, int j, double* alpha) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) alpha[j] = h1[j] + h2[j];
+}
+
+__global__ void lanczos_tri_kernel(const double* alpha, const double* beta, int m, double* T) {
+  for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
+    const int r = t / m, c = t % m;
+    T[t] = r == c ? alpha[r] : (c == r + 1 ? beta[r] : (r == c + 1 ? beta[c] : 0.0));
+  }
+}
+
+// out = [1 / theta, 1 / (theta + beta_m |s_m|), theta, beta_m |s_m|] from the top Ritz pair of T
+// (sigma[0]^2 = theta, coef[m - 1] sigma[0] = the last component of its unit eigenvector).
+__global__ void lanczos_final_kernel(const double* sigma, const double* coef, const double* beta, int m, double* out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const double theta = sigma[0] * sigma[0];
+  const double res = beta[m - 1] * fabs(coef[m - 1] * sigma[0]);
+  out[0] = 1.0 / theta;
+  out[1] = 1.0 / (theta + res);
+  out[2] = theta;
+  out[3] = res;
+}
+
+}  // namespace topo
+
+extern "C" topo_status topo_sigma_min(topo_ctx* c, const double* rho, int steps, double rtol, double* out) {
+  if (!c) return TOPO_ERR_INVALID;
+  if (steps < 2 || steps > POD_MAX) return fail(c, TOPO_ERR_INVALID, "topo_sigma_min: 2 <= steps <= 64");
+  if (!(rtol > 0.0 && rtol <= 1e-2)) return fail(c, TOPO_ERR_INVALID, "topo_sigma_min: 0 < rtol <= 1e-2");
+  if (!dev_ptr_ok(rho) || !dev_ptr_ok(out)) return fail(c, TOPO_ERR_INVALID, "topo_sigma_min: null or misaligned pointer");
+  const long long N = c->g.ndof;
+  const size_t pcap = partial_capacity(c, N, steps + 1);
+  // one buffer of its own: the solves use the context's scratch
+  const size_t nV = (size_t)(steps + 1) * N, nsmall = 4 * (size_t)(steps + 1) + (size_t)steps * steps + 2 * steps + 8;
+  double* buf = nullptr;
+  TOPO_CUDA_TRY(c, cudaMalloc(&buf, sizeof(double) * (nV + pcap + nsmall)));
+  double* V = buf;
+  double* partial = V + nV;
+  double* h1 = partial + pcap;
+  double* h2 = h1 + (steps + 1);
+  double* alpha = h2 + (steps + 1);
+  double* beta = alpha + (steps + 1);
+  double* T = beta + (steps + 1);
+  double* coef = T + (size_t)steps * steps;
+  double* sigma = coef + steps;
+  double* nrm = sigma + steps;
+  topo_status st = TOPO_OK;
+  const int nb = stream_blocks(c, N);
+  const RowSplit rs = row_split(c, N, 4);
+  auto normalize = [&](double* x, double* into) -> topo_status {
+    nrm2_partial_kernel<<<rs.G, 256, 0, c->stream>>>(x, N, partial);
+    note_launch();
+    nrm2_final_kernel<<<1, 256, 0, c->stream>>>(partial, rs.G, into);
+    note_launch();
+    scale_kernel<<<nb, 256, 0, c->stream>>>(x, N, into);
+    note_launch();
+    TOPO_CUDA_TRY(c, cudaGetLastError());
+    return TOPO_OK;
+  };
+  lanczos_start_kernel<<<nb, 256, 0, c->stream>>>(c->g, V);
+  note_launch();
+  st = normalize(V, nrm);
+  for (int j = 0; j < steps && !st; ++j) {
+    double* vj = V + (size_t)j * N;
+    double* w = V + (size_t)(j + 1) * N;
+    if (cudaMemsetAsync(w, 0, sizeof(double) * N, c->stream) != cudaSuccess) {
+      st = fail(c, TOPO_ERR_CUDA, "topo_sigma_min: memset");
+      break;
+    }
+    topo_solve_info info;
+    st = topo_solve_hdm(c, rho, vj, w, 1, (int)N, rtol, 200000, TOPO_FP64, &info);
+    if (st) break;
+    // w -= V_j (V_j^T w), twice (CGS2); alpha_j is the sum of both passes' j-th coefficient
+    const int k = j + 1;
+    st = launch_atv(c, V, N, k, w, N, partial, pcap, h1, nullptr);
+    if (st) break;
+    gemv_kernel<<<nb, 256, k * sizeof(double), c->stream>>>(V, N, k, h1, w, N, 1, nullptr);
+    note_launch();
+    st = launch_atv(c, V, N, k, w, N, partial, pcap, h2, nullptr);
+    if (st) break;
+    gemv_kernel<<<nb, 256, k * sizeof(double), c->stream>>>(V, N, k, h2, w, N, 1, nullptr);
+    note_launch();
+    lanczos_alpha_kernel<<<1, 32, 0, c->stream>>>(h1, h2, j, alpha);
+    note_launch();
+    st = normalize(w, beta + j);
+  }
+  if (!st) {
+    lanczos_tri_kernel<<<1, 256, 0, c->stream>>>(alpha, beta, steps, T);
+    note_launch();
+    const int smem = 2 * POD_MAX * (POD_MAX + 1) * (int)sizeof(double);
+    if (cudaFuncSetAttribute(pod_jacobi_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+      st = fail(c, TOPO_ERR_CUDA, "topo_sigma_min: shared memory attribute");
+  }
+  if (!st) {
+    pod_jacobi_kernel<<<1, 256, 2 * POD_MAX * (POD_MAX + 1) * sizeof(double), c->stream>>>(T, steps, -1, 1, coef, sigma);
+    note_launch();
+    lanczos_final_kernel<<<1, 32, 0, c->stream>>>(sigma, coef, beta, steps, out);
+    note_launch();
+    if (cudaGetLastError() != cudaSuccess) st = fail(c, TOPO_ERR_CUDA, "topo_sigma_min: launch");
+  }
+  cudaStreamSynchronize(c->stream);
+  cudaFree(buf);
+  return st;
+}

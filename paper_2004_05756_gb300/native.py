@@ -34,7 +34,7 @@ EXPORTS = ["topo_create", "topo_destroy", "topo_last_error", "topo_set_param", "
            "topo_batch_last_error", "topo_batch_context", "topo_batch_solve_hdm", "topo_batch_filter",
            "topo_batch_compliance_grad", "topo_batch_rom_solve_elem", "topo_tr_init", "topo_tr_project",
            "topo_tr_trials", "topo_tr_select", "topo_tr_update", "topo_rom_pod", "topo_output_grad",
-           "topo_rom_rhs"]
+           "topo_rom_rhs", "topo_sigma_min"]
 
 
 class TopoError(RuntimeError):
@@ -113,6 +113,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "topo_rom_pod": ([P, P, I, I, I, I, P, P, I, P], I),
         "topo_output_grad": ([P, P, P, P, I, I, P, P, P, P], I),
         "topo_rom_rhs": ([P, P, I, I, P, P], I),
+        "topo_sigma_min": ([P, P, I, D, P], I),
         "topo_tr_project": ([P, P, P, D, I, D, P, P], I),
         "topo_tr_trials": ([P, I, P, P, P, I], I),
         "topo_tr_select": ([P, P, ctypes.POINTER(topo_tr_params), I, P, P, P, P, I, P, I, I, P, P, P], I),
@@ -295,6 +296,10 @@ class Topo:
     def topo_rom_rhs(self, Phi, k: int, v, out):
         self._chk(self.lib.topo_rom_rhs(self.h, _ptr(Phi), int(k), _ld(Phi, self.N), _ptr(v), _ptr(out)),
                   "topo_rom_rhs")
+
+    def topo_sigma_min(self, rho, out, steps: int = 30, rtol: float = 1e-10):
+        """out (device FP64[4]): estimate, lower bound, theta, Ritz residual."""
+        self._chk(self.lib.topo_sigma_min(self.h, _ptr(rho), int(steps), float(rtol), _ptr(out)), "topo_sigma_min")
 
     # -- trust-region step (Algorithm 2) ----------------------------------------------------
     def topo_tr_init(self, st, f, tau: float, dmax_factor: float, J_c):

@@ -109,3 +109,15 @@ def test_pod_pins():
     P1, s1 = rom.pod(np.outer(a, b), 1)
     assert s1[0] == pytest.approx(np.linalg.norm(a) * np.linalg.norm(b), rel=1e-13)
     assert abs(abs(P1[:, 0] @ a) / np.linalg.norm(a) - 1) < 1e-13
+
+
+def test_sigma_min_dense_by_shift_invert():
+    """sigma_min of K_ff (dense eigvalsh) against scipy's shift-invert Lanczos (ARPACK): two
+    independent routes to the smallest eigenvalue that the Section 3.3 bounds use."""
+    import scipy.sparse.linalg as spla
+    for p in (w.mbb_2d(12, 5), w.cantilever_3d(4, 3, 2)):
+        rho = hatfilter.filter_fwd(p, w.design_field(p, 1))
+        s_dense = rom.sigma_min_dense(p, rho)
+        s_arpack = spla.eigsh(fem.reduced_K(p, rho), k=1, sigma=0.0, which="LM", return_eigenvectors=False)[0]
+        assert s_dense == pytest.approx(s_arpack, rel=1e-9)
+        assert s_dense > 0
