@@ -144,10 +144,18 @@ typedef enum {
                                       eigenvectors of the 1D Q1 Neumann matrices (two transforms of
                                       FP64 mode products and a diagonal scaling); self-adjoint, so
                                       adjoint = 1 gives the same map */
-  TOPO_PARAM_HELMHOLTZ_R = 16      /* the Helmholtz length r in element lengths (0 = default:
+  TOPO_PARAM_HELMHOLTZ_R = 16,     /* the Helmholtz length r in element lengths (0 = default:
                                       rmin / (2 sqrt 3), the length the filter's cited reference
                                       relates to a cone radius rmin; the paper prints
                                       r = 2 sqrt(3) R) */
+  TOPO_PARAM_ROM_ASSEMBLY = 17     /* contraction H_r = sum_e E(rho_r,e) Hel[e] of
+                                      topo_rom_eval_batch and topo_rom_assemble_batch: 1 (default) =
+                                      tensor cores (tcgen05 kind::f16) on the Ozaki scheme's exact
+                                      split of each FP64 operand into 8 BF16 digits, with exact
+                                      FP32 sums over 512 element rows and FP64 beyond: each entry
+                                      within about 2^-51 of sum_e |E_e| |Hel[e]| of the exact sum,
+                                      up to 128 candidates per pass over Hel; 0 = FP64 SIMT (the
+                                      rounding of FP64 sums), 32 candidates per pass */
 } topo_param;
 
 /* Create a context for one problem; computes K_e (2x2(x2) Gauss quadrature), the filter
@@ -282,6 +290,16 @@ topo_status topo_rom_solve_elem_noalloc(topo_ctx* ctx, const double* rho, const 
 topo_status topo_rom_eval_batch(topo_ctx* ctx, int R, const double* psi, int ldp, int filtered,
                                 const double* Hel, const double* Phi, int k, int ld, const double* b,
                                 const double* f, double* Jk, double* resnorm, double* yhat, double* dpsi);
+
+/* Reduced matrices of R densities on one basis from their moduli (Section 3.4, Remark
+ * rom_assemble): H[r] = sum_{e < N_e} E[r][e] Hel[e] + E[r][N_e] Hel[N_e], unpacked to k x k
+ * row-major. E: R rows of N_e + 1 doubles at stride ldE >= N_e + 1 (E[r][e] = E(rho_e) for
+ * e < N_e and E[r][N_e] = 1 give the H of topo_rom_solve_elem); Hel from topo_rom_elem; H:
+ * device FP64[R * k * k]. R >= 0, 1 <= k <= 128. The contraction is the one
+ * TOPO_PARAM_ROM_ASSEMBLY selects; each H[r] depends only on row r of E. Asynchronous on the
+ * context's stream. */
+topo_status topo_rom_assemble_batch(topo_ctx* ctx, int R, const double* E, long long ldE, const double* Hel, int k,
+                                    double* H);
 
 /* A posteriori residual (Section 3.3; the trust-region constraint of Eq. trcon-topopt):
  * u_k = Phi yhat, r = f - K(rho) u_k on the free DOFs, resnorm[0] = ||r||_2,

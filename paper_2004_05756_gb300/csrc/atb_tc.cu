@@ -33,6 +33,7 @@
 #include <mutex>
 
 #include "common.cuh"
+#include "tcgen05.cuh"
 #include "tma.cuh"
 
 namespace topo {
@@ -51,18 +52,6 @@ constexpr int SMEM_BYTES = 1024 + STAGES * STAGE_BYTES + 512;
 // bits 24-28; M = N = 128.
 constexpr uint32_t IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
 
-// Shared-memory matrix descriptor: K-major operand in 8-row x 128-B atoms with the 128-byte
-// swizzle; start address >> 4 (bits 0-13), leading offset unused for this layout, stride
-// between 8-row atoms 1024 B (bits 32-45), descriptor version 1 (bits 46-47), swizzle mode 2
-// (bits 61-63). The tile base is 1024-byte aligned, so the base offset is 0.
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
-  return (uint64_t)((addr & 0x3FFFFu) >> 4) | ((uint64_t)(1024 >> 4) << 32) | ((uint64_t)1 << 46) |
-         ((uint64_t)2 << 61);
-}
-
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
 __device__ __forceinline__ void tc_mma(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
@@ -70,17 +59,6 @@ __device__ __forceinline__ void tc_mma(uint32_t dtmem, uint64_t adesc, uint64_t 
       "l"(adesc), "l"(bdesc), "r"(IDESC), "r"(accumulate)
       : "memory");
 }
-__device__ __forceinline__ void tc_commit(uint32_t bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
-}
-// 8 consecutive FP32 columns of this thread's TMEM lane.
-__device__ __forceinline__ void tc_ld8(uint32_t taddr, uint32_t (&r)[8]) {
-  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-               : "r"(taddr)
-               : "memory");
-}
-__device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
 
@@ -186,7 +164,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
           }
           tc_fence_after();
           const uint32_t st = stage0 + s * STAGE_BYTES;
-          const uint64_t da = smem_desc(st), db = smem_desc(st + 2 * HALF);
+          const uint64_t da = smem_desc_sw128(st), db = smem_desc_sw128(st + 2 * HALF);
 #pragma unroll
           for (int kk = 0; kk < 4; ++kk)  // K = 8 TF32 = 32 B per MMA: advance the start address by 32 B
             tc_mma(dt, da + 2 * kk, db + 2 * kk, (ci > q * SEG || kk > 0) ? 1u : 0u);

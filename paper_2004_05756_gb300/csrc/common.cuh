@@ -562,6 +562,7 @@ struct topo_ctx {
   int hdm_kernel;  // 0: assembled-stencil Chronopoulos-Gear PCG (FP64); 1: element-form PCG
   int pcg_max_ctas;  // cap on the CTAs of one persistent solve (0 = none)
   int rom_tensor;    // FP32 projection contraction: 1 tensor cores (tcgen05), 0 SIMT FP32
+  int rom_asm_tensor;  // per-density reduced assembly of many candidates: 1 tensor cores (Ozaki digits), 0 FP64 SIMT
   int apply_cols;    // columns per CTA of the 2D node-centric apply (0 = default split)
   int apply_stages;  // 2D FP32 block apply: 0 cp.async staging, 2-4 TMA units in flight per CTA
   int pcg_poly;      // FP64 stencil PCG: degree of the Chebyshev polynomial preconditioner (0 = auto)

@@ -414,6 +414,7 @@ extern "C" topo_status topo_create(const topo_problem* prob, void* cuda_stream, 
   c->max_outer = 30;
   c->wait_cycles = 2000000000LL;
   c->rom_tensor = 1;
+  c->rom_asm_tensor = 1;
   c->apply_stages = 3;
   c->pcg_poly = 0;
   c->pcg_mg = 1;
@@ -599,6 +600,10 @@ extern "C" topo_status topo_set_param(topo_ctx* c, topo_param which, double v) {
     case TOPO_PARAM_ROM_TENSOR:
       if (!(v == 0 || v == 1)) return fail(c, TOPO_ERR_INVALID, "rom tensor must be 0 or 1");
       c->rom_tensor = (int)v;
+      return TOPO_OK;
+    case TOPO_PARAM_ROM_ASSEMBLY:
+      if (!(v == 0 || v == 1)) return fail(c, TOPO_ERR_INVALID, "rom assembly must be 0 or 1");
+      c->rom_asm_tensor = (int)v;
       return TOPO_OK;
     case TOPO_PARAM_APPLY_STAGES:
       if (!(v == 0 || v == 2 || v == 3 || v == 4)) return fail(c, TOPO_ERR_INVALID, "apply stages must be 0, 2, 3 or 4");

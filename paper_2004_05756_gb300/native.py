@@ -23,7 +23,7 @@ PREC = {"fp64": TOPO_FP64, "fp32": TOPO_FP32_REFINED, "fp32_bf16ke": TOPO_FP32_B
  TOPO_PARAM_TILE_X, TOPO_PARAM_PCG_BLOCKS_PER_SM, TOPO_PARAM_INNER_CAP, TOPO_PARAM_HDM_KERNEL,
  TOPO_PARAM_PCG_MAX_CTAS, TOPO_PARAM_ROM_TENSOR, TOPO_PARAM_APPLY_STAGES, TOPO_PARAM_PCG_POLY,
  TOPO_PARAM_PCG_MG, TOPO_PARAM_MG_DEGREE, TOPO_PARAM_MG_SINGLE_NODES, TOPO_PARAM_FILTER,
- TOPO_PARAM_HELMHOLTZ_R) = range(17)
+ TOPO_PARAM_HELMHOLTZ_R, TOPO_PARAM_ROM_ASSEMBLY) = range(18)
 
 # Every entry point declared in include/topo.h (checked by the tests).
 EXPORTS = ["topo_create", "topo_destroy", "topo_last_error", "topo_set_param", "topo_check", "topo_sizes",
@@ -34,7 +34,7 @@ EXPORTS = ["topo_create", "topo_destroy", "topo_last_error", "topo_set_param", "
            "topo_batch_last_error", "topo_batch_context", "topo_batch_solve_hdm", "topo_batch_filter",
            "topo_batch_compliance_grad", "topo_batch_rom_solve_elem", "topo_tr_init", "topo_tr_project",
            "topo_tr_trials", "topo_tr_select", "topo_tr_update", "topo_rom_pod", "topo_output_grad",
-           "topo_rom_rhs", "topo_sigma_min"]
+           "topo_rom_rhs", "topo_sigma_min", "topo_rom_assemble_batch"]
 
 
 class TopoError(RuntimeError):
@@ -101,6 +101,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
         "topo_rom_solve_elem": ([P, P, P, I, P, P, P, P], I),
         "topo_rom_solve_elem_noalloc": ([P, P, P, I, P, P, P, P], I),
         "topo_rom_eval_batch": ([P, I, P, I, I, P, P, I, I, P, P, P, P, P, P], I),
+        "topo_rom_assemble_batch": ([P, I, P, LL, P, I, P], I),
         "topo_batch_create": ([ctypes.POINTER(topo_problem), I, P, ctypes.POINTER(P)], I),
         "topo_batch_destroy": ([P], I),
         "topo_batch_last_error": ([P], ctypes.c_char_p),
@@ -273,6 +274,13 @@ class Topo:
         self._chk(self.lib.topo_rom_eval_batch(self.h, R, _ptr(psi), ldp, 1 if filtered else 0, _ptr(Hel), _ptr(Phi),
                                                int(k), ld, _ptr(b), _ptr(f), _ptr(Jk), _ptr(resnorm), _ptr(yhat),
                                                _ptr(dpsi)), "topo_rom_eval_batch")
+
+    def topo_rom_assemble_batch(self, E, Hel, k: int, H):
+        """E: (R, ldE) moduli rows (N_e + 1 used each); H: R * k * k doubles."""
+        R = int(E.shape[0]) if E.dim() == 2 else 1
+        ldE = int(E.stride(0)) if E.dim() == 2 and R > 1 else int(self.Ne) + 1
+        self._chk(self.lib.topo_rom_assemble_batch(self.h, R, _ptr(E), ldE, _ptr(Hel), int(k), _ptr(H)),
+                  "topo_rom_assemble_batch")
 
     def topo_rom_error(self, rho, Phi, k: int, yhat, f, resnorm, uk=None):
         ld = _ld(Phi, self.N)

@@ -44,6 +44,8 @@ def main(argv=None):
     ap.add_argument("--mg", type=int, default=1, help="FP64 solve: 1 multigrid preconditioner, 0 polynomial")
     ap.add_argument("--mg-deg", type=int, default=2, help="multigrid: Chebyshev smoothing steps per side")
     ap.add_argument("--filter", default="cone", choices=["cone", "helmholtz"], help="density filter")
+    ap.add_argument("--rom-asm", type=int, default=1,
+                    help="reduced assembly of rom_eval_batch: 1 tensor cores (Ozaki digits), 0 FP64 SIMT")
     ap.add_argument("--mg-single", type=int, default=-1,
                     help="multigrid: nodes of levels run on one CTA (-1: the library's default)")
     a = ap.parse_args(argv)
@@ -60,6 +62,7 @@ def main(argv=None):
     T.topo_set_param(native.TOPO_PARAM_PCG_BLOCKS_PER_SM, a.blocks_per_sm)
     T.topo_set_param(native.TOPO_PARAM_ROM_TENSOR, a.rom_tensor)
     T.topo_set_param(native.TOPO_PARAM_FILTER, 1 if a.filter == "helmholtz" else 0)
+    T.topo_set_param(native.TOPO_PARAM_ROM_ASSEMBLY, a.rom_asm)
     T.topo_set_param(native.TOPO_PARAM_TILE_X, a.apply_cols)
     T.topo_set_param(native.TOPO_PARAM_APPLY_STAGES, a.apply_stages)
     T.topo_set_param(native.TOPO_PARAM_PCG_POLY, a.poly)
@@ -137,7 +140,7 @@ def main(argv=None):
     e1.synchronize()
     print(f"{a.call} {a.prec} shape={a.shape} m={a.m} k={k} hdm_kernel={a.hdm_kernel} bps={a.blocks_per_sm} "
           f"rom_tensor={a.rom_tensor} apply_cols={a.apply_cols} apply_stages={a.apply_stages} ld={ldp} "
-          f"filter={a.filter}: "
+          f"filter={a.filter} rom_asm={a.rom_asm}: "
           f"{e0.elapsed_time(e1) / a.reps * 1e3:.1f} us/call" +
           (f" poly={a.poly} mg={a.mg} deg={a.mg_deg} single={a.mg_single} {last_info}" if last_info else ""))
     T.topo_check()

@@ -77,8 +77,12 @@ def test_batched_filter_and_gradient(torch):
     reduced compliance equals the one-candidate path on topo_filter's density; the filtered
     gradient of topo_compliance_grad is the oracle's adjoint of the GPU's element gradient."""
     import torch as th
+    from paper_2004_05756_gb300.native import TOPO_PARAM_ROM_ASSEMBLY
     p = MESHES["q4_70x37"]()
     T = _ctx(p)
+    # the comparison is of the batched filter: the one-candidate reduced solve assembles in FP64
+    # SIMT, so the batch does too (the tensor-core assembly has its own tests)
+    T.topo_set_param(TOPO_PARAM_ROM_ASSEMBLY, 0)
     rr = helmholtz.default_length(p.rmin)
     f64 = dict(dtype=th.float64, device="cuda")
     psi0 = w.design_field(p, 1)
