@@ -501,6 +501,10 @@ topo_status launch_apply(topo_ctx* c, const double* rho, const void* V, void* Y,
 // ---------------------------------------------------------------------------------------
 // FP64 residual r = f - K u on free DOFs (0 on Dirichlet DOFs) with per-CTA partial sums of
 // ||r||^2 and ||f||^2 (free DOFs), then a fixed-order final reduction to sqrt values.
+// GRAD: each thread also forms the compliance gradient dc_e = -E'(rho_e) u_e^T K_e u_e of the
+// element whose lower-left node it owns, from the tile's staged u (its corners lie in the node
+// box and its halo), in the symmetric form and order of grad_kernel, so the values equal that
+// kernel's bit for bit without its global gathers of u_e.
 // ---------------------------------------------------------------------------------------
 template <int DIM>
 struct ResArgs {
@@ -512,9 +516,40 @@ struct ResArgs {
   double* r;        // may be null
   double* partial;  // [2 * G] per design
   long long ldr, ldu;  // strides of rho and u between the designs of blockIdx.y (several per launch)
+  double* dc;          // GRAD: element gradients, stride ldd between designs
+  long long ldd;
 };
 
-template <int DIM>
+template <int DIM, bool GRAD>
+__device__ __forceinline__ void tile_element_grad(const TileSmem<DIM, double>& s, const Grid& g, TileCoord tc, int tx,
+                                                  int ty, int tz, const typename KeOf<DIM, double>::type& ke,
+                                                  const double* rho, double* dc) {
+  using TS = TileSmem<DIM, double>;
+  constexpr int NN = DIM == 2 ? 4 : 8, ND = DIM * NN;
+  const int i = tc.i0 + tx, j = tc.j0 + ty, k = tc.k0 + tz;
+  if (i >= g.nx || j >= g.ny || (DIM == 3 && k >= g.nz)) return;
+  const long long e = (long long)i + (long long)g.nx * (j + (long long)g.ny * k);
+  double ue[ND];
+#pragma unroll
+  for (int L = 0; L < NN; ++L) {
+    const int cx = (L == 1 || L == 2 || L == 5 || L == 6) ? 1 : 0, cy = (L & 3) >= 2 ? 1 : 0, cz = L >= 4 ? 1 : 0;
+    const int h = ((tz + (DIM == 3 ? 1 + cz : 0)) * TS::HY + (ty + 1 + cy)) * TS::HX + (tx + 1 + cx);
+#pragma unroll
+    for (int c = 0; c < DIM; ++c) ue[DIM * L + c] = s.v[DIM * h + c];
+  }
+  double ce = 0.0;
+#pragma unroll(DIM == 2 ? ND : 1)
+  for (int r2 = 0; r2 < ND; ++r2) {
+    double t = 0.0;
+#pragma unroll
+    for (int c2 = r2 + 1; c2 < ND; ++c2) t = fma(ke.k[r2 * ND + c2], ue[c2], t);
+    t = fma(ke.k[r2 * ND + r2], ue[r2], t + t);
+    ce = fma(ue[r2], t, ce);
+  }
+  dc[e] = -dyoung<double>(rho[e], g.E0, g.Emin, g.ipenal) * ce;
+}
+
+template <int DIM, bool GRAD = false>
 __global__ void __launch_bounds__(TileShape<DIM>::NT) residual_kernel(const __grid_constant__ ResArgs<DIM> a) {
   __shared__ TileSmem<DIM, double> s;
   __shared__ double red[32];
@@ -543,6 +578,7 @@ __global__ void __launch_bounds__(TileShape<DIM>::NT) residual_kernel(const __gr
       }
       if (a.r) a.r[dof] = rv;
     }
+    if (GRAD) tile_element_grad<DIM, GRAD>(s, g, tc, tx, ty, tz, a.ke, rho, a.dc + blockIdx.y * a.ldd);
   }
   double t1 = block_sum(rr, red);
   double t2 = block_sum(ff, red);
@@ -599,8 +635,8 @@ long long residual_tiles(topo_ctx* c) {
 
 template <int DIM>
 static topo_status residual_batch_impl(topo_ctx* c, const double* rho, long long ldr, const double* U, long long ldu,
-                                       const double* f, double* out2, int R, double* partial,
-                                       const typename KeOf<DIM, double>::type& ke) {
+                                       const double* f, double* out2, int R, double* partial, double* dc,
+                                       long long ldd, const typename KeOf<DIM, double>::type& ke) {
   const long long tiles = num_tiles<DIM>(c->g);
   ResArgs<DIM> a;
   a.g = c->g;
@@ -612,7 +648,12 @@ static topo_status residual_batch_impl(topo_ctx* c, const double* rho, long long
   a.partial = partial;
   a.ldr = ldr;
   a.ldu = ldu;
-  residual_kernel<DIM><<<dim3((unsigned)tiles, (unsigned)R), TileShape<DIM>::NT, 0, c->stream>>>(a);
+  a.dc = dc;
+  a.ldd = ldd;
+  if (dc)
+    residual_kernel<DIM, true><<<dim3((unsigned)tiles, (unsigned)R), TileShape<DIM>::NT, 0, c->stream>>>(a);
+  else
+    residual_kernel<DIM><<<dim3((unsigned)tiles, (unsigned)R), TileShape<DIM>::NT, 0, c->stream>>>(a);
   note_launch();
   residual_final_kernel<<<R, 256, 0, c->stream>>>(partial, (int)tiles, out2);
   note_launch();
@@ -621,9 +662,9 @@ static topo_status residual_batch_impl(topo_ctx* c, const double* rho, long long
 }
 
 topo_status launch_residual64_batch(topo_ctx* c, const double* rho, long long ldr, const double* U, long long ldu,
-                                    const double* f, double* out2, int R, double* partial) {
-  if (c->g.dim == 2) return residual_batch_impl<2>(c, rho, ldr, U, ldu, f, out2, R, partial, c->q4_64);
-  return residual_batch_impl<3>(c, rho, ldr, U, ldu, f, out2, R, partial, c->h8_64);
+                                    const double* f, double* out2, int R, double* partial, double* dc, long long ldd) {
+  if (c->g.dim == 2) return residual_batch_impl<2>(c, rho, ldr, U, ldu, f, out2, R, partial, dc, ldd, c->q4_64);
+  return residual_batch_impl<3>(c, rho, ldr, U, ldu, f, out2, R, partial, dc, ldd, c->h8_64);
 }
 
 topo_status launch_residual64(topo_ctx* c, const double* rho, const double* u, const double* f, double* r,

@@ -593,12 +593,11 @@ topo_status launch_apply(topo_ctx* c, const double* rho, const void* V, void* Y,
 topo_status launch_filter_batch(topo_ctx* c, const double* in, long long ldin, double* out, long long ldout, int R,
                                 int adjoint);
 // Compliance gradients of R designs with one state each (ctx.cu).
-topo_status launch_grad_batch(topo_ctx* c, const double* rho, long long ldr, const double* U, long long ldu,
-                              double* dc, long long ldd, int R);
 // Residual norms ||f - K(rho_r) u_r|| (and / ||f||) of R designs in one launch (apply.cu): out2 +
 // 2 r receives them; partial holds 2 x tiles x R doubles.
 topo_status launch_residual64_batch(topo_ctx* c, const double* rho, long long ldr, const double* U, long long ldu,
-                                    const double* f, double* out2, int R, double* partial);
+                                    const double* f, double* out2, int R, double* partial, double* dc = nullptr,
+                                    long long ldd = 0);
 long long residual_tiles(topo_ctx* c);
 // Residual r = f - K(rho) u on free DOFs (0 on Dirichlet DOFs), FP64, with ||r||^2 and ||f||^2
 // partials reduced to out2[0..1] (device). r may be NULL (norms only).

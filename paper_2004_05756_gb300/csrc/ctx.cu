@@ -339,48 +339,6 @@ topo_status launch_filter_batch(topo_ctx* c, const double* in, long long ldin, d
   return filter_launch(c, in, out, adjoint ? 2 : 1, R, ldin, ldout);
 }
 
-// dc_r = -E'(rho_r) u_r,e^T K_e u_r,e for R designs with one state each, in one launch.
-topo_status launch_grad_batch(topo_ctx* c, const double* rho, long long ldr, const double* U, long long ldu,
-                              double* dc, long long ldd, int R) {
-  const Grid& g = c->g;
-  long long blocks = (g.nel + 127) / 128;
-  const long long cap = std::max(1LL, (16LL * c->num_sms + R - 1) / R);
-  if (blocks > cap) blocks = cap;
-  const dim3 grid((unsigned)blocks, (unsigned)R);
-  if (g.dim == 2) {
-    GradArgs<2> a;
-    a.g = g;
-    a.ke = c->q4_64;
-    a.rho = rho;
-    a.U = U;
-    a.ld = ldu;
-    a.m = 1;
-    a.dc = dc;
-    a.ldr = ldr;
-    a.ldu = ldu;
-    a.ldd = ldd;
-    a.Lam = nullptr;
-    grad_kernel<2><<<grid, 128, 0, c->stream>>>(a);
-  } else {
-    GradArgs<3> a;
-    a.g = g;
-    a.ke = c->h8_64;
-    a.rho = rho;
-    a.U = U;
-    a.ld = ldu;
-    a.m = 1;
-    a.dc = dc;
-    a.ldr = ldr;
-    a.ldu = ldu;
-    a.ldd = ldd;
-    a.Lam = nullptr;
-    grad_kernel<3><<<grid, 128, 0, c->stream>>>(a);
-  }
-  note_launch();
-  TOPO_CUDA_TRY(c, cudaGetLastError());
-  return TOPO_OK;
-}
-
 }  // namespace topo
 
 using namespace topo;

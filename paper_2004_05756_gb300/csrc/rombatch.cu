@@ -12,8 +12,9 @@
 //                                                   candidates, RC accumulators per thread and pair
 //   y_r = H_r^-1 b, J_k,r = b^T y_r                 one warp per candidate
 //   u_r = Phi y_r                                   Phi read once per group
-//   ||f - K(rho_r) u_r||, its ratio to ||f||        one launch (grid.y = candidate)
-//   dc_r = -E'(rho_r) u_r,e^T K_e u_r,e, dpsi_r      one launch each
+//   ||f - K(rho_r) u_r||, its ratio to ||f||,      one launch (grid.y = candidate) on staged
+//   dc_r = -E'(rho_r) u_r,e^T K_e u_r,e             tiles of u_r; the adjoint filter of dc_r
+//                                                   one more
 // Every sum runs in a fixed order, so each candidate's results are bitwise independent of the
 // others in the batch.
 #include <algorithm>
@@ -245,11 +246,11 @@ extern "C" topo_status topo_rom_eval_batch(topo_ctx* c, int R, const double* psi
       note_launch();
       TOPO_CUDA_TRY(c, cudaGetLastError());
       const int rg = s0 + r0;
-      s = launch_residual64_batch(c, rho_g, ldr, U, N, f, resnorm + 2 * (size_t)rg, nr, rpart);
+      // residual norms, and with dpsi the element gradients from the same staged tiles
+      s = launch_residual64_batch(c, rho_g, ldr, U, N, f, resnorm + 2 * (size_t)rg, nr, rpart, dpsi ? dc : nullptr,
+                                  Ne);
       if (s) return s;
       if (dpsi) {
-        s = launch_grad_batch(c, rho_g, ldr, U, N, dc, Ne, nr);
-        if (s) return s;
         s = filtered ? launch_filter_batch(c, dc, Ne, dpsi + (size_t)rg * ldp, ldp, nr, 1)
                      : (cudaMemcpy2DAsync(dpsi + (size_t)rg * ldp, (size_t)ldp * 8, dc, (size_t)Ne * 8, (size_t)Ne * 8,
                                           nr, cudaMemcpyDeviceToDevice, c->stream) == cudaSuccess
