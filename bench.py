@@ -69,10 +69,11 @@ def make_problem(cfg):
 
 
 def designs(p, args):
-    """Seeded inputs: per-step centre designs, R candidate designs, k snapshot designs."""
+    """Seeded inputs: per-step centre designs (warm-up, timed, then distinct ones for the
+    end-to-end pass), R candidate designs, k snapshot designs."""
     from paper_2004_05756_gb300 import workloads as w
     psi0 = w.design_field(p, 0)
-    nsteps = args.steps + args.warmup
+    nsteps = 2 * args.steps + args.warmup
     centres = w.perturbed_designs(p, psi0, nsteps, amplitude=0.05, first_seed=500)
     cands = w.perturbed_designs(p, psi0, args.rom_evals, amplitude=0.02, first_seed=2000)
     snaps = w.perturbed_designs(p, psi0, args.k, amplitude=0.1, first_seed=1)
@@ -316,6 +317,8 @@ def run_ours(args, rank, world):
         dcr = torch.empty(Ne, **f64)
         dpr = torch.empty((R, Ne), **f64)
         rho_r = torch.empty(Ne, **f64)
+        Jw = torch.zeros(1, **f64)
+        rnw = torch.zeros(2, **f64)
         flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > L2
         # initial snapshot window: HDM solves of k seeded designs (setup, untimed)
         for i in range(k):
@@ -325,7 +328,8 @@ def run_ours(args, rank, world):
 
     ev = lambda: torch.cuda.Event(enable_timing=True)
     stats = dict(step=[], hdm=[], solve=[], build=[], rom=[], rom_batch=[], iters=[], outer=[], relres=[], poly=[], mg=[],
-                 fallback=[])
+                 fallback=[], start_relres=[])
+    warm = {"kk": 0}  # reduced dimension of the basis the previous step left (0: none yet)
 
     def step(s, record=True, host_io=None):
         """One trust-region-shaped pass; host_io = (pinned inputs, pinned outputs) for e2e."""
@@ -336,7 +340,17 @@ def run_ours(args, rank, world):
             d_cent[s].copy_(hin["centre"][s], non_blocking=True)
             d_cand.copy_(hin["cands"], non_blocking=True)
         T.topo_filter(d_cent[s], rho)
-        Uc.zero_()
+        kw = warm["kk"] if args.hdm_start == "rom" else 0
+        if kw:
+            # the HDM solve starts from the ROM prediction at the new centre on the current basis,
+            # as the trust-region driver starts its solves from the reduced state
+            if Hel is not None:
+                T.topo_rom_solve_elem(rho, Hel, kw, b[:kw], Hw[:kw * kw], y[:kw], Jw)
+            else:
+                T.topo_rom_solve(rho, Phi[:kw], kw, b[:kw], Hw[:kw * kw], y[:kw], Jw, prec)
+            T.topo_rom_error(rho, Phi[:kw], kw, y[:kw], f, rnw, Uc[0])
+        else:
+            Uc.zero_()
         es0.record(stream)
         info = T.topo_solve_hdm(rho, F, Uc, rtol=1e-8, maxit=400000, prec=prec)
         es1.record(stream)
@@ -348,6 +362,7 @@ def run_ours(args, rank, world):
         kk = T.topo_rom_build(rho, Usnap, Phi, None if Hel is not None else H, b, f)
         if Hel is not None:
             T.topo_rom_elem(Phi[:kk], kk, Hel)
+        warm["kk"] = kk
         e2.record(stream)
         rom_ev = []
         if args.rom_batch and Hel is not None:
@@ -395,6 +410,8 @@ def run_ours(args, rank, world):
             stats["mg"].append(info.get("mg_levels", 0))
             stats["fallback"].append(info.get("fallback", 0))
             stats["relres"].append(info["relres"])
+            if kw:
+                stats["start_relres"].append(rnw[1].item())
         return info
 
     with torch.cuda.stream(stream):
@@ -430,9 +447,10 @@ def run_ours(args, rank, world):
         e2e_steps = []
         saved = stats["step"]
         stats_e2e = dict(step=[], hdm=[], solve=[], build=[], rom=[], rom_batch=[], iters=[], outer=[], relres=[], poly=[], mg=[],
-                 fallback=[])
+                 fallback=[], start_relres=[])
         stats_main = stats
-        for s in range(args.warmup, args.warmup + args.steps):
+        # centres the timed pass has not visited: their states are not in the snapshot window
+        for s in range(args.warmup + args.steps, args.warmup + 2 * args.steps):
             flush.zero_()
             stats = stats_e2e
             step(s, host_io=(hin, hout))
@@ -607,7 +625,9 @@ def run_ours(args, rank, world):
                                                       f"cantilever {p.nx}x{p.ny}x{p.nz} H8") +
                                f" ({N} DOFs), 1 HDM eval + basis update (k={k}) + {R} ROM evals per step", "k": k, "rom_evals_per_step": R, "precision": prec,
                    "rom_path": args.rom_path, "rom_batch": bool(args.rom_batch),
-                   "rtol": 1e-8, "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}"},
+                   "rtol": 1e-8, "hdm_start": ("ROM prediction at the centre on the previous step's basis"
+                                               if args.hdm_start == "rom" else "zero"),
+                   "l2": "flushed between steps (256 MB write)", "parallelism": f"replicas x{world}"},
         "p50_ms": pct(0.50), "p99_ms": pct(0.99),
         "latency_note": ("p50/p99 of the per-evaluation time; with the batched ROM evaluation (one call for "
                          "all R candidates) that is the batch time / R, and every candidate of a step is "
@@ -619,7 +639,9 @@ def run_ours(args, rank, world):
         "hdm_fp64_evals_per_s": 1e3 / statistics.fmean(hdm64) if hdm64 else None,
         "hdm_evals_per_s": 1e3 / hdm_ms, "rom_evals_per_s": 1e3 / statistics.fmean(rom_ms) if rom_ms else None,
         "basis_update_ms": statistics.fmean(stats["build"]),
-        "pcg": {"inner_iters": iters, "outer": outer, "relres": max(stats["relres"]), "fp64_iters": info64["iters"]},
+        "pcg": {"inner_iters": iters, "outer": outer, "relres": max(stats["relres"]), "fp64_iters": info64["iters"],
+                "start_relres_mean": statistics.fmean(stats["start_relres"]) if stats["start_relres"] else None,
+                "fp64_iters_note": "fp64_iters: the plain FP64 HDM evaluation (hdm_fp64_eval_ms), started from zero"},
         "accuracy": {"probe": probe, "J_centre_last_step": J_centre},
         "rom_model_error": {"candidates": len(model["J_rel"]), "k": kk, **model,
                             "note": "|J_k - J_HDM| / J_HDM at candidate designs (FP64 HDM at rtol 1e-10), next to "
@@ -952,6 +974,9 @@ def main():
     ap.add_argument("--rom-path", default="elem", choices=["elem", "phi"],
                     help="reduced matrix from cached element reduced matrices, or from K(rho) Phi")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--hdm-start", default="rom", choices=["rom", "zero"],
+                    help="initial iterate of each step's HDM solve: the ROM prediction at the new centre on "
+                         "the current basis (as the trust-region driver), or zero")
     ap.add_argument("--rom-batch", type=int, default=1,
                     help="1: the step's R ROM evaluations in one topo_rom_eval_batch call; 0: one by one")
     ap.add_argument("--cpu-baseline-3d", action="store_true",
