@@ -595,6 +595,9 @@ topo_status launch_filter_batch(topo_ctx* c, const double* in, long long ldin, d
 // Compliance gradients of R designs with one state each (ctx.cu).
 // Residual norms ||f - K(rho_r) u_r|| (and / ||f||) of R designs in one launch (apply.cu): out2 +
 // 2 r receives them; partial holds 2 x tiles x R doubles.
+size_t cgs2_scratch_doubles(topo_ctx* c);
+topo_status launch_cgs2(topo_ctx* c, const double* U, int m, long long ld, double* Phi, const double* f, double* b,
+                        double drop_rel, double* scratch, int* k_dev);
 topo_status launch_residual64_batch(topo_ctx* c, const double* rho, long long ldr, const double* U, long long ldu,
                                     const double* f, double* out2, int R, double* partial, double* dc = nullptr,
                                     long long ldd = 0);

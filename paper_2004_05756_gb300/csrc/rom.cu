@@ -795,61 +795,22 @@ extern "C" topo_status topo_rom_build(topo_ctx* c, const double* rho, const doub
   if (!dev_ptr_ok(rho) || !dev_ptr_ok(Usnap) || !dev_ptr_ok(Phi) || (H && !dev_ptr_ok(H)) || !dev_ptr_ok(b) ||
       !dev_ptr_ok(f))
     return fail(c, TOPO_ERR_INVALID, "topo_rom_build: null or misaligned pointer");
-  size_t pcap = partial_capacity(c, N, m);
-  size_t need = std::max(project_scratch(c, m, ld, TOPO_FP64), (pcap + 2 * 128 + 64) * sizeof(double));
+  // CGS2 with the rank rule (drop a column whose orthogonalised norm is below 1e-10 of the
+  // largest snapshot norm), b = Phi^T f and k in one cooperative launch, then one read of k
+  const size_t ncg = cgs2_scratch_doubles(c);
+  size_t need = std::max(project_scratch(c, m, ld, TOPO_FP64), (ncg + 64) * sizeof(double));
   topo_status s = ensure_scratch(c, need);
   if (s) return s;
   char* scratch = (char*)c->d_scratch;
-  double* partial = (double*)scratch;
-  double* coef = partial + pcap;       // [128]
-  double* nrm = coef + 128;            // [64]
-  RowSplit rs = row_split(c, N, 4);
-  const int nb = stream_blocks(c, N);
-  // largest snapshot norm
-  std::vector<double> norms(m);
-  for (int j = 0; j < m; ++j) {
-    nrm2_partial_kernel<<<rs.G, 256, 0, c->stream>>>(Usnap + (long long)j * ld, N, partial);
-    note_launch();
-    nrm2_final_kernel<<<1, 256, 0, c->stream>>>(partial, rs.G, nrm + (j % 64));
-    note_launch();
-    if (j % 64 == 63 || j == m - 1) {
-      int base = (j / 64) * 64, cnt = j - base + 1;
-      TOPO_CUDA_TRY(c, cudaMemcpyAsync(norms.data() + base, nrm, cnt * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-      TOPO_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-    }
-  }
-  double scale = 0.0;
-  for (double v : norms) scale = std::max(scale, v);
+  int* k_dev = (int*)((double*)scratch + ncg);
+  s = launch_cgs2(c, Usnap, m, ld, Phi, f, b, 1e-10, (double*)scratch, k_dev);
+  if (s) return s;
   int k = 0;
-  if (scale > 0.0) {
-    for (int j = 0; j < m; ++j) {
-      double* v = Phi + (long long)k * ld;
-      const double* u = Usnap + (long long)j * ld;
-      if (v != u) TOPO_CUDA_TRY(c, cudaMemcpyAsync(v, u, N * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
-      for (int pass = 0; pass < 2 && k > 0; ++pass) {
-        s = launch_atv(c, Phi, ld, k, v, N, partial, pcap, coef, nullptr);
-        if (s) return s;
-        gemv_kernel<<<nb, 256, k * sizeof(double), c->stream>>>(Phi, ld, k, coef, v, N, 1, nullptr);
-        note_launch();
-      }
-      nrm2_partial_kernel<<<rs.G, 256, 0, c->stream>>>(v, N, partial);
-      note_launch();
-      nrm2_final_kernel<<<1, 256, 0, c->stream>>>(partial, rs.G, nrm);
-      note_launch();
-      double hn = 0.0;
-      TOPO_CUDA_TRY(c, cudaMemcpyAsync(&hn, nrm, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-      TOPO_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-      if (hn >= 1e-10 * scale) {
-        scale_kernel<<<nb, 256, 0, c->stream>>>(v, N, nrm);
-        note_launch();
-        ++k;
-      }
-    }
-  }
+  TOPO_CUDA_TRY(c, cudaMemcpyAsync(&k, k_dev, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  TOPO_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   TOPO_CUDA_TRY(c, cudaGetLastError());
   *k_out = k;
-  if (k == 0) return TOPO_OK;
-  if (!H) return launch_atv(c, Phi, ld, k, f, N, partial, pcap, b, nullptr);  // b = Phi^T f only
+  if (k == 0 || !H) return TOPO_OK;  // b = Phi^T f is in place
   return project(c, rho, Phi, k, ld, TOPO_FP64, H, b, f, scratch);
 }
 
