@@ -811,7 +811,7 @@ extern "C" topo_status topo_rom_build(topo_ctx* c, const double* rho, const doub
   TOPO_CUDA_TRY(c, cudaGetLastError());
   *k_out = k;
   if (k == 0 || !H) return TOPO_OK;  // b = Phi^T f is in place
-  return project(c, rho, Phi, k, ld, TOPO_FP64, H, b, f, scratch);
+  return project(c, rho, Phi, k, ld, TOPO_FP64, H, nullptr, nullptr, scratch);  // H only: b stays the launch's
 }
 
 extern "C" topo_status topo_rom_solve(topo_ctx* c, const double* rho, const double* Phi, int k, int ld,
