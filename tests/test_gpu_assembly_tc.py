@@ -14,7 +14,8 @@ and FP64 references, through topo_rom_assemble_batch and topo_rom_eval_batch.
   within 2^-46 of the candidate's largest |H| entry (the balancing's purpose).
 - Shapes: a ragged last chunk and block (482 rows), several exact-accumulation drains per CTA
   (120,001 rows), one and several column tiles (k = 8, 16, 24, 40), R = 1, 100, 128 and 130 (two
-  passes); candidates evaluated alone and inside a batch agree bit for bit.
+  passes); candidates evaluated alone and inside a batch agree bit for bit, also through
+  topo_rom_eval_batch with 150 candidates.
 - topo_rom_eval_batch with either contraction: J_k and y differ by no more than the first-order
   effect of the assembly bound, |y|^T B |y| and |H^-1| B |y| with B = 3 eps sum_e |E_e| |Hel_e|."""
 import math
@@ -165,6 +166,40 @@ def test_independent_of_the_batch(torch):
     full = _assemble(T, E, Hel, k)
     for r in (0, 77, 127):
         assert np.array_equal(_assemble(T, E[r:r + 1], Hel, k)[0], full[r])
+
+
+def test_rom_eval_batch_more_than_one_pass(torch):
+    """150 candidates in one topo_rom_eval_batch call (two tensor-core passes of up to 128, groups
+    of 32 inside each): every candidate's J_k, residual norms, y and gradient equal its own
+    one-candidate call bit for bit."""
+    import torch as th
+    p = w.mbb_2d(30, 12)
+    k = 6
+    T = _ctx(p, True)
+    psi0 = w.design_field(p, 2)
+    snaps = w.perturbed_designs(p, psi0, k, amplitude=0.1, first_seed=21)
+    Phi = rom.basis(np.stack([fem.solve(p, hatfilter.filter_fwd(p, snaps[:, i]))[:, 0] for i in range(k)], 1))
+    kk = Phi.shape[1]
+    f = p.F[:, 0]
+    f64 = dict(dtype=th.float64, device="cuda")
+    Hel = th.zeros((p.nel + 1) * kk * (kk + 1) // 2, **f64)
+    T.topo_rom_elem(cols(Phi), kk, Hel)
+    b, fd = dev(Phi.T @ f), dev(f)
+    R = 150
+    psi = dev(np.ascontiguousarray(w.perturbed_designs(p, psi0, R, amplitude=0.02, first_seed=500).T))
+
+    def run(ps):
+        n = ps.shape[0]
+        out = (th.zeros(n, **f64), th.zeros((n, 2), **f64), th.zeros((n, kk), **f64), th.zeros((n, p.nel), **f64))
+        T.topo_rom_eval_batch(ps, Hel, cols(Phi), kk, b, fd, *out)
+        T.topo_check()
+        return [o.cpu().numpy() for o in out]
+
+    full = run(psi)
+    for r in (0, 31, 127, 128, 149):
+        one = run(psi[r:r + 1].contiguous())
+        for a, o in zip(full, one):
+            assert np.array_equal(a[r], o[0]), r
 
 
 def test_rom_eval_batch_both_contractions(torch):
