@@ -520,7 +520,7 @@ struct ResArgs {
   long long ldd;
 };
 
-template <int DIM, bool GRAD>
+template <int DIM>
 __device__ __forceinline__ void tile_element_grad(const TileSmem<DIM, double>& s, const Grid& g, TileCoord tc, int tx,
                                                   int ty, int tz, const typename KeOf<DIM, double>::type& ke,
                                                   const double* rho, double* dc) {
@@ -578,7 +578,7 @@ __global__ void __launch_bounds__(TileShape<DIM>::NT) residual_kernel(const __gr
       }
       if (a.r) a.r[dof] = rv;
     }
-    if (GRAD) tile_element_grad<DIM, GRAD>(s, g, tc, tx, ty, tz, a.ke, rho, a.dc + blockIdx.y * a.ldd);
+    if (GRAD) tile_element_grad<DIM>(s, g, tc, tx, ty, tz, a.ke, rho, a.dc + blockIdx.y * a.ldd);
   }
   double t1 = block_sum(rr, red);
   double t2 = block_sum(ff, red);
